@@ -1,0 +1,243 @@
+"""CPU oracle for sparse-sign sketch-and-precondition least squares.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg import this package; the CUDA library and its
+Python binding never do.  It is a ctypes wrapper around ``lsq_oracle.c``: plain,
+slow, single-threaded FP64 C written from the paper (arXiv 2506.03070):
+
+* ``philox4x64_10``      -- the counter-based generator both sides implement
+                           from its published definition (Salmon et al., SC'11).
+* ``sketch_indices``     -- Sec. 3.1.2 rejection sampling + Algorithm 3 signs.
+* ``sketch_apply``       -- Y = S [A | b] (Sec. 2.1 definition, Algorithm 1).
+* ``householder_qr``     -- Algorithm 1 "QR(Y)" (textbook unblocked Householder).
+* ``tri_inverse``        -- Algorithm 1 "M = R^{-1}", explicit (Sec. 3.2).
+* ``lsqr``               -- Algorithm 2, preconditioned LSQR.
+* ``backward_error``     -- Stewart's normal-equation bound ||A^T r|| / (||A||_F ||r||).
+* ``backward_error_kw``  -- Karlson-Waldén estimate of the optimal normwise
+                           backward error (the acceptance metric).
+* ``solve``              -- Algorithm 1 end to end.
+
+Pins: every function is checked in ``tests/test_oracle_*.py`` against facts
+fixed by the paper or by mathematics (numpy's Philox, closed-form redraw
+probabilities, uniformity over subsets, dense S@A, numpy QR/lstsq, scipy
+LSQR iterates, the App. A bounds).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lsq_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liblsq_oracle.so")
+_lib = None
+
+ORC_OK, ORC_ERR_ARG, ORC_ERR_SKETCH, ORC_ERR_RANK, ORC_ERR_NOCONV, ORC_ERR_OOM = 0, -1, -2, -3, -4, -5
+
+
+def build(force: bool = False) -> str:
+    """Compile lsq_oracle.c with gcc (plain -O2, no fast-math, no OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class LsqrInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int64), ("stop", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("anorm_est", ctypes.c_double), ("normal_rel", ctypes.c_double), ("rnorm_est", ctypes.c_double)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int64), ("stop", ctypes.c_int32), ("sketch_rounds_max", ctypes.c_int32),
+                ("backward_error", ctypes.c_double), ("anorm_est", ctypes.c_double)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build()
+        L = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        i64, i32, u64, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_double
+        L.orc_philox4x64_10.argtypes = [P, P, P]
+        L.orc_philox4x64_10.restype = None
+        L.orc_sketch_row.argtypes = [u64, i64, i64, i32, P, P]
+        L.orc_sketch_indices.argtypes = [u64, i64, i64, i64, i32, P, P, P]
+        L.orc_sketch_apply.argtypes = [P, i64, i64, i64, P, i64, i32, u64, i64, P, i64]
+        L.orc_householder_qr.argtypes = [P, i64, i64, i64, P]
+        L.orc_tri_inverse.argtypes = [P, i64, i64, P, i64]
+        L.orc_lsqr.argtypes = [P, i64, i64, i64, P, P, P, f64, i64, P, P, P, P]
+        L.orc_backward_error.argtypes = [P, i64, i64, i64, P, P, f64, P]
+        L.orc_backward_error.restype = f64
+        L.orc_solve.argtypes = [P, i64, i64, i64, P, i64, i32, u64, f64, i64, P, P, P, P, P]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class OracleError(RuntimeError):
+    def __init__(self, rc, what):
+        super().__init__(f"oracle {what} failed with status {rc}")
+        self.rc = rc
+
+
+def philox4x64_10(counter, key):
+    c = np.asarray(counter, dtype=np.uint64).copy()
+    k = np.asarray(key, dtype=np.uint64).copy()
+    out = np.zeros(4, dtype=np.uint64)
+    lib().orc_philox4x64_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def sketch_indices(seed, row0, rows, d, zeta, with_rounds=False):
+    """(idx int32 rows x zeta, sign int8 rows x zeta[, rounds int32 rows])."""
+    idx = np.zeros((rows, zeta), dtype=np.int32)
+    sgn = np.zeros((rows, zeta), dtype=np.int8)
+    rnd = np.zeros(rows, dtype=np.int32)
+    rc = lib().orc_sketch_indices(seed, row0, rows, d, zeta, _p(idx), _p(sgn), _p(rnd))
+    if rc != ORC_OK:
+        raise OracleError(rc, "sketch_indices")
+    return (idx, sgn, rnd) if with_rounds else (idx, sgn)
+
+
+def sketch_apply(A, b, d, zeta, seed, row0=0):
+    """Y = S [A | b] (d x (n+1)), or S A (d x n) when b is None."""
+    A = _f64(A)
+    m, n = A.shape
+    bb = None if b is None else _f64(b)
+    ncol = n + (0 if b is None else 1)
+    Y = np.zeros((d, ncol), dtype=np.float64)
+    rc = lib().orc_sketch_apply(_p(A), m, n, n, _p(bb), d, zeta, seed, row0, _p(Y), ncol)
+    if rc != ORC_OK:
+        raise OracleError(rc, "sketch_apply")
+    return Y
+
+
+def householder_qr(Y):
+    """Returns (R_full, tau): R_full holds R in its upper triangle (rows x cols)."""
+    W = _f64(Y).copy()
+    rows, cols = W.shape
+    tau = np.zeros(min(rows, cols), dtype=np.float64)
+    rc = lib().orc_householder_qr(_p(W), rows, cols, cols, _p(tau))
+    if rc != ORC_OK:
+        raise OracleError(rc, "householder_qr")
+    return np.triu(W[: min(rows, cols)]), W, tau
+
+
+def tri_inverse(R):
+    R = _f64(R)
+    n = R.shape[0]
+    M = np.zeros((n, n), dtype=np.float64)
+    rc = lib().orc_tri_inverse(_p(R), n, n, _p(M), n)
+    if rc != ORC_OK:
+        raise OracleError(rc, "tri_inverse")
+    return M
+
+
+def lsqr(A, b, M, x0, tol, maxit, trace=False):
+    A, b, M, x0 = _f64(A), _f64(b), _f64(M), _f64(x0)
+    m, n = A.shape
+    x = np.zeros(n, dtype=np.float64)
+    info = LsqrInfo()
+    tr = np.zeros((max(maxit, 1), n), dtype=np.float64) if trace else None
+    ab = np.zeros((maxit + 2, 2), dtype=np.float64) if trace else None
+    rc = lib().orc_lsqr(_p(A), m, n, n, _p(b), _p(M), _p(x0), tol, maxit, _p(x), ctypes.byref(info), _p(tr), _p(ab))
+    if rc not in (ORC_OK, ORC_ERR_NOCONV):
+        raise OracleError(rc, "lsqr")
+    out = {"x": x, "iters": info.iters, "stop": info.stop, "anorm_est": info.anorm_est,
+           "normal_rel": info.normal_rel, "rnorm_est": info.rnorm_est, "status": rc}
+    if trace:
+        out["trace"] = tr[: info.iters]
+        out["alpha_beta"] = ab[: info.iters + 1]
+    return out
+
+
+def backward_error(A, b, x, tol=1e-12, parts=False):
+    A, b, x = _f64(A), _f64(b), _f64(x)
+    m, n = A.shape
+    out = np.zeros(3, dtype=np.float64)
+    eta = lib().orc_backward_error(_p(A), m, n, n, _p(b), _p(x), tol, _p(out))
+    if parts:
+        return eta, {"rnorm": out[0], "normal": out[1], "fro": out[2]}
+    return eta
+
+
+def backward_error_kw(A, b, x):
+    """Karlson-Waldén estimate of the optimal backward error of x as a
+    least-squares solution, relative to ||A||_F:
+
+        mu~(x) = || (||x||^2 A^T A + ||r||^2 I)^{-1/2} A^T r || / ||A||_F,  r = b - A x.
+
+    Grcar, Saunders & Su (2007) show mu~ agrees with the optimal
+    Waldén-Karlson-Sun backward error to within a small factor (asymptotically
+    exactly as x -> x_star).  Computed without an SVD: with K = [||x|| A ; ||r|| I]
+    and K = Q_K R_K, K^T K = ||x||^2 A^T A + ||r||^2 I, so mu~ = ||R_K^{-T} A^T r||.
+    Works on numpy arrays (LAPACK QR) or on torch tensors of any device."""
+    try:
+        import torch
+        is_torch = isinstance(A, torch.Tensor)
+    except ImportError:  # pragma: no cover
+        is_torch = False
+    if is_torch:
+        import torch
+        r = b - A @ x
+        g = A.T @ r
+        nx, nr = torch.linalg.vector_norm(x), torch.linalg.vector_norm(r)
+        n = A.shape[1]
+        K = torch.cat([nx * A, nr * torch.eye(n, dtype=A.dtype, device=A.device)], dim=0)
+        R = torch.linalg.qr(K, mode="r")[1]
+        del K
+        y = torch.linalg.solve_triangular(R.T, g[:, None], upper=False)[:, 0]
+        return float(torch.linalg.vector_norm(y) / torch.linalg.matrix_norm(A))
+    import scipy.linalg as sl
+    A, b, x = _f64(A), _f64(b), _f64(x)
+    r = b - A @ x
+    g = A.T @ r
+    n = A.shape[1]
+    K = np.vstack([np.linalg.norm(x) * A, np.linalg.norm(r) * np.eye(n)])
+    R = np.linalg.qr(K, mode="r")
+    y = sl.solve_triangular(R, g, trans="T")
+    return float(np.linalg.norm(y) / np.linalg.norm(A))
+
+
+def solve(A, b, d, zeta, seed, tol, maxit):
+    A, b = _f64(A), _f64(b)
+    m, n = A.shape
+    x = np.zeros(n)
+    R = np.zeros((n, n))
+    M = np.zeros((n, n))
+    x0 = np.zeros(n)
+    info = SolveInfo()
+    rc = lib().orc_solve(_p(A), m, n, n, _p(b), d, zeta, seed, tol, maxit, _p(x), _p(R), _p(M), _p(x0),
+                         ctypes.byref(info))
+    if rc not in (ORC_OK, ORC_ERR_NOCONV):
+        raise OracleError(rc, "solve")
+    return {"x": x, "R": R, "M": M, "x0": x0, "iters": info.iters, "stop": info.stop,
+            "backward_error": info.backward_error, "status": rc}
+
+
+def default_maxit(n, d, tol):
+    """10 * ceil(log(tol) / log(sqrt(n/d))): ten times the rate estimate of
+    Sec. 4.3 (error ~ (n/d)^{t/2})."""
+    rate = np.sqrt(n / d)
+    return int(10 * np.ceil(np.log(tol) / np.log(rate)))
+
+
+if __name__ == "__main__":  # pragma: no cover
+    print(build(force="--force" in sys.argv))

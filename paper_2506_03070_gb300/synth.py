@@ -1,0 +1,112 @@
+"""Seeded synthetic least-squares problems shaped like the paper's dense test
+problems (tall, dense, controlled condition number, optional coherent rows;
+Sec. 4.1 and Table 1).  The paper's own matrices (MNIST, SuiteSparse, Krylov
+bases) are not available; these stand in for them.
+
+This module holds input generation only -- none of the solver's arithmetic --
+so both the CUDA path's tests and the CPU oracle can take their inputs from it.
+
+Recipe (``dense_problem``):
+  U = Q of QR(G1), G1 ~ N(0,1)^{m x n}        (seed)
+  V = Q of QR(G2), G2 ~ N(0,1)^{n x n}        (seed + 1)
+  s = geomspace(1, 1/cond, n)
+  A = U diag(s) V^T
+  optionally: a seeded fraction of rows scaled by ``coherent_scale`` (seed + 4)
+  x_true ~ N(0,1)^n                            (seed + 2)
+  r_perp = (I - Q Q^T) g, g ~ N(0,1)^m         (seed + 3), Q = orthonormal basis
+           of range(A) (U itself when no rows were scaled), scaled to norm
+           ``resid_norm``
+  b = A x_true + r_perp
+
+Because r_perp is orthogonal to range(A), x_true is the exact least-squares
+solution and ||b - A x_true|| = resid_norm (up to rounding of the construction).
+
+``batched_problem`` is the cheap construction used for many small problems:
+  A = (G / sqrt(m)) diag(s) H1 H2 with H1, H2 random Householder reflectors,
+  b = A x_true + 1e-6 g/||g||.
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+
+def _gen(device, seed):
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    return g
+
+
+def _orth(G):
+    Q, R = torch.linalg.qr(G, mode="reduced")
+    # fix signs so the construction does not depend on the QR's sign convention
+    d = torch.sign(torch.diagonal(R))
+    d[d == 0] = 1
+    return Q * d
+
+
+def dense_problem(m, n, cond, *, resid_norm=1e-6, coherent_frac=0.0, coherent_scale=1e4, seed=0,
+                  device="cpu", dtype=torch.float64):
+    dev = torch.device(device)
+    G1 = torch.randn(m, n, generator=_gen(dev, seed), device=dev, dtype=dtype)
+    U = _orth(G1)
+    del G1
+    G2 = torch.randn(n, n, generator=_gen(dev, seed + 1), device=dev, dtype=dtype)
+    V = _orth(G2)
+    s = torch.logspace(0.0, -math.log10(cond), n, device=dev, dtype=dtype)
+    A = (U * s) @ V.T
+    Q = U
+    if coherent_frac > 0:
+        k = max(1, int(round(coherent_frac * m)))
+        perm = torch.randperm(m, generator=_gen("cpu", seed + 4))[:k].to(dev)
+        A[perm] *= coherent_scale
+        del U
+        Q = _orth(A)
+    x_true = torch.randn(n, generator=_gen(dev, seed + 2), device=dev, dtype=dtype)
+    g = torch.randn(m, generator=_gen(dev, seed + 3), device=dev, dtype=dtype)
+    for _ in range(2):  # project twice for orthogonality to rounding level
+        g = g - Q @ (Q.T @ g)
+    r_perp = g * (resid_norm / torch.linalg.vector_norm(g))
+    del Q
+    b = A @ x_true + r_perp
+    return {"A": A.contiguous(), "b": b, "x_true": x_true, "resid_norm": resid_norm, "cond": cond}
+
+
+def config0(device="cpu"):
+    """A 20000 x 200, s geometric 1..1e-8, ||r_perp|| = 1e-6; d = 800, zeta = 8."""
+    p = dense_problem(20000, 200, 1e8, resid_norm=1e-6, seed=0, device=device)
+    p.update(d=800, zeta=8, tol=1e-12, seed_sketch=42, name="dense_20000x200_cond1e8")
+    return p
+
+
+def config1(device="cuda"):
+    """A 2,000,000 x 500 (8 GB), s geometric 1..1e-10, 1% of rows scaled x1e4;
+    d = 2000, zeta = 8."""
+    p = dense_problem(2_000_000, 500, 1e10, resid_norm=1e-6, coherent_frac=0.01, coherent_scale=1e4, seed=10,
+                      device=device)
+    p.update(d=2000, zeta=8, tol=1e-12, seed_sketch=43, name="dense_2000000x500_cond1e10_coherent")
+    return p
+
+
+def _householder(n, gen, device, dtype):
+    v = torch.randn(n, generator=gen, device=device, dtype=dtype)
+    v = v / torch.linalg.vector_norm(v)
+    return v
+
+
+def batched_problem(m, n, cond, *, seed, device="cpu", dtype=torch.float64):
+    """Cheap construction: A = (G/sqrt(m)) diag(s) H1 H2, H = I - 2 v v^T.
+    cond(A) is within (1+sqrt(n/m))/(1-sqrt(n/m)) of ``cond``."""
+    dev = torch.device(device)
+    gen = _gen(dev, seed)
+    G = torch.randn(m, n, generator=gen, device=dev, dtype=dtype) / math.sqrt(m)
+    s = torch.logspace(0.0, -math.log10(cond), n, device=dev, dtype=dtype)
+    A = G * s
+    for _ in range(2):
+        v = _householder(n, gen, dev, dtype)
+        A = A - 2.0 * (A @ v)[:, None] * v[None, :]
+    x_true = torch.randn(n, generator=gen, device=dev, dtype=dtype)
+    g = torch.randn(m, generator=gen, device=dev, dtype=dtype)
+    b = A @ x_true + 1e-6 * g / torch.linalg.vector_norm(g)
+    return {"A": A.contiguous(), "b": b, "x_true": x_true, "cond": cond}
