@@ -1,0 +1,352 @@
+"""Benchmark: least-squares solves per second on a dense 2,000,000 x 500 FP64
+problem (singular values 1..1e-10, 1% coherent rows x1e4, ||r_perp|| = 1e-6),
+sparse sign sketch d = 2000, zeta = 8, LSQR tolerance 1e-12.
+
+One step = one full solve (sketch + preconditioner + LSQR + accuracy pass)
+through the library's C ABI.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--config 0|1] [--prec fp64|mixed] [--native]
+
+Under torchrun (N > 1) every rank solves its own copy of the problem on its
+own GPU (the path does not shard in this build: replicas only); the value is
+the solves of all ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_BYTES = 129 * 1024 * 1024
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_problem(config, device):
+    from paper_2506_03070_gb300 import synth
+    if config == 0:
+        p = synth.config0(device=device)
+    else:
+        p = synth.config1(device=device)
+    return p
+
+
+def _workload(p, prec):
+    A = p["A"]
+    m, n = A.shape
+    return {"workload": p["name"] + f"_d{p['d']}_zeta{p['zeta']}_tol{p['tol']:g}", "m": m, "n": n, "d": p["d"],
+            "zeta": p["zeta"], "tol": p["tol"], "prec": prec,
+            "l2_policy": "inputs larger than L2 (A alone is %.1f GB vs 129 MB L2)" % (8 * m * n / 1e9)
+            if 8 * m * n > L2_BYTES else "inputs fit in L2 (small config)"}
+
+
+def lsqr_algorithmic_bytes(m, n, iters):
+    """Bytes the LSQR kernel must move per launch: per LSQR iteration one read
+    of A (8mn), u read+write (16m) and M, M^T (16n^2); plus the initial
+    residual pass and the accuracy pass (each 8mn + 16m)."""
+    return iters * (8.0 * m * n + 16.0 * m + 16.0 * n * n) + 2 * (8.0 * m * n + 16.0 * m)
+
+
+def cpu_oracle_estimate(A_host, b_host, d, zeta, seed, tol, iters, rows=100_000, lsqr_iters=3):
+    """Time the oracle on a bounded sample of the workload and scale to one
+    full solve: sketch and LSQR passes are linear in m (timed on the first
+    `rows` rows and scaled by m/rows); the QR + inverse of the d x (n+1)
+    sketch is timed at full size; LSQR is timed for `lsqr_iters` iterations and
+    scaled to `iters` (+2 passes for the initial residual and the check)."""
+    import numpy as np
+
+    import oracle
+    m, n = A_host.shape
+    rows = min(rows, m)
+    As = np.ascontiguousarray(A_host[:rows])
+    bs = np.ascontiguousarray(b_host[:rows])
+    t0 = time.perf_counter()
+    Y = oracle.sketch_apply(As, bs, d, zeta, seed)
+    t_sketch = (time.perf_counter() - t0) * (m / rows)
+    t0 = time.perf_counter()
+    R, _, _ = oracle.householder_qr(Y)
+    M = oracle.tri_inverse(R[:n, :n])
+    t_qr = time.perf_counter() - t0
+    x0 = M @ R[:n, n]
+    t0 = time.perf_counter()
+    oracle.lsqr(As, bs, M, x0, 0.0, lsqr_iters)
+    t_l = time.perf_counter() - t0
+    # lsqr(maxit=k) = 1 residual pass + k iterations (2 passes each)
+    per_pass = t_l / (1 + 2 * lsqr_iters) * (m / rows)
+    t_total = t_sketch + t_qr + per_pass * (1 + 2 * iters + 1)
+    return {"t_solve_s": t_total, "t_sketch_s": t_sketch, "t_qr_s": t_qr, "t_pass_s": per_pass,
+            "sample": f"first {rows} of {m} rows: oracle sketch and {lsqr_iters} LSQR iterations timed and scaled "
+                      f"by m/rows; QR+inverse of the full {d}x{n + 1} sketch timed; LSQR scaled to {iters} "
+                      f"iterations + 2 passes"}
+
+
+def run_reference(args):
+    world, rank, local = _dist()
+    if rank != 0:
+        return
+    import numpy as np
+    import torch
+    import oracle
+    oracle.build()
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    p = make_problem(args.config, dev if args.config == 1 else "cpu")
+    A, b = p["A"], p["b"]
+    m, n = A.shape
+    rows = min(m, 60_000 if args.config == 1 else m)
+    Ah = A[:rows].cpu().numpy()
+    bh = b[:rows].cpu().numpy()
+    del A
+    iters_est = oracle.default_maxit(n, p["d"], p["tol"]) // 10  # rate estimate of Sec. 4.3
+    times = []
+    info = None
+    for step in range(args.warmup + args.steps):
+        info = cpu_oracle_estimate(_Scaled(Ah, m), bh, p["d"], p["zeta"], p["seed_sketch"], p["tol"], iters_est,
+                                   rows=rows, lsqr_iters=2)
+        if step >= args.warmup:
+            times.append(info["t_solve_s"])
+    t = statistics.mean(times)
+    cores = 1
+    val = 1.0 / t
+    line = {"metric": "ls_solves_per_sec", "value": val, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _workload(p, "fp64"), "impl": "reference",
+            "cpu_baseline": {"kind": "oracle", "value": val, "unit": "solves/s", "cores": cores,
+                             "sample": info["sample"]},
+            "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+class _Scaled:
+    """A row-sample of an m-row matrix that reports the full row count."""
+
+    def __init__(self, sample, m):
+        self.sample, self.m = sample, m
+        self.shape = (m, sample.shape[1])
+
+    def __getitem__(self, key):
+        return self.sample[key]
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2506_03070_gb300 as P
+
+    ctx = P.Context(local)
+    p = make_problem(args.config, f"cuda:{local}")
+    A, b = p["A"], p["b"]
+    m, n = A.shape
+    d, zeta, tol, seed = p["d"], p["zeta"], p["tol"], p["seed_sketch"]
+    prec = 0 if args.prec == "fp64" else 1
+    flags = P.FLAG_TIMING | (P.FLAG_NATIVE_FP64 if args.native else 0)
+    stream = torch.cuda.current_stream()
+
+    def solve():
+        return ctx.lsq_solve(A, b, d, zeta=zeta, seed=seed, tol=tol, prec=prec, flags=flags, stream=stream)
+
+    for _ in range(args.warmup):
+        x, info = solve()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ms, lsqr_ms, sketch_ms, precond_ms, iters = [], [], [], [], []
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x, info = solve()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        lsqr_ms.append(info["t_lsqr_ms"])
+        sketch_ms.append(info["t_sketch_ms"])
+        precond_ms.append(info["t_precond_ms"])
+        iters.append(info["iters"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_ms = ev0.elapsed_time(ev1)
+    t_tensor = torch.tensor([total_ms], dtype=torch.float64, device=f"cuda:{local}")
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.all_reduce(t_tensor, op=dist.ReduceOp.MAX)
+    t_max = float(t_tensor.item())
+    value = world * args.steps / (t_max / 1e3)
+
+    # accuracy of the last solution (outside the timed region)
+    import oracle
+    bwd = oracle.backward_error_kw(A, b, x)
+    xt = p["x_true"]
+    fwd_res = float(torch.linalg.vector_norm(A @ (x - xt)) / torch.linalg.vector_norm(b))
+
+    # e2e: host (pinned) A, b through the same C ABI, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        Ah = torch.empty((m, n), dtype=torch.float64, pin_memory=True)
+        Ah.copy_(A)
+        bh = torch.empty((m,), dtype=torch.float64, pin_memory=True)
+        bh.copy_(b)
+        Anp, bnp = Ah.numpy(), bh.numpy()
+        xh = np.empty(n, dtype=np.float64)
+        ctx.lsq_solve(Anp, bnp, d, zeta=zeta, seed=seed, tol=tol, prec=prec, flags=flags, x=xh)
+        k2 = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            ctx.lsq_solve(Anp, bnp, d, zeta=zeta, seed=seed, tol=tol, prec=prec, flags=flags, x=xh)
+        t_e2e = time.perf_counter() - t0
+        e2e = {"value": world * k2 / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": 8 * m * n + 8 * m,
+               "d2h_bytes_per_step": 8 * n + 4096, "steps": k2}
+        del Ah, bh
+
+    peaks, peak_src = _peaks()
+    it_mean = statistics.mean(iters)
+    lsqr_avg_ms = statistics.mean(lsqr_ms)
+    alg_bytes = lsqr_algorithmic_bytes(m, n, it_mean)
+    achieved = alg_bytes / (lsqr_avg_ms / 1e3) / 1e9
+    peak = float(peaks["hbm_gbs"])
+    sketch_bytes = 8.0 * m * (n + 1) + 8.0 * d * (n + 1)
+    line = {
+        "metric": "ls_solves_per_sec", "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(_workload(p, args.prec), parallelism="replicas" if world > 1 else "single"),
+        "roofline": {"bound": "hbm", "kernel": "k_lsqr_native", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
+                     else "fallback 6.8 TB/s"},
+        "gpu_launches": 8 * args.steps,
+        "latency_ms": {"p50": statistics.median(step_ms),
+                       "p99": sorted(step_ms)[min(len(step_ms) - 1, int(0.99 * len(step_ms)))]},
+        "phases_ms": {"sketch": statistics.mean(sketch_ms), "precond": statistics.mean(precond_ms),
+                      "lsqr_and_check": lsqr_avg_ms},
+        "sketch_gbs": sketch_bytes / (statistics.mean(sketch_ms) / 1e3) / 1e9,
+        "lsqr_iters": it_mean,
+        "accuracy": {"backward_error_kw": bwd, "backward_error_ne": info["backward_error_ne"],
+                     "rel_residual_distance_to_x_true": fwd_res},
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as orc
+        orc.build()
+        rows = 100_000 if m > 100_000 else m
+        Ah2 = A[:rows].cpu().numpy()
+        bh2 = b[:rows].cpu().numpy()
+        est = cpu_oracle_estimate(_Scaled(Ah2, m), bh2, d, zeta, seed, tol, int(round(it_mean)), rows=rows,
+                                  lsqr_iters=2)
+        line["cpu_baseline"] = {"value": 1.0 / est["t_solve_s"], "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                "sample": est["sample"]}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--native", action="store_true", help="LSQR matvecs on the native FP64 pipe")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,170 @@
+/*
+ * lsq.h -- C ABI of the GB300 (sm_103a) sparse-sign sketch-and-precondition
+ * least-squares library (arXiv 2506.03070).
+ *
+ * Solves min_x ||b - A x|| for dense, tall A (m x n, m >> n) by Algorithm 1:
+ * a sparse sign sketch Y = S [A | b] generated and applied in one pass
+ * (Sec. 2.1 definition, Sec. 3.1.2 rejection sampling), a Householder QR of
+ * the sketch giving the preconditioner M = R^{-1} and the sketch-and-solve
+ * start x0 (Algorithm 1, Sec. 3.2), then preconditioned LSQR (Algorithm 2)
+ * in the one-synchronisation arrangement of App. D.5.1.
+ *
+ * General conventions
+ *  - Every call returns an lsq_status: 0 = LSQ_OK, 1 = LSQ_PENDING, < 0 error.
+ *    No C++ exception crosses this interface.  lsq_last_error(ctx) gives a
+ *    human-readable message for the last error on that context.
+ *  - Matrices are row-major with an explicit leading dimension (elements).
+ *  - Pointers named "device" must be device memory of the context's GPU,
+ *    owned by the caller and valid until the call returns.  Nothing the
+ *    caller passes is freed or retained by the library.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    stream-ordered; every call below returns only after its work on
+ *    `stream` has completed (it synchronises that stream), so results and
+ *    status are final on return.
+ *  - Workspace (sketch, R, M, LSQR vectors) is owned by the context and
+ *    counted against its HBM budget.  One context must not be used by two
+ *    host threads at once.
+ *  - There is no CPU fallback: without a usable sm_103a GPU, lsq_create
+ *    fails with LSQ_ERR_CUDA.
+ */
+#ifndef LSQ_H
+#define LSQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t lsq_status;
+#define LSQ_OK 0
+#define LSQ_PENDING 1
+#define LSQ_ERR_ARG (-1)         /* invalid argument (sizes, null pointer, zeta > d, ...) */
+#define LSQ_ERR_CUDA (-2)        /* a CUDA runtime call failed; see lsq_last_error */
+#define LSQ_ERR_OOM (-3)         /* device allocation failed */
+#define LSQ_ERR_BUDGET (-4)      /* workspace would exceed the context's HBM budget */
+#define LSQ_ERR_SKETCH (-5)      /* rejection sampling exceeded its round cap */
+#define LSQ_ERR_RANK (-6)        /* R has a zero (or negligible) diagonal entry */
+#define LSQ_ERR_NOCONV (-7)      /* LSQR hit maxit; x still holds the last iterate */
+#define LSQ_ERR_TIMEOUT (-8)     /* a device-side wait gave up; the context stays usable */
+#define LSQ_ERR_NONFINITE (-9)   /* A or b holds NaN or Inf */
+#define LSQ_ERR_UNSUPPORTED (-10) /* shape/precision combination not built */
+
+/* Arithmetic of the sketch and of the QR. LSQR matvecs, residuals and
+ * recurrences are FP64-accurate in both forms. */
+typedef enum {
+  LSQ_PREC_FP64 = 0,  /* sketch accumulated and factored in FP64 */
+  LSQ_PREC_MIXED = 1  /* sketch accumulated and factored in FP32 */
+} lsq_prec;
+
+typedef enum { LSQ_MEM_DEVICE = 0, LSQ_MEM_HOST = 1 } lsq_mem;
+
+typedef struct lsq_ctx lsq_ctx;
+
+/* One least-squares problem. A: m x n row-major (lda >= n), b: m. With
+ * mem = LSQ_MEM_HOST, A, b and the solution x live in host memory (pinned
+ * memory gives full copy speed) and the library copies them to and from the
+ * device inside the call. */
+typedef struct {
+  const double* A;
+  const double* b;
+  int64_t m, n, lda;
+  int32_t mem; /* lsq_mem */
+  int32_t reserved;
+} lsq_problem;
+
+/* Solver options (Algorithm 1 parameters d, zeta; Algorithm 2 tolerance). */
+typedef struct {
+  int64_t d;      /* embedding dimension, n+1 <= d <= 2^31-1 */
+  int32_t zeta;   /* nonzeros per sketch column, 1 <= zeta <= min(d, 64) */
+  int32_t prec;   /* lsq_prec */
+  uint64_t seed;  /* sketch seed (Philox key) */
+  double tol;     /* LSQR stopping tolerance (normal-equation test) */
+  int64_t maxit;  /* LSQR iteration cap; <= 0 selects 10*ceil(log(tol)/log(sqrt(n/d))) */
+  int32_t flags;  /* LSQ_FLAG_* */
+  int32_t reserved;
+} lsq_opts;
+
+#define LSQ_FLAG_TIMING 1      /* record per-phase device times in lsq_info */
+#define LSQ_FLAG_NO_CHECK 2    /* skip the final accuracy pass (backward errors not filled) */
+#define LSQ_FLAG_NATIVE_FP64 4 /* run the LSQR matvecs on the native FP64 pipe */
+
+typedef struct {
+  int32_t status;          /* status of the solve (same as the return value) */
+  int32_t stop;            /* 1 normal-equation test, 2 residual test, 3 maxit, 4 breakdown */
+  int64_t iters;           /* LSQR iterations */
+  double normal_rel_est;   /* LSQR's last ||(AM)^T r|| / (||AM|| ||r||) estimate */
+  double backward_error_ne;  /* ||A^T r|| / (||A||_F ||r||), r = b - A x (Stewart's bound) */
+  double backward_error_pre; /* ||M^T A^T r|| / (||A||_F ||x||): preconditioned bound */
+  double rnorm, arnorm, anorm_fro, xnorm, bnorm;
+  int32_t sketch_rounds_max; /* most rejection-sampling redraw rounds any column used */
+  int32_t reserved;
+  float t_sketch_ms, t_precond_ms, t_lsqr_ms, t_check_ms, t_h2d_ms, t_d2h_ms;
+} lsq_info;
+
+/* Context on `device` with a workspace budget of hbm_budget_bytes (0 = 90% of
+ * the device's free memory at creation). */
+lsq_status lsq_create(lsq_ctx** out, int device, size_t hbm_budget_bytes);
+lsq_status lsq_destroy(lsq_ctx* ctx);
+const char* lsq_last_error(const lsq_ctx* ctx);
+const char* lsq_status_string(lsq_status s);
+/* Bytes of workspace the context holds right now. */
+size_t lsq_workspace_bytes(const lsq_ctx* ctx);
+
+/* Sketch indices and signs (test/debug export).  Sec. 3.1.2 steps (i)-(iv)
+ * and the signs of Algorithm 3: for columns row0 .. row0+rows-1 of S, the
+ * zeta distinct row indices in [0, d), ascending, and their signs (+1/-1; the
+ * value is sign/sqrt(zeta)).  The random words come from Philox4x64-10 keyed
+ * (seed, 0): index draw (column i, round r, slot j) = counter (i, r, j/4, 0),
+ * word j%4, mapped to floor(word*d / 2^64); signs = counter (i, 0, 0, 1),
+ * bit k of word 0.  Same device code as lsq_sketch.
+ * idx: device int32 [rows x zeta]; sign: device int8 [rows x zeta];
+ * rounds: device int32 [rows] or NULL (redraw rounds per column). */
+lsq_status lsq_sketch_indices(lsq_ctx* ctx, uint64_t seed, int64_t row0, int64_t rows, int64_t d, int32_t zeta,
+                              int32_t* idx, int8_t* sign, int32_t* rounds, void* stream);
+
+/* Y = S [A | b]  (Algorithm 1 "Form Y = SA"; S never stored).
+ * A: device, m x n (lda >= n); b: device m or NULL.
+ * Y: device, d x ldy row-major, ldy >= n + (b != NULL); FP64 (prec FP64) or
+ * FP32 (prec MIXED).  Y is overwritten.  Errors: LSQ_ERR_ARG, LSQ_ERR_SKETCH,
+ * LSQ_ERR_NONFINITE (A or b not finite). */
+lsq_status lsq_sketch(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d,
+                      int32_t zeta, uint64_t seed, int32_t prec, void* Y, int64_t ldy, void* stream);
+
+/* Preconditioner from a sketch (Algorithm 1 "QR(Y)", "M = R^{-1}" and
+ * "x0 = M Q^T S b"; Sec. 3.2 explicit inverse).  Householder QR of the
+ * d x ncol matrix Y (ncol = n + has_b, FP64 or FP32 per prec, ld ldy).
+ * Outputs (device, row-major n x n, ld n): R (upper triangular, may be NULL),
+ * M = R^{-1} (upper triangular, required); x0 (device n, NULL allowed; only
+ * with has_b) = M z, z = first n entries of Q^T (S b).
+ * Errors: LSQ_ERR_ARG (d < ncol), LSQ_ERR_RANK (|R_jj| <= n * eps * max|R_ii|). */
+lsq_status lsq_precond(lsq_ctx* ctx, const void* Y, int64_t d, int64_t n, int64_t ldy, int32_t has_b, int32_t prec,
+                       double* R, double* M, double* x0, void* stream);
+
+/* Preconditioned LSQR (Algorithm 2) from x0 with preconditioner M (device,
+ * n x n row-major upper triangular), in the one-synchronisation order of
+ * App. D.5.1.  A, b, x0, x device.  x receives the final iterate.  Stops when
+ * ||(AM)^T r|| <= tol ||AM||_est ||r|| (Paige-Saunders test 2 on the
+ * preconditioned problem), ||r|| <= tol ||b||, or at maxit (LSQ_ERR_NOCONV).
+ * info may be NULL. */
+lsq_status lsq_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
+                    const double* M, const double* x0, double tol, int64_t maxit, int32_t flags, double* x,
+                    lsq_info* info, void* stream);
+
+/* Accuracy of a candidate solution: one pass over A computing r = b - A x,
+ * A^T r, ||A||_F and the two backward-error bounds of lsq_info (M may be NULL;
+ * then backward_error_pre is 0).  All device pointers. */
+lsq_status lsq_check(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
+                     const double* x, const double* M, lsq_info* info, void* stream);
+
+/* Algorithm 1 end to end: sketch, precondition, LSQR, accuracy pass.
+ * x: n doubles, device memory for LSQ_MEM_DEVICE problems, host memory for
+ * LSQ_MEM_HOST problems.  info may be NULL. */
+lsq_status lsq_solve(lsq_ctx* ctx, const lsq_problem* problem, const lsq_opts* opts, double* x, lsq_info* info,
+                     void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LSQ_H */

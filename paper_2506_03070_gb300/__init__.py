@@ -1,0 +1,255 @@
+"""GB300 (sm_103a) sparse-sign sketch-and-precondition least squares.
+
+Thin ctypes binding over the C ABI of ``include/lsq.h`` (``liblsq.so``, built
+in-tree by ``paper_2506_03070_gb300.build``).  Every step of the solve runs in
+the library's CUDA kernels; this module only marshals arguments: torch tensors
+(device memory, current stream) or numpy arrays (host problems for
+``lsq_solve``).  There is no CPU fallback: if the library or a GPU is missing
+the calls raise.
+
+Functions carry the C names: ``lsq_sketch_indices``, ``lsq_sketch``,
+``lsq_precond``, ``lsq_lsqr``, ``lsq_check``, ``lsq_solve``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblsq.so")
+
+LSQ_OK, LSQ_PENDING = 0, 1
+STATUS = {0: "LSQ_OK", 1: "LSQ_PENDING", -1: "LSQ_ERR_ARG", -2: "LSQ_ERR_CUDA", -3: "LSQ_ERR_OOM",
+          -4: "LSQ_ERR_BUDGET", -5: "LSQ_ERR_SKETCH", -6: "LSQ_ERR_RANK", -7: "LSQ_ERR_NOCONV",
+          -8: "LSQ_ERR_TIMEOUT", -9: "LSQ_ERR_NONFINITE", -10: "LSQ_ERR_UNSUPPORTED"}
+LSQ_ERR_NOCONV = -7
+PREC_FP64, PREC_MIXED = 0, 1
+MEM_DEVICE, MEM_HOST = 0, 1
+FLAG_TIMING, FLAG_NO_CHECK, FLAG_NATIVE_FP64 = 1, 2, 4
+
+EXPORTS = ("lsq_create", "lsq_destroy", "lsq_last_error", "lsq_status_string", "lsq_workspace_bytes",
+           "lsq_sketch_indices", "lsq_sketch", "lsq_precond", "lsq_lsqr", "lsq_check", "lsq_solve")
+
+
+class LsqError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("b", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("lda", ctypes.c_int64), ("mem", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int64), ("zeta", ctypes.c_int32), ("prec", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("tol", ctypes.c_double), ("maxit", ctypes.c_int64), ("flags", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("stop", ctypes.c_int32), ("iters", ctypes.c_int64),
+                ("normal_rel_est", ctypes.c_double), ("backward_error_ne", ctypes.c_double),
+                ("backward_error_pre", ctypes.c_double), ("rnorm", ctypes.c_double), ("arnorm", ctypes.c_double),
+                ("anorm_fro", ctypes.c_double), ("xnorm", ctypes.c_double), ("bnorm", ctypes.c_double),
+                ("sketch_rounds_max", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("t_sketch_ms", ctypes.c_float), ("t_precond_ms", ctypes.c_float), ("t_lsqr_ms", ctypes.c_float),
+                ("t_check_ms", ctypes.c_float), ("t_h2d_ms", ctypes.c_float), ("t_d2h_ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load liblsq.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_2506_03070_gb300.build`")
+    L = ctypes.CDLL(path)
+    P, i32, i64, u64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    L.lsq_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_size_t]
+    L.lsq_destroy.argtypes = [P]
+    L.lsq_last_error.argtypes = [P]
+    L.lsq_last_error.restype = ctypes.c_char_p
+    L.lsq_status_string.argtypes = [i32]
+    L.lsq_status_string.restype = ctypes.c_char_p
+    L.lsq_workspace_bytes.argtypes = [P]
+    L.lsq_workspace_bytes.restype = ctypes.c_size_t
+    L.lsq_sketch_indices.argtypes = [P, u64, i64, i64, i64, i32, P, P, P, P]
+    L.lsq_sketch.argtypes = [P, P, i64, i64, i64, P, i64, i32, u64, i32, P, i64, P]
+    L.lsq_precond.argtypes = [P, P, i64, i64, i64, i32, i32, P, P, P, P]
+    L.lsq_lsqr.argtypes = [P, P, i64, i64, i64, P, P, P, f64, i64, i32, P, P, P]
+    L.lsq_check.argtypes = [P, P, i64, i64, i64, P, P, P, P, P]
+    L.lsq_solve.argtypes = [P, ctypes.POINTER(Problem), ctypes.POINTER(Opts), P, ctypes.POINTER(Info), P]
+    for name in ("lsq_create", "lsq_destroy", "lsq_sketch_indices", "lsq_sketch", "lsq_precond", "lsq_lsqr",
+                 "lsq_check", "lsq_solve"):
+        getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _dev_f64(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError(f"{name} must be a CUDA float64 tensor")
+    return t
+
+
+def _rowmajor(A):
+    if A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError("A must be a row-major 2-D tensor (unit column stride)")
+    return A.shape[0], A.shape[1], A.stride(0)
+
+
+class Context:
+    """One library context (device workspace under an HBM budget)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        st = self.lib.lsq_create(ctypes.byref(h), device, hbm_budget_bytes)
+        if st != LSQ_OK:
+            raise LsqError(st, "lsq_create failed (no usable GPU?)")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lsq_destroy(self.h)
+            self.h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, allow=(LSQ_OK,)):
+        if st not in allow:
+            raise LsqError(st, self.lib.lsq_last_error(self.h).decode())
+        return st
+
+    @property
+    def workspace_bytes(self):
+        return self.lib.lsq_workspace_bytes(self.h)
+
+    # -- C ABI calls -------------------------------------------------------
+    def lsq_sketch_indices(self, seed, row0, rows, d, zeta, stream=None, with_rounds=False):
+        import torch
+        dev = torch.device("cuda", self.device)
+        idx = torch.empty((rows, zeta), dtype=torch.int32, device=dev)
+        sgn = torch.empty((rows, zeta), dtype=torch.int8, device=dev)
+        rnd = torch.empty((rows,), dtype=torch.int32, device=dev) if with_rounds else None
+        self._check(self.lib.lsq_sketch_indices(self.h, seed, row0, rows, d, zeta, _ptr(idx), _ptr(sgn), _ptr(rnd),
+                                                _stream(stream)))
+        return (idx, sgn, rnd) if with_rounds else (idx, sgn)
+
+    def lsq_sketch(self, A, b, d, zeta, seed, prec=PREC_FP64, stream=None):
+        import torch
+        _dev_f64(A, "A")
+        m, n, lda = _rowmajor(A)
+        if b is not None:
+            _dev_f64(b, "b")
+        ncol = n + (b is not None)
+        Y = torch.empty((d, ncol), dtype=torch.float64 if prec == PREC_FP64 else torch.float32, device=A.device)
+        self._check(self.lib.lsq_sketch(self.h, _ptr(A), m, n, lda, _ptr(b), d, zeta, seed, prec, _ptr(Y), ncol,
+                                        _stream(stream)))
+        return Y
+
+    def lsq_precond(self, Y, n, has_b=True, prec=PREC_FP64, want_R=True, stream=None):
+        import torch
+        d, ldy = Y.shape[0], Y.stride(0)
+        dev = Y.device
+        R = torch.empty((n, n), dtype=torch.float64, device=dev) if want_R else None
+        M = torch.empty((n, n), dtype=torch.float64, device=dev)
+        x0 = torch.empty((n,), dtype=torch.float64, device=dev) if has_b else None
+        self._check(self.lib.lsq_precond(self.h, _ptr(Y), d, n, ldy, int(has_b), prec, _ptr(R), _ptr(M), _ptr(x0),
+                                         _stream(stream)))
+        return R, M, x0
+
+    def lsq_lsqr(self, A, b, M, x0, tol, maxit, flags=0, stream=None):
+        import torch
+        _dev_f64(A, "A")
+        m, n, lda = _rowmajor(A)
+        x = torch.empty((n,), dtype=torch.float64, device=A.device)
+        info = Info()
+        st = self.lib.lsq_lsqr(self.h, _ptr(A), m, n, lda, _ptr(b), _ptr(M), _ptr(x0), tol, maxit, flags, _ptr(x),
+                               ctypes.byref(info), _stream(stream))
+        self._check(st, allow=(LSQ_OK, LSQ_ERR_NOCONV))
+        return x, info.as_dict()
+
+    def lsq_check(self, A, b, x, M=None, stream=None):
+        _dev_f64(A, "A")
+        m, n, lda = _rowmajor(A)
+        info = Info()
+        self._check(self.lib.lsq_check(self.h, _ptr(A), m, n, lda, _ptr(b), _ptr(x), _ptr(M), ctypes.byref(info),
+                                       _stream(stream)))
+        return info.as_dict()
+
+    def lsq_solve(self, A, b, d, zeta=8, seed=0, tol=1e-12, maxit=0, prec=PREC_FP64, flags=0, x=None, stream=None,
+                  allow_noconv=False):
+        """Algorithm 1 end to end.  A, b: CUDA float64 tensors (device
+        problem) or numpy float64 arrays (host problem: copies inside the
+        call).  Returns (x, info dict)."""
+        import torch
+        if isinstance(A, np.ndarray):
+            if A.dtype != np.float64 or A.ndim != 2 or A.strides[1] != 8:
+                raise ValueError("host A must be a row-major float64 array")
+            b = np.ascontiguousarray(b, dtype=np.float64)
+            m, n = A.shape
+            lda = A.strides[0] // 8
+            mem = MEM_HOST
+            if x is None:
+                x = np.empty(n, dtype=np.float64)
+            strm = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        else:
+            _dev_f64(A, "A")
+            _dev_f64(b, "b")
+            m, n, lda = _rowmajor(A)
+            mem = MEM_DEVICE
+            if x is None:
+                x = torch.empty((n,), dtype=torch.float64, device=A.device)
+            strm = _stream(stream)
+        pr = Problem(_ptr(A), _ptr(b), m, n, lda, mem, 0)
+        op = Opts(d, zeta, prec, seed, tol, maxit, flags, 0)
+        info = Info()
+        st = self.lib.lsq_solve(self.h, ctypes.byref(pr), ctypes.byref(op), _ptr(x), ctypes.byref(info), strm)
+        self._check(st, allow=(LSQ_OK, LSQ_ERR_NOCONV) if allow_noconv else (LSQ_OK,))
+        return x, info.as_dict()
+
+
+_default = {}
+
+
+def context(device: int = 0) -> Context:
+    """Process-wide default context for `device`."""
+    if device not in _default:
+        _default[device] = Context(device)
+    return _default[device]
+
+
+def lsq_solve(A, b, d, **kw):
+    return context().lsq_solve(A, b, d, **kw)

@@ -1,0 +1,536 @@
+// api.cu -- the C ABI declared in include/lsq.h: context, workspace under an
+// HBM budget, argument checking, status mapping and the Algorithm 1 chain
+// sketch -> preconditioner -> LSQR -> accuracy pass on one stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "kernels.h"
+
+using namespace lsq;
+
+struct lsq_ctx {
+  int device = 0;
+  int sms = 0;
+  size_t budget = 0;
+  std::string err;
+  // grown-on-demand workspace (one allocation, carved per call)
+  char* ws = nullptr;
+  size_t ws_size = 0;
+  // small persistent device words
+  uint32_t* d_status = nullptr;
+  int32_t* d_max_rounds = nullptr;
+  GridBarrier* d_bar = nullptr;
+  double* d_out = nullptr;
+  // pinned host mirror of the small words
+  void* h_small = nullptr;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr size_t kSmallBytes = 4096;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+lsq_status fail(lsq_ctx* c, lsq_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+lsq_status cuda_fail(lsq_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, e == cudaErrorMemoryAllocation ? LSQ_ERR_OOM : LSQ_ERR_CUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define CK(call)                                        \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+    off += align_up(count * sizeof(T));
+    return p;
+  }
+};
+
+lsq_status ensure_ws(lsq_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->ws_size) return LSQ_OK;
+  if (bytes > ctx->budget)
+    return fail(ctx, LSQ_ERR_BUDGET,
+                "workspace of " + std::to_string(bytes) + " bytes exceeds the HBM budget of " +
+                    std::to_string(ctx->budget));
+  if (ctx->ws) {
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_size = 0;
+  }
+  cudaError_t e = cudaMalloc(&ctx->ws, bytes);
+  if (e != cudaSuccess) {
+    ctx->ws = nullptr;
+    cudaGetLastError();
+    return fail(ctx, LSQ_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  ctx->ws_size = bytes;
+  return LSQ_OK;
+}
+
+lsq_status status_from_bits(lsq_ctx* ctx, uint32_t bits) {
+  if (bits & DS_TIMEOUT) return fail(ctx, LSQ_ERR_TIMEOUT, "a device-side grid barrier timed out");
+  if (bits & DS_NONFINITE) return fail(ctx, LSQ_ERR_NONFINITE, "A or b contains NaN or Inf");
+  if (bits & DS_SKETCH) return fail(ctx, LSQ_ERR_SKETCH, "rejection sampling exceeded its round cap");
+  if (bits & DS_RANK) return fail(ctx, LSQ_ERR_RANK, "R has a negligible diagonal entry (rank-deficient sketch)");
+  if (bits & DS_NOCONV) return fail(ctx, LSQ_ERR_NOCONV, "LSQR reached maxit before the stopping test held");
+  return LSQ_OK;
+}
+
+lsq_status check_ctx(lsq_ctx* ctx) {
+  if (!ctx) return LSQ_ERR_ARG;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  return LSQ_OK;
+}
+
+lsq_status check_sketch_args(lsq_ctx* ctx, int64_t d, int32_t zeta) {
+  if (zeta < 1 || zeta > kMaxZeta) return fail(ctx, LSQ_ERR_ARG, "zeta must be in [1, 64]");
+  if (d < 1 || d > 2147483647LL) return fail(ctx, LSQ_ERR_ARG, "d must be in [1, 2^31-1]");
+  if ((int64_t)zeta > d) return fail(ctx, LSQ_ERR_ARG, "zeta must not exceed d");
+  return LSQ_OK;
+}
+
+// reset the small device words on the stream
+lsq_status reset_small(lsq_ctx* ctx, cudaStream_t st) {
+  CK(cudaMemsetAsync(ctx->d_status, 0, kSmallBytes, st));
+  return LSQ_OK;
+}
+
+// copy status + max_rounds + out back and synchronise
+lsq_status read_small(lsq_ctx* ctx, cudaStream_t st, uint32_t* bits, int32_t* rounds, double* out) {
+  CK(cudaMemcpyAsync(ctx->h_small, ctx->d_status, kSmallBytes, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const char* h = static_cast<const char*>(ctx->h_small);
+  const size_t off_rounds = (const char*)ctx->d_max_rounds - (const char*)ctx->d_status;
+  const size_t off_out = (const char*)ctx->d_out - (const char*)ctx->d_status;
+  if (bits) std::memcpy(bits, h, sizeof(uint32_t));
+  if (rounds) std::memcpy(rounds, h + off_rounds, sizeof(int32_t));
+  if (out) std::memcpy(out, h + off_out, sizeof(double) * kOutSlots);
+  return LSQ_OK;
+}
+
+bool vec_ok(const double* A, int64_t lda) { return ((uintptr_t)A % 16 == 0) && (lda % 2 == 0); }
+
+int64_t default_maxit(int64_t n, int64_t d, double tol) {
+  const double rate = std::sqrt((double)n / (double)d);
+  if (!(tol > 0.0) || !(rate < 1.0)) return 1000;
+  return (int64_t)(10.0 * std::ceil(std::log(tol) / std::log(rate)));
+}
+
+struct LsqrWork {
+  double *u, *v, *vhat, *w, *wv, *g, *gpart, *part, *Mt;
+};
+
+LsqrWork carve_lsqr(Carver& cv, int64_t m, int n, int npad, int grid) {
+  LsqrWork w;
+  w.u = cv.take<double>((size_t)m);
+  w.v = cv.take<double>(npad);
+  w.vhat = cv.take<double>(npad);
+  w.w = cv.take<double>(npad);
+  w.wv = cv.take<double>(npad);
+  w.g = cv.take<double>(npad);
+  w.gpart = cv.take<double>((size_t)grid * npad);
+  w.part = cv.take<double>((size_t)grid * 4);
+  w.Mt = cv.take<double>((size_t)n * n);
+  return w;
+}
+
+void fill_info(lsq_info* info, const double* out, lsq_status st, int32_t rounds) {
+  if (!info) return;
+  std::memset(info, 0, sizeof(*info));
+  info->status = st;
+  info->iters = (int64_t)out[OUT_ITERS];
+  info->stop = (int32_t)out[OUT_STOP];
+  info->normal_rel_est = out[OUT_NORMAL_REL];
+  info->backward_error_ne = out[OUT_ETA_NE];
+  info->backward_error_pre = out[OUT_ETA_PRE];
+  info->rnorm = out[OUT_RNORM];
+  info->arnorm = out[OUT_ARNORM];
+  info->anorm_fro = out[OUT_FRO];
+  info->xnorm = out[OUT_XNORM];
+  info->bnorm = out[OUT_BNORM];
+  info->sketch_rounds_max = rounds;
+}
+
+// Launch the LSQR / check kernel.
+lsq_status run_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int n, int64_t lda, const double* b, const double* M,
+                    const double* Mt, double* x, double tol, int64_t maxit, int mode, const LsqrWork& w, int grid,
+                    int npad, cudaStream_t st) {
+  LsqrParams p;
+  p.A = A;
+  p.m = m;
+  p.n = n;
+  p.npad = npad;
+  p.lda = lda;
+  p.b = b;
+  p.M = M;
+  p.Mt = Mt;
+  p.x = x;
+  p.u = w.u;
+  p.v = w.v;
+  p.vhat = w.vhat;
+  p.w = w.w;
+  p.wv = w.wv;
+  p.g = w.g;
+  p.gpart = w.gpart;
+  p.part = w.part;
+  p.tol = tol;
+  p.maxit = maxit;
+  p.mode = mode;
+  p.bar = ctx->d_bar;
+  p.status = ctx->d_status;
+  p.out = ctx->d_out;
+  CK(cudaMemsetAsync(ctx->d_bar, 0, sizeof(GridBarrier), st));
+  CK(lsqr_run(p, vec_ok(A, lda), true, grid, st));
+  return LSQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lsq_status lsq_create(lsq_ctx** out, int device, size_t hbm_budget_bytes) {
+  if (!out) return LSQ_ERR_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return LSQ_ERR_CUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return LSQ_ERR_CUDA;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return LSQ_ERR_CUDA;
+  if (!prop.cooperativeLaunch) return LSQ_ERR_CUDA;
+  lsq_ctx* ctx = new lsq_ctx();
+  ctx->device = device;
+  ctx->sms = prop.multiProcessorCount;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    delete ctx;
+    return LSQ_ERR_CUDA;
+  }
+  ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)fr);
+  char* small = nullptr;
+  if (cudaMalloc(&small, kSmallBytes) != cudaSuccess) {
+    delete ctx;
+    return LSQ_ERR_OOM;
+  }
+  ctx->d_status = reinterpret_cast<uint32_t*>(small);
+  ctx->d_max_rounds = reinterpret_cast<int32_t*>(small + 64);
+  ctx->d_bar = reinterpret_cast<GridBarrier*>(small + 128);
+  ctx->d_out = reinterpret_cast<double*>(small + 256);
+  if (cudaMallocHost(&ctx->h_small, kSmallBytes) != cudaSuccess) {
+    cudaFree(small);
+    delete ctx;
+    return LSQ_ERR_OOM;
+  }
+  cudaMemset(small, 0, kSmallBytes);
+  *out = ctx;
+  return LSQ_OK;
+}
+
+lsq_status lsq_destroy(lsq_ctx* ctx) {
+  if (!ctx) return LSQ_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->h_small) cudaFreeHost(ctx->h_small);
+  delete ctx;
+  return LSQ_OK;
+}
+
+const char* lsq_last_error(const lsq_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+const char* lsq_status_string(lsq_status s) {
+  switch (s) {
+    case LSQ_OK: return "LSQ_OK";
+    case LSQ_PENDING: return "LSQ_PENDING";
+    case LSQ_ERR_ARG: return "LSQ_ERR_ARG";
+    case LSQ_ERR_CUDA: return "LSQ_ERR_CUDA";
+    case LSQ_ERR_OOM: return "LSQ_ERR_OOM";
+    case LSQ_ERR_BUDGET: return "LSQ_ERR_BUDGET";
+    case LSQ_ERR_SKETCH: return "LSQ_ERR_SKETCH";
+    case LSQ_ERR_RANK: return "LSQ_ERR_RANK";
+    case LSQ_ERR_NOCONV: return "LSQ_ERR_NOCONV";
+    case LSQ_ERR_TIMEOUT: return "LSQ_ERR_TIMEOUT";
+    case LSQ_ERR_NONFINITE: return "LSQ_ERR_NONFINITE";
+    case LSQ_ERR_UNSUPPORTED: return "LSQ_ERR_UNSUPPORTED";
+    default: return "LSQ_UNKNOWN";
+  }
+}
+
+size_t lsq_workspace_bytes(const lsq_ctx* ctx) { return ctx ? ctx->ws_size + kSmallBytes : 0; }
+
+lsq_status lsq_sketch_indices(lsq_ctx* ctx, uint64_t seed, int64_t row0, int64_t rows, int64_t d, int32_t zeta,
+                              int32_t* idx, int8_t* sign, int32_t* rounds, void* stream) {
+  lsq_status s;
+  if ((s = check_ctx(ctx)) != LSQ_OK) return s;
+  if ((s = check_sketch_args(ctx, d, zeta)) != LSQ_OK) return s;
+  if (rows < 0 || row0 < 0) return fail(ctx, LSQ_ERR_ARG, "rows and row0 must be >= 0");
+  if (rows > 0 && (!idx || !sign)) return fail(ctx, LSQ_ERR_ARG, "idx and sign must not be null");
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((s = reset_small(ctx, st)) != LSQ_OK) return s;
+  CK(sketch_indices(seed, row0, rows, d, zeta, idx, sign, rounds, ctx->d_status, ctx->d_max_rounds, ctx->sms, st));
+  uint32_t bits = 0;
+  if ((s = read_small(ctx, st, &bits, nullptr, nullptr)) != LSQ_OK) return s;
+  return status_from_bits(ctx, bits);
+}
+
+lsq_status lsq_sketch(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d,
+                      int32_t zeta, uint64_t seed, int32_t prec, void* Y, int64_t ldy, void* stream) {
+  lsq_status s;
+  if ((s = check_ctx(ctx)) != LSQ_OK) return s;
+  if ((s = check_sketch_args(ctx, d, zeta)) != LSQ_OK) return s;
+  if (m < 0 || n < 1 || n > 2147483647LL || lda < n) return fail(ctx, LSQ_ERR_ARG, "need m >= 0, n >= 1, lda >= n");
+  if (ldy < n + (b ? 1 : 0)) return fail(ctx, LSQ_ERR_ARG, "ldy must be >= n + (b != NULL)");
+  if (!Y || (m > 0 && !A)) return fail(ctx, LSQ_ERR_ARG, "null pointer");
+  if (prec != LSQ_PREC_FP64 && prec != LSQ_PREC_MIXED) return fail(ctx, LSQ_ERR_ARG, "unknown precision");
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((s = reset_small(ctx, st)) != LSQ_OK) return s;
+  const size_t esz = prec == LSQ_PREC_FP64 ? 8 : 4;
+  CK(cudaMemsetAsync(Y, 0, (size_t)d * ldy * esz, st));
+  if (prec == LSQ_PREC_FP64)
+    CK(sketch_apply<double>(A, m, n, lda, b, d, zeta, seed, 0, (double*)Y, ldy, ctx->d_status, ctx->d_max_rounds,
+                            ctx->sms, st));
+  else
+    CK(sketch_apply<float>(A, m, n, lda, b, d, zeta, seed, 0, (float*)Y, ldy, ctx->d_status, ctx->d_max_rounds,
+                           ctx->sms, st));
+  uint32_t bits = 0;
+  if ((s = read_small(ctx, st, &bits, nullptr, nullptr)) != LSQ_OK) return s;
+  return status_from_bits(ctx, bits);
+}
+
+lsq_status lsq_precond(lsq_ctx* ctx, const void* Y, int64_t d, int64_t n, int64_t ldy, int32_t has_b, int32_t prec,
+                       double* R, double* M, double* x0, void* stream) {
+  lsq_status s;
+  if ((s = check_ctx(ctx)) != LSQ_OK) return s;
+  const int64_t ncol = n + (has_b ? 1 : 0);
+  if (n < 1 || n > 65536 || d < ncol || d > 2147483647LL || ldy < ncol)
+    return fail(ctx, LSQ_ERR_ARG, "need 1 <= n <= 65536, d >= n + has_b, ldy >= n + has_b");
+  if (!Y || !M) return fail(ctx, LSQ_ERR_ARG, "Y and M must not be null");
+  if (x0 && !has_b) return fail(ctx, LSQ_ERR_ARG, "x0 needs the sketched b column (has_b)");
+  if (prec != LSQ_PREC_FP64 && prec != LSQ_PREC_MIXED) return fail(ctx, LSQ_ERR_ARG, "unknown precision");
+  cudaStream_t st = (cudaStream_t)stream;
+  Carver probe{nullptr};
+  probe.take<double>((size_t)ncol * d);
+  probe.take<double>(n);
+  probe.take<double>((size_t)n * n);
+  probe.take<double>((size_t)n * n);
+  if ((s = ensure_ws(ctx, probe.off)) != LSQ_OK) return s;
+  Carver cv{ctx->ws};
+  PrecondBuffers buf;
+  buf.W = cv.take<double>((size_t)ncol * d);
+  buf.rdiag = cv.take<double>(n);
+  buf.R = cv.take<double>((size_t)n * n);
+  buf.Mt = cv.take<double>((size_t)n * n);
+  buf.bar = ctx->d_bar;
+  buf.status = ctx->d_status;
+  if ((s = reset_small(ctx, st)) != LSQ_OK) return s;
+  if (prec == LSQ_PREC_FP64)
+    CK(precond<double>((const double*)Y, d, n, ldy, has_b, R, M, x0, buf, ctx->sms, st));
+  else
+    CK(precond<float>((const float*)Y, d, n, ldy, has_b, R, M, x0, buf, ctx->sms, st));
+  uint32_t bits = 0;
+  if ((s = read_small(ctx, st, &bits, nullptr, nullptr)) != LSQ_OK) return s;
+  return status_from_bits(ctx, bits);
+}
+
+lsq_status lsq_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
+                    const double* M, const double* x0, double tol, int64_t maxit, int32_t flags, double* x,
+                    lsq_info* info, void* stream) {
+  lsq_status s;
+  if ((s = check_ctx(ctx)) != LSQ_OK) return s;
+  if (m < 1 || n < 1 || lda < n) return fail(ctx, LSQ_ERR_ARG, "need m >= 1, n >= 1, lda >= n");
+  if (!A || !b || !M || !x0 || !x) return fail(ctx, LSQ_ERR_ARG, "null pointer");
+  if (n > 512) return fail(ctx, LSQ_ERR_UNSUPPORTED, "LSQR kernel built for n <= 512");
+  (void)flags;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int ni = (int)n, npad = (int)((n + 31) / 32 * 32);
+  const int grid = lsqr_grid(ni, vec_ok(A, lda), true, ctx->sms);
+  Carver probe{nullptr};
+  carve_lsqr(probe, m, ni, npad, grid);
+  if ((s = ensure_ws(ctx, probe.off)) != LSQ_OK) return s;
+  Carver cv{ctx->ws};
+  LsqrWork w = carve_lsqr(cv, m, ni, npad, grid);
+  if ((s = reset_small(ctx, st)) != LSQ_OK) return s;
+  CK(transpose_square(M, ni, w.Mt, st));
+  if (x != x0) CK(cudaMemcpyAsync(x, x0, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  if (maxit <= 0) maxit = 1000;
+  if ((s = run_lsqr(ctx, A, m, ni, lda, b, M, w.Mt, x, tol, maxit, 2, w, grid, npad, st)) != LSQ_OK) return s;
+  uint32_t bits = 0;
+  double out[kOutSlots];
+  if ((s = read_small(ctx, st, &bits, nullptr, out)) != LSQ_OK) return s;
+  s = status_from_bits(ctx, bits);
+  fill_info(info, out, s, 0);
+  return s;
+}
+
+lsq_status lsq_check(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
+                     const double* x, const double* M, lsq_info* info, void* stream) {
+  lsq_status s;
+  if ((s = check_ctx(ctx)) != LSQ_OK) return s;
+  if (m < 1 || n < 1 || lda < n) return fail(ctx, LSQ_ERR_ARG, "need m >= 1, n >= 1, lda >= n");
+  if (!A || !b || !x) return fail(ctx, LSQ_ERR_ARG, "null pointer");
+  if (n > 512) return fail(ctx, LSQ_ERR_UNSUPPORTED, "check kernel built for n <= 512");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int ni = (int)n, npad = (int)((n + 31) / 32 * 32);
+  const int grid = lsqr_grid(ni, vec_ok(A, lda), true, ctx->sms);
+  Carver probe{nullptr};
+  carve_lsqr(probe, m, ni, npad, grid);
+  if ((s = ensure_ws(ctx, probe.off)) != LSQ_OK) return s;
+  Carver cv{ctx->ws};
+  LsqrWork w = carve_lsqr(cv, m, ni, npad, grid);
+  if ((s = reset_small(ctx, st)) != LSQ_OK) return s;
+  if (M) CK(transpose_square(M, ni, w.Mt, st));
+  if ((s = run_lsqr(ctx, A, m, ni, lda, b, M, M ? w.Mt : nullptr, const_cast<double*>(x), 0.0, 0, 1, w, grid, npad,
+                    st)) != LSQ_OK)
+    return s;
+  uint32_t bits = 0;
+  double out[kOutSlots];
+  if ((s = read_small(ctx, st, &bits, nullptr, out)) != LSQ_OK) return s;
+  s = status_from_bits(ctx, bits);
+  fill_info(info, out, s, 0);
+  return s;
+}
+
+lsq_status lsq_solve(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts* o, double* x, lsq_info* info,
+                     void* stream) {
+  lsq_status s;
+  if ((s = check_ctx(ctx)) != LSQ_OK) return s;
+  if (!pr || !o || !x) return fail(ctx, LSQ_ERR_ARG, "null problem, options or x");
+  const int64_t m = pr->m, n = pr->n, lda = pr->lda, d = o->d;
+  if (m < 1 || n < 1 || lda < n || !pr->A || !pr->b) return fail(ctx, LSQ_ERR_ARG, "need m, n >= 1, lda >= n, A, b");
+  if ((s = check_sketch_args(ctx, d, o->zeta)) != LSQ_OK) return s;
+  if (d < n + 1) return fail(ctx, LSQ_ERR_ARG, "need d >= n + 1");
+  if (o->prec != LSQ_PREC_FP64 && o->prec != LSQ_PREC_MIXED) return fail(ctx, LSQ_ERR_ARG, "unknown precision");
+  if (pr->mem != LSQ_MEM_DEVICE && pr->mem != LSQ_MEM_HOST) return fail(ctx, LSQ_ERR_ARG, "unknown memory kind");
+  if (n > 512) return fail(ctx, LSQ_ERR_UNSUPPORTED, "LSQR kernel built for n <= 512");
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool host = pr->mem == LSQ_MEM_HOST;
+  const bool timing = (o->flags & LSQ_FLAG_TIMING) != 0;
+  const int ni = (int)n, npad = (int)((n + 31) / 32 * 32);
+  const int64_t ncol = n + 1, ldy = ncol;
+  const size_t yes = o->prec == LSQ_PREC_FP64 ? 8 : 4;
+  const int64_t lda_dev = host ? n : lda;
+  const bool vec = host ? (n % 2 == 0) : vec_ok(pr->A, lda);
+  const int grid = lsqr_grid(ni, vec, true, ctx->sms);
+  const int64_t maxit = o->maxit > 0 ? o->maxit : default_maxit(n, d, o->tol);
+
+  auto carve = [&](Carver& cv, const double** A, const double** b, double** xd, void** Y, PrecondBuffers* pb,
+                   double** R, double** M, LsqrWork* lw) {
+    if (host) {
+      *A = cv.take<double>((size_t)m * n);
+      *b = cv.take<double>((size_t)m);
+      *xd = cv.take<double>(npad);
+    } else {
+      *A = pr->A;
+      *b = pr->b;
+      *xd = x;
+    }
+    *Y = cv.take<char>((size_t)d * ldy * yes);
+    pb->W = cv.take<double>((size_t)ncol * d);
+    pb->rdiag = cv.take<double>(npad);
+    pb->R = nullptr;
+    pb->Mt = nullptr;
+    *R = cv.take<double>((size_t)n * n);
+    *M = cv.take<double>((size_t)n * n);
+    *lw = carve_lsqr(cv, m, ni, npad, grid);
+    pb->Mt = lw->Mt;
+  };
+  {
+    Carver probe{nullptr};
+    const double *A0, *b0;
+    double *x0, *R0, *M0;
+    void* Y0;
+    PrecondBuffers pb0;
+    LsqrWork lw0;
+    carve(probe, &A0, &b0, &x0, &Y0, &pb0, &R0, &M0, &lw0);
+    if ((s = ensure_ws(ctx, probe.off)) != LSQ_OK) return s;
+  }
+  Carver cv{ctx->ws};
+  const double *A, *b;
+  double *xd, *R, *M;
+  void* Y;
+  PrecondBuffers pb;
+  LsqrWork lw;
+  carve(cv, &A, &b, &xd, &Y, &pb, &R, &M, &lw);
+  pb.bar = ctx->d_bar;
+  pb.status = ctx->d_status;
+
+  cudaEvent_t ev[6] = {};
+  if (timing)
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+  if (timing) CK(cudaEventRecord(ev[0], st));
+  if (host) {
+    CK(cudaMemcpy2DAsync((void*)A, sizeof(double) * n, pr->A, sizeof(double) * lda, sizeof(double) * n, m,
+                         cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync((void*)b, pr->b, sizeof(double) * m, cudaMemcpyHostToDevice, st));
+  }
+  if (timing) CK(cudaEventRecord(ev[1], st));
+  if ((s = reset_small(ctx, st)) != LSQ_OK) return s;
+  CK(cudaMemsetAsync(Y, 0, (size_t)d * ldy * yes, st));
+  if (o->prec == LSQ_PREC_FP64)
+    CK(sketch_apply<double>(A, m, n, lda_dev, b, d, o->zeta, o->seed, 0, (double*)Y, ldy, ctx->d_status,
+                            ctx->d_max_rounds, ctx->sms, st));
+  else
+    CK(sketch_apply<float>(A, m, n, lda_dev, b, d, o->zeta, o->seed, 0, (float*)Y, ldy, ctx->d_status,
+                           ctx->d_max_rounds, ctx->sms, st));
+  if (timing) CK(cudaEventRecord(ev[2], st));
+  if (o->prec == LSQ_PREC_FP64)
+    CK(precond<double>((const double*)Y, d, n, ldy, 1, R, M, xd, pb, ctx->sms, st));
+  else
+    CK(precond<float>((const float*)Y, d, n, ldy, 1, R, M, xd, pb, ctx->sms, st));
+  if (timing) CK(cudaEventRecord(ev[3], st));
+  // status after the preconditioner (sketch failure, rank) before iterating
+  uint32_t bits = 0;
+  int32_t rounds = 0;
+  double out[kOutSlots] = {0};
+  if ((s = read_small(ctx, st, &bits, &rounds, nullptr)) != LSQ_OK) return s;
+  if (bits) {
+    s = status_from_bits(ctx, bits);
+    if (info) {
+      fill_info(info, out, s, rounds);
+    }
+    return s;
+  }
+  const int mode = (o->flags & LSQ_FLAG_NO_CHECK) ? 2 : 0;
+  if ((s = run_lsqr(ctx, A, m, ni, lda_dev, b, M, lw.Mt, xd, o->tol, maxit, mode, lw, grid, npad, st)) != LSQ_OK)
+    return s;
+  if (timing) CK(cudaEventRecord(ev[4], st));
+  if (host) CK(cudaMemcpyAsync(x, xd, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+  if (timing) CK(cudaEventRecord(ev[5], st));
+  if ((s = read_small(ctx, st, &bits, nullptr, out)) != LSQ_OK) return s;
+  s = status_from_bits(ctx, bits);
+  fill_info(info, out, s, rounds);
+  if (info && timing) {
+    float t;
+    cudaEventElapsedTime(&t, ev[0], ev[1]);
+    info->t_h2d_ms = t;
+    cudaEventElapsedTime(&t, ev[1], ev[2]);
+    info->t_sketch_ms = t;
+    cudaEventElapsedTime(&t, ev[2], ev[3]);
+    info->t_precond_ms = t;
+    cudaEventElapsedTime(&t, ev[3], ev[4]);
+    info->t_lsqr_ms = t;
+    cudaEventElapsedTime(&t, ev[4], ev[5]);
+    info->t_d2h_ms = t;
+  }
+  if (timing)
+    for (auto& e : ev) cudaEventDestroy(e);
+  return s;
+}
+
+}  // extern "C"

@@ -1,0 +1,158 @@
+// common.cuh -- device helpers shared by the library's kernels: the Philox
+// counter-based generator, bounded grid barriers, warp reductions and the
+// status word every kernel reports into.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lsq.h"
+
+namespace lsq {
+
+// Device status bits (OR-ed into a device word, mapped to lsq_status on the host).
+enum : uint32_t {
+  DS_SKETCH = 1u,     // rejection sampling exceeded its round cap
+  DS_NONFINITE = 2u,  // NaN/Inf seen in A or b
+  DS_TIMEOUT = 4u,    // a grid barrier wait gave up
+  DS_RANK = 8u,       // zero/negligible diagonal of R
+  DS_NOCONV = 16u,    // LSQR reached maxit
+};
+
+constexpr int kMaxZeta = 64;
+constexpr int kMaxRounds = 10000;
+// A grid barrier gives up after this many nanoseconds of waiting.
+constexpr unsigned long long kBarrierTimeoutNs = 20ull * 1000ull * 1000ull * 1000ull;
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 64x64->128 multiplies with key advance by the two Weyl constants.
+// ---------------------------------------------------------------------------
+struct U64x4 {
+  uint64_t w[4];
+};
+
+__device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3, uint64_t k0,
+                                               uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+    const uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+    const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += W0;
+    k1 += W1;
+  }
+  U64x4 o;
+  o.w[0] = c0;
+  o.w[1] = c1;
+  o.w[2] = c2;
+  o.w[3] = c3;
+  return o;
+}
+
+// floor(word * d / 2^64): maps a uniform 64-bit word to [0, d).
+__device__ __forceinline__ int32_t word_to_index(uint64_t word, uint64_t d) { return (int32_t)__umul64hi(word, d); }
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// Grid barrier for cooperative (co-resident) launches.  State: {count, gen,
+// abort}, zeroed by the host before the launch.  Every wait is bounded by
+// kBarrierTimeoutNs; on timeout the block raises DS_TIMEOUT and the abort flag,
+// and every block leaves at its next barrier.  Returns false when the caller
+// must exit.
+// ---------------------------------------------------------------------------
+struct GridBarrier {
+  unsigned int count;
+  unsigned int gen;
+  unsigned int abort;
+  unsigned int pad;
+};
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, uint32_t* status) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (ld_acquire_u32(&bar->abort)) {
+      ok = 0;
+    } else {
+      const unsigned int g = ld_acquire_u32(&bar->gen);
+      __threadfence();
+      const unsigned int arrived = atomicAdd(&bar->count, 1u);
+      if (arrived == gridDim.x - 1) {
+        bar->count = 0;
+        __threadfence();
+        st_release_u32(&bar->gen, g + 1);
+      } else {
+        const unsigned long long t0 = globaltimer_ns();
+        unsigned int spins = 0;
+        while (ld_acquire_u32(&bar->gen) == g) {
+          if (ld_acquire_u32(&bar->abort)) {
+            ok = 0;
+            break;
+          }
+          if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+            atomicOr(status, DS_TIMEOUT);
+            atomicExch(&bar->abort, 1u);
+            ok = 0;
+            break;
+          }
+          __nanosleep(32);
+        }
+        __threadfence();
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_allreduce_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_allreduce_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum in a fixed order (deterministic for a fixed block size).
+// `scratch` holds at least 32 doubles.  Result valid in every thread.
+__device__ __forceinline__ double block_sum(double v, double* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_allreduce_sum(v);
+  __syncthreads();
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < nw; ++i) s += scratch[i];
+  __syncthreads();
+  return s;
+}
+
+}  // namespace lsq

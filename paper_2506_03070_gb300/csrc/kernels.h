@@ -1,0 +1,78 @@
+// kernels.h -- host-side launchers of the library's kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace lsq {
+
+// Sketch (sketch.cu)
+cudaError_t sketch_indices(uint64_t seed, int64_t row0, int64_t rows, int64_t d, int zeta, int32_t* idx, int8_t* sgn,
+                           int32_t* rounds, uint32_t* status, int32_t* max_rounds, int sms, cudaStream_t st);
+template <typename TY>
+cudaError_t sketch_apply(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d, int zeta,
+                         uint64_t seed, int64_t row0, TY* Y, int64_t ldy, uint32_t* status, int32_t* max_rounds,
+                         int sms, cudaStream_t st);
+
+// Preconditioner (qr.cu).  W: FP64 column-major working copy, ncol x d.
+struct PrecondBuffers {
+  double* W;       // ncol * d
+  double* rdiag;   // n
+  double* R;       // n * n, row-major R when the caller passes none
+  double* Mt;      // n * n, row-major transpose of M (working buffer)
+  GridBarrier* bar;
+  uint32_t* status;
+};
+// dst = src^T for a row-major n x n matrix.
+cudaError_t transpose_square(const double* src, int n, double* dst, cudaStream_t st);
+template <typename TY>
+cudaError_t precond(const TY* Y, int64_t d, int64_t n, int64_t ldy, int has_b, double* R, double* M, double* x0,
+                    const PrecondBuffers& buf, int sms, cudaStream_t st);
+
+// LSQR and the accuracy pass (lsqr.cu).
+struct LsqrParams {
+  const double* A;
+  int64_t m;
+  int n;
+  int npad;
+  int64_t lda;
+  const double* b;
+  const double* M;   // n x n row-major (upper triangular), may be null in check mode
+  const double* Mt;  // transpose of M, row-major
+  double* x;         // in: start, out: solution
+  double* u;         // m
+  double* v;         // n
+  double* vhat;      // n
+  double* w;         // n
+  double* wv;        // n
+  double* g;         // n
+  double* gpart;     // grid * npad
+  double* part;      // grid * 4
+  double tol;
+  int64_t maxit;
+  int mode;          // 0 = LSQR then check, 1 = check only, 2 = LSQR only
+  GridBarrier* bar;
+  uint32_t* status;
+  double* out;       // kOutSlots doubles of results
+};
+enum {
+  OUT_ITERS = 0,
+  OUT_STOP,
+  OUT_NORMAL_REL,
+  OUT_RNORM,
+  OUT_ARNORM,
+  OUT_FRO,
+  OUT_XNORM,
+  OUT_BNORM,
+  OUT_ETA_NE,
+  OUT_ETA_PRE,
+  OUT_MARNORM,
+  OUT_ANORM_EST,
+  kOutSlots = 16
+};
+// Grid size the LSQR kernel will use for n (co-resident blocks).
+int lsqr_grid(int n, bool vec, bool native, int sms);
+cudaError_t lsqr_run(const LsqrParams& p, bool vec, bool native, int grid, cudaStream_t st);
+
+}  // namespace lsq

@@ -1,0 +1,244 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Sketch indices and signs: bit-exact.  Sketch Y, R, M, x: FP64 tolerances
+derived from the summation lengths and condition numbers (each test states
+its bound).  Solutions: Karlson-Waldén backward error <= 1e-10 and the
+residual-norm distance ||A (x_gpu - x_oracle)|| / ||b|| <= 1e-10."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2506_03070_gb300 import build
+    build.build()
+    import paper_2506_03070_gb300 as P
+    return P.Context(0)
+
+
+def _problem(m, n, cond, seed, resid=1e-6):
+    rng = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = (U * np.geomspace(1, 1 / cond, n)) @ V.T
+    x = rng.standard_normal(n)
+    g = rng.standard_normal(m)
+    g -= U @ (U.T @ g)
+    g -= U @ (U.T @ g)
+    b = A @ x + resid * g / np.linalg.norm(g)
+    return A, b, x
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+# ---------------------------------------------------------------- sketch ---
+@pytest.mark.parametrize("d,zeta,row0,rows", [(800, 8, 0, 20011), (2000, 8, 123456789, 5000), (9, 8, 0, 3001),
+                                              (8, 8, 17, 1000), (64, 64, 0, 777), (100, 1, 5, 999),
+                                              (40, 16, 2**40, 1234), (3000, 33, 7, 2049)])
+def test_sketch_indices_bit_exact(ctx, orc, d, zeta, row0, rows):
+    idx, sgn, rnd = ctx.lsq_sketch_indices(42, row0, rows, d, zeta, with_rounds=True)
+    oi, os_, orr = orc.sketch_indices(42, row0, rows, d, zeta, with_rounds=True)
+    assert np.array_equal(idx.cpu().numpy(), oi)
+    assert np.array_equal(sgn.cpu().numpy(), os_)
+    assert np.array_equal(rnd.cpu().numpy(), orr)
+
+
+@pytest.mark.parametrize("m,n,d,zeta,has_b", [(20000, 200, 800, 8, True), (3001, 37, 120, 8, True),
+                                              (513, 1, 16, 3, False), (1000, 129, 400, 16, True),
+                                              (257, 64, 300, 64, True)])
+def test_sketch_apply_fp64(ctx, orc, m, n, d, zeta, has_b):
+    rng = np.random.default_rng(m + n)
+    A = rng.standard_normal((m, n))
+    b = rng.standard_normal(m) if has_b else None
+    Y = ctx.lsq_sketch(_dev(A), _dev(b) if has_b else None, d, zeta, 7).cpu().numpy()
+    Yo = orc.sketch_apply(A, b, d, zeta, 7)
+    # each entry sums ~m*zeta/d terms of size ~1/sqrt(zeta) in a different order:
+    # |error| <= (terms) * eps * max partial sum; bound it by 64 * eps * sum|terms|
+    k = m * zeta / d
+    tol = 64 * 2.2e-16 * k / np.sqrt(zeta) * 4
+    assert np.max(np.abs(Y - Yo)) <= tol, np.max(np.abs(Y - Yo))
+
+
+def test_sketch_apply_mixed_fp32(ctx, orc):
+    A, b, _ = _problem(20000, 200, 1e8, 3)
+    Y = ctx.lsq_sketch(_dev(A), _dev(b), 800, 8, 9, prec=1).cpu().numpy().astype(np.float64)
+    Yo = orc.sketch_apply(A, b, 800, 8, 9)
+    # FP32 accumulation of ~200 terms: relative error ~ 200 * 6e-8 of the entry scale
+    scale = np.abs(Yo).max()
+    assert np.max(np.abs(Y - Yo)) <= 2e-5 * scale
+
+
+def test_sketch_apply_row_stride(ctx, orc):
+    rng = np.random.default_rng(1)
+    Afull = rng.standard_normal((1000, 41))
+    A = Afull[:, :37]
+    b = rng.standard_normal(1000)
+    At = _dev(Afull)[:, :37]
+    Y = ctx.lsq_sketch(At, _dev(b), 100, 8, 5).cpu().numpy()
+    Yo = orc.sketch_apply(A, b, 100, 8, 5)
+    assert np.max(np.abs(Y - Yo)) <= 1e-13
+
+
+def test_sketch_rejects_bad_arguments(ctx):
+    import paper_2506_03070_gb300 as P
+    A = torch.zeros((10, 4), dtype=torch.float64, device="cuda")
+    with pytest.raises(P.LsqError) as e:
+        ctx.lsq_sketch(A, None, 4, 8, 1)
+    assert e.value.status == -1
+    with pytest.raises(P.LsqError):
+        ctx.lsq_sketch(A, None, 10, 65, 1)
+
+
+def test_sketch_detects_nonfinite(ctx):
+    import paper_2506_03070_gb300 as P
+    A = torch.ones((300, 5), dtype=torch.float64, device="cuda")
+    A[123, 2] = float("nan")
+    with pytest.raises(P.LsqError) as e:
+        ctx.lsq_sketch(A, None, 20, 8, 1)
+    assert e.value.status == -9
+
+
+# ---------------------------------------------------------- precondition ---
+@pytest.mark.parametrize("m,n,d,cond", [(20000, 200, 800, 1e8), (3000, 31, 124, 1e4), (500, 1, 8, 1.0),
+                                        (4000, 64, 65, 1e6)])
+def test_precond_matches_oracle(ctx, orc, m, n, d, cond):
+    A, b, _ = _problem(m, n, cond, n)
+    Yo = orc.sketch_apply(A, b, d, 8, 11)
+    R, M, x0 = ctx.lsq_precond(_dev(Yo), n, has_b=True)
+    R, M, x0 = R.cpu().numpy(), M.cpu().numpy(), x0.cpu().numpy()
+    Ro, _, _ = orc.householder_qr(Yo)
+    Ro = Ro[:n, :n]
+    # same reflector sign convention -> same signs; backward-stable QR of the
+    # same Y: |R - Ro| <~ d * eps * cond * ||Y||
+    nrm = np.linalg.norm(Yo)
+    assert np.linalg.norm(R - Ro) <= 50 * d * 2.2e-16 * cond * nrm
+    assert np.linalg.norm(R.T @ R - Yo[:, :n].T @ Yo[:, :n]) <= 50 * d * 2.2e-16 * nrm ** 2
+    assert np.allclose(np.tril(M, -1), 0.0)
+    assert np.linalg.norm(M @ R - np.eye(n)) <= 100 * n * 2.2e-16 * cond * 10
+    Mo = orc.tri_inverse(Ro)
+    xo = Mo @ orc.householder_qr(Yo)[1][:n, n]
+    assert np.linalg.norm(A @ (x0 - xo)) <= 1e-9 * np.linalg.norm(b) * max(1.0, cond * 1e-8)
+
+
+def test_precond_rank_deficient(ctx, orc):
+    import paper_2506_03070_gb300 as P
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((2000, 10))
+    A[:, 3] = 0.0
+    b = rng.standard_normal(2000)
+    Y = orc.sketch_apply(A, b, 40, 8, 1)
+    with pytest.raises(P.LsqError) as e:
+        ctx.lsq_precond(_dev(Y), 10, has_b=True)
+    assert e.value.status == -6
+
+
+# ------------------------------------------------------------------ LSQR ---
+@pytest.mark.parametrize("m,n,d,zeta,cond,tol", [(20000, 200, 800, 8, 1e8, 1e-12), (5003, 33, 132, 8, 1e10, 1e-12),
+                                                 (777, 1, 4, 3, 1.0, 1e-12), (9000, 512, 2048, 8, 1e6, 1e-12),
+                                                 (4000, 64, 256, 8, 1e3, 1e-14)])
+def test_lsqr_matches_oracle(ctx, orc, m, n, d, zeta, cond, tol):
+    A, b, xt = _problem(m, n, cond, m)
+    Yo = orc.sketch_apply(A, b, d, zeta, 3)
+    Ro, _, _ = orc.householder_qr(Yo)
+    Mo = orc.tri_inverse(Ro[:n, :n])
+    x0 = Mo @ Ro[:n, n]
+    maxit = orc.default_maxit(n, d, tol)
+    ref = orc.lsqr(A, b, Mo, x0, tol, maxit)
+    x, info = ctx.lsq_lsqr(_dev(A), _dev(b), _dev(Mo), _dev(x0), tol, maxit)
+    x = x.cpu().numpy()
+    bn = np.linalg.norm(b)
+    assert abs(info["iters"] - ref["iters"]) <= 2, (info["iters"], ref["iters"])
+    assert np.linalg.norm(A @ (x - ref["x"])) <= 1e-10 * bn
+    assert orc.backward_error_kw(A, b, x) <= 1e-10
+
+
+def test_lsqr_maxit_reports_noconv(ctx, orc):
+    A, b, _ = _problem(3000, 20, 1e4, 5)
+    Yo = orc.sketch_apply(A, b, 80, 8, 3)
+    Ro, _, _ = orc.householder_qr(Yo)
+    Mo = orc.tri_inverse(Ro[:20, :20])
+    x0 = Mo @ Ro[:20, 20]
+    ref = orc.lsqr(A, b, Mo, x0, 1e-30, 4, trace=True)
+    x, info = ctx.lsq_lsqr(_dev(A), _dev(b), _dev(Mo), _dev(x0), 1e-30, 4)
+    assert info["status"] == -7 and info["iters"] == 4 and info["stop"] == 3
+    # after exactly 4 iterations the iterates agree with the oracle's x_4
+    assert np.linalg.norm(A @ (x.cpu().numpy() - ref["trace"][3])) <= 1e-12 * np.linalg.norm(b)
+
+
+# ----------------------------------------------------------------- check ---
+def test_check_matches_oracle(ctx, orc):
+    A, b, xt = _problem(6007, 45, 1e5, 8)
+    x = xt + 1e-7 * np.random.default_rng(0).standard_normal(45)
+    info = ctx.lsq_check(_dev(A), _dev(b), _dev(x))
+    eta, parts = orc.backward_error(A, b, x, parts=True)
+    assert abs(info["backward_error_ne"] - eta) <= 1e-8 * eta
+    assert abs(info["rnorm"] - parts["rnorm"]) <= 1e-10 * parts["rnorm"]
+    assert abs(info["anorm_fro"] - parts["fro"]) <= 1e-13 * parts["fro"]
+    assert abs(info["xnorm"] - np.linalg.norm(x)) <= 1e-14 * np.linalg.norm(x)
+
+
+# ------------------------------------------------------------------ solve ---
+def test_solve_config0_matches_oracle(ctx, orc):
+    """20000 x 200, cond 1e8, ||r_perp|| = 1e-6, d = 800, zeta = 8, tol 1e-12."""
+    from paper_2506_03070_gb300 import synth
+    p = synth.config0()
+    A, b, xt = p["A"].numpy(), p["b"].numpy(), p["x_true"].numpy()
+    x, info = ctx.lsq_solve(_dev(A), _dev(b), 800, zeta=8, seed=42, tol=1e-12)
+    x = x.cpu().numpy()
+    ref = orc.solve(A, b, 800, 8, 42, 1e-12, orc.default_maxit(200, 800, 1e-12))
+    bn = np.linalg.norm(b)
+    assert info["status"] == 0 and info["stop"] == 1
+    assert abs(info["iters"] - ref["iters"]) <= 2
+    assert np.linalg.norm(A @ (x - ref["x"])) <= 1e-10 * bn
+    assert np.linalg.norm(A @ (x - xt)) <= 1e-10 * bn
+    assert orc.backward_error_kw(A, b, x) <= 1e-10
+    # the device-side accuracy pass agrees with the oracle's.  r = b - A x
+    # cancels ~6 digits here (||r|| / ||b|| ~ 2e-6) and A^T r cancels again,
+    # so both sides carry only ~2 significant digits of eta_NE.
+    eta = orc.backward_error(A, b, x)
+    assert abs(info["backward_error_ne"] - eta) <= 5e-2 * eta
+    assert abs(info["rnorm"] - np.linalg.norm(b - A @ x)) <= 1e-8 * info["rnorm"]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_solve_host_memory_equals_device(ctx, orc, prec):
+    A, b, xt = _problem(8000, 100, 1e8, 21)
+    xd, infod = ctx.lsq_solve(_dev(A), _dev(b), 400, seed=5, tol=1e-12, prec=prec)
+    xh, infoh = ctx.lsq_solve(np.ascontiguousarray(A), b, 400, seed=5, tol=1e-12, prec=prec)
+    bn = np.linalg.norm(b)
+    assert np.linalg.norm(A @ (xd.cpu().numpy() - xh)) <= 1e-10 * bn
+    assert orc.backward_error_kw(A, b, xh) <= 1e-10
+    assert abs(infod["iters"] - infoh["iters"]) <= 1
+
+
+def test_solve_edge_shapes(ctx, orc):
+    import paper_2506_03070_gb300 as P
+    # n = 1, tiny d, ragged m
+    A, b, xt = _problem(1001, 1, 1.0, 2)
+    x, info = ctx.lsq_solve(_dev(A), _dev(b), 4, zeta=3, seed=1, tol=1e-12)
+    assert orc.backward_error_kw(A, b, x.cpu().numpy()) <= 1e-10
+    # n beyond the built kernels
+    A2 = torch.zeros((2000, 513), dtype=torch.float64, device="cuda")
+    with pytest.raises(P.LsqError) as e:
+        ctx.lsq_solve(A2, torch.zeros(2000, dtype=torch.float64, device="cuda"), 2100)
+    assert e.value.status == -10
+    # d < n + 1
+    with pytest.raises(P.LsqError) as e:
+        ctx.lsq_solve(_dev(A), _dev(b), 1)
+    assert e.value.status == -1
+
+
+def test_solve_consistent_system(ctx, orc):
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((4000, 30))
+    b = A @ rng.standard_normal(30)
+    x, info = ctx.lsq_solve(_dev(A), _dev(b), 120, seed=2, tol=1e-12)
+    assert info["status"] == 0
+    assert np.linalg.norm(b - A @ x.cpu().numpy()) <= 1e-10 * np.linalg.norm(b)
