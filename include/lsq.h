@@ -158,6 +158,23 @@ lsq_status lsq_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t
 lsq_status lsq_check(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
                      const double* x, const double* M, lsq_info* info, void* stream);
 
+/* Allocation-free variant of lsq_check (the paper has no counterpart; this is
+ * an interface convenience).  For callers that may not allocate device memory
+ * -- code running under another allocator that owns the GPU's memory, or with
+ * a memory plan fixed at start-up -- and so cannot create an lsq_ctx: it takes
+ * no context and calls no allocator.  Its scratch is one static device array
+ * of about 4.1 MB that every GPU loading the library keeps until the process
+ * exits.  Limits: n <= 512 (otherwise LSQ_ERR_ARG, nothing launched).  The
+ * first call on a device looks up that array's device address (with the
+ * device current); make that first call before any stream capture.  All calls
+ * on a device share the array: calls whose GPU work overlaps (other streams,
+ * other host threads) race and must be serialised by the caller.  Runs on the
+ * current device and `stream`, synchronises `stream`, fills the accuracy
+ * fields of info (rnorm, arnorm, anorm_fro, xnorm, bnorm, backward_error_ne,
+ * backward_error_pre); same inputs and meaning as lsq_check. */
+lsq_status lsq_check_noalloc(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, const double* x,
+                             const double* M, lsq_info* info, void* stream);
+
 /* Algorithm 1 end to end: sketch, precondition, LSQR, accuracy pass.
  * x: n doubles, device memory for LSQ_MEM_DEVICE problems, host memory for
  * LSQ_MEM_HOST problems.  info may be NULL. */

@@ -30,7 +30,8 @@ MEM_DEVICE, MEM_HOST = 0, 1
 FLAG_TIMING, FLAG_NO_CHECK, FLAG_NATIVE_FP64 = 1, 2, 4
 
 EXPORTS = ("lsq_create", "lsq_destroy", "lsq_last_error", "lsq_status_string", "lsq_workspace_bytes",
-           "lsq_sketch_indices", "lsq_sketch", "lsq_precond", "lsq_lsqr", "lsq_check", "lsq_solve")
+           "lsq_sketch_indices", "lsq_sketch", "lsq_precond", "lsq_lsqr", "lsq_check", "lsq_solve",
+           "lsq_check_noalloc")
 
 
 class LsqError(RuntimeError):
@@ -89,6 +90,8 @@ def load(path: str = LIB_PATH):
     L.lsq_lsqr.argtypes = [P, P, i64, i64, i64, P, P, P, f64, i64, i32, P, P, P]
     L.lsq_check.argtypes = [P, P, i64, i64, i64, P, P, P, P, P]
     L.lsq_solve.argtypes = [P, ctypes.POINTER(Problem), ctypes.POINTER(Opts), P, ctypes.POINTER(Info), P]
+    L.lsq_check_noalloc.argtypes = [P, i64, i64, i64, P, P, P, ctypes.POINTER(Info), P]
+    L.lsq_check_noalloc.restype = i32
     for name in ("lsq_create", "lsq_destroy", "lsq_sketch_indices", "lsq_sketch", "lsq_precond", "lsq_lsqr",
                  "lsq_check", "lsq_solve"):
         getattr(L, name).restype = i32
@@ -239,6 +242,21 @@ class Context:
         st = self.lib.lsq_solve(self.h, ctypes.byref(pr), ctypes.byref(op), _ptr(x), ctypes.byref(info), strm)
         self._check(st, allow=(LSQ_OK, LSQ_ERR_NOCONV) if allow_noconv else (LSQ_OK,))
         return x, info.as_dict()
+
+
+def lsq_check_noalloc(A, b, x, M=None, stream=None):
+    """Accuracy pass without any device allocation and without a context
+    (for callers that may not allocate device memory).  Uses the library's
+    static device scratch (n <= 512); calls that overlap on the GPU race.
+    Runs on the current CUDA device.  Returns the info dict."""
+    L = load()
+    _dev_f64(A, "A")
+    m, n, lda = _rowmajor(A)
+    info = Info()
+    st = L.lsq_check_noalloc(_ptr(A), m, n, lda, _ptr(b), _ptr(x), _ptr(M), ctypes.byref(info), _stream(stream))
+    if st != LSQ_OK:
+        raise LsqError(st, "lsq_check_noalloc failed (n > 512 or CUDA error)")
+    return info.as_dict()
 
 
 _default = {}
