@@ -92,8 +92,12 @@ def _dist():
     return world, rank, local
 
 
-def make_problem(config, device):
+def make_problem(config, device, m=None, n=None):
     from paper_2506_03070_gb300 import synth
+    if m and n:
+        p = synth.dense_problem(m, n, 1e10, resid_norm=1e-6, coherent_frac=0.01, seed=10, device=device)
+        p.update(d=4 * n, zeta=8, tol=1e-12, seed_sketch=43, name=f"dense_{m}x{n}_cond1e10_coherent")
+        return p
     if config == 0:
         p = synth.config0(device=device)
     else:
@@ -212,16 +216,17 @@ def run_gpu(args):
     import paper_2506_03070_gb300 as P
 
     ctx = P.Context(local)
-    p = make_problem(args.config, f"cuda:{local}")
+    p = make_problem(args.config, f"cuda:{local}", args.m, args.n)
     A, b = p["A"], p["b"]
     m, n = A.shape
     d, zeta, tol, seed = p["d"], p["zeta"], p["tol"], p["seed_sketch"]
     prec = 0 if args.prec == "fp64" else 1
-    flags = P.FLAG_TIMING | (P.FLAG_NATIVE_FP64 if args.native else 0)
+    flags = P.FLAG_TIMING | (P.FLAG_NATIVE_FP64 if args.native else 0) | (P.FLAG_NO_CHECK if args.no_check else 0)
     stream = torch.cuda.current_stream()
 
     def solve():
-        return ctx.lsq_solve(A, b, d, zeta=zeta, seed=seed, tol=tol, prec=prec, flags=flags, stream=stream)
+        return ctx.lsq_solve(A, b, d, zeta=zeta, seed=seed, tol=tol, prec=prec, flags=flags, stream=stream,
+                             maxit=args.maxit, allow_noconv=args.maxit > 0)
 
     for _ in range(args.warmup):
         x, info = solve()
@@ -274,12 +279,14 @@ def run_gpu(args):
         bh.copy_(b)
         Anp, bnp = Ah.numpy(), bh.numpy()
         xh = np.empty(n, dtype=np.float64)
-        ctx.lsq_solve(Anp, bnp, d, zeta=zeta, seed=seed, tol=tol, prec=prec, flags=flags, x=xh)
+        ctx.lsq_solve(Anp, bnp, d, zeta=zeta, seed=seed, tol=tol, prec=prec, flags=flags, x=xh, maxit=args.maxit,
+                      allow_noconv=args.maxit > 0)
         k2 = max(1, min(args.steps, 3))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(k2):
-            ctx.lsq_solve(Anp, bnp, d, zeta=zeta, seed=seed, tol=tol, prec=prec, flags=flags, x=xh)
+            ctx.lsq_solve(Anp, bnp, d, zeta=zeta, seed=seed, tol=tol, prec=prec, flags=flags, x=xh,
+                          maxit=args.maxit, allow_noconv=args.maxit > 0)
         t_e2e = time.perf_counter() - t0
         e2e = {"value": world * k2 / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": 8 * m * n + 8 * m,
                "d2h_bytes_per_step": 8 * n + 4096, "steps": k2}
@@ -340,6 +347,10 @@ def main():
     ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--native", action="store_true", help="LSQR matvecs on the native FP64 pipe")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--m", type=int, default=0, help="custom problem rows (profiling runs)")
+    ap.add_argument("--n", type=int, default=0, help="custom problem columns (profiling runs)")
+    ap.add_argument("--maxit", type=int, default=0, help="cap LSQR iterations (profiling runs)")
+    ap.add_argument("--no-check", action="store_true", help="skip the accuracy pass (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

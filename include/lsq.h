@@ -89,6 +89,8 @@ typedef struct {
 #define LSQ_FLAG_TIMING 1      /* record per-phase device times in lsq_info */
 #define LSQ_FLAG_NO_CHECK 2    /* skip the final accuracy pass (backward errors not filled) */
 #define LSQ_FLAG_NATIVE_FP64 4 /* run the LSQR matvecs on the native FP64 pipe */
+#define LSQ_FLAG_NO_IMAGE 8    /* do not keep the 8 B/entry float-pair image of A (saves
+                                  m*n*8 bytes of workspace; each pass splits A itself) */
 
 typedef struct {
   int32_t status;          /* status of the solve (same as the return value) */

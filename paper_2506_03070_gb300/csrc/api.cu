@@ -132,17 +132,19 @@ int64_t default_maxit(int64_t n, int64_t d, double tol) {
 
 struct LsqrWork {
   double *u, *v, *vhat, *w, *wv, *g, *gpart, *part, *Mt;
+  float2* image;  // (hi, mid) float-pair image of A for the double-float pass, or null
 };
 
-LsqrWork carve_lsqr(Carver& cv, int64_t m, int n, int npad, int grid) {
+LsqrWork carve_lsqr(Carver& cv, int64_t m, int n, int npad, int grid, bool image = false) {
   LsqrWork w;
+  w.image = image ? cv.take<float2>((size_t)m * n) : nullptr;
   w.u = cv.take<double>((size_t)m);
   w.v = cv.take<double>(npad);
   w.vhat = cv.take<double>(npad);
   w.w = cv.take<double>(npad);
   w.wv = cv.take<double>(npad);
   w.g = cv.take<double>(npad);
-  w.gpart = cv.take<double>((size_t)grid * npad);
+  w.gpart = cv.take<double>((size_t)lsqr_gparts(grid) * npad);
   w.part = cv.take<double>((size_t)grid * 4);
   w.Mt = cv.take<double>((size_t)n * n);
   return w;
@@ -165,10 +167,10 @@ void fill_info(lsq_info* info, const double* out, lsq_status st, int32_t rounds)
   info->sketch_rounds_max = rounds;
 }
 
-// Launch the LSQR / check kernel.
+// Launch the LSQR / check kernel (native: FP64-pipe pass; else double-float pass).
 lsq_status run_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int n, int64_t lda, const double* b, const double* M,
                     const double* Mt, double* x, double tol, int64_t maxit, int mode, const LsqrWork& w, int grid,
-                    int npad, cudaStream_t st) {
+                    int npad, bool native, cudaStream_t st) {
   LsqrParams p;
   p.A = A;
   p.m = m;
@@ -176,6 +178,7 @@ lsq_status run_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int n, int64_t lda
   p.npad = npad;
   p.lda = lda;
   p.b = b;
+  p.asplit = native ? nullptr : w.image;
   p.M = M;
   p.Mt = Mt;
   p.x = x;
@@ -194,7 +197,7 @@ lsq_status run_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int n, int64_t lda
   p.status = ctx->d_status;
   p.out = ctx->d_out;
   CK(cudaMemsetAsync(ctx->d_bar, 0, sizeof(GridBarrier), st));
-  CK(lsqr_run(p, vec_ok(A, lda), true, grid, st));
+  CK(lsqr_run(p, vec_ok(A, lda), native, grid, st));
   return LSQ_OK;
 }
 
@@ -356,20 +359,28 @@ lsq_status lsq_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t
   if (m < 1 || n < 1 || lda < n) return fail(ctx, LSQ_ERR_ARG, "need m >= 1, n >= 1, lda >= n");
   if (!A || !b || !M || !x0 || !x) return fail(ctx, LSQ_ERR_ARG, "null pointer");
   if (n > 512) return fail(ctx, LSQ_ERR_UNSUPPORTED, "LSQR kernel built for n <= 512");
-  (void)flags;
   cudaStream_t st = (cudaStream_t)stream;
   const int ni = (int)n, npad = (int)((n + 31) / 32 * 32);
-  const int grid = lsqr_grid(ni, vec_ok(A, lda), true, ctx->sms);
+  const bool native = (flags & LSQ_FLAG_NATIVE_FP64) || !lsqr_df_ok(A, n, lda);
+  const int grid = lsqr_grid(ni, vec_ok(A, lda), native, ctx->sms);
+  if (grid < 1) return fail(ctx, LSQ_ERR_CUDA, "no launchable LSQR configuration");
+  bool image = !native && !(flags & LSQ_FLAG_NO_IMAGE);
   Carver probe{nullptr};
-  carve_lsqr(probe, m, ni, npad, grid);
+  carve_lsqr(probe, m, ni, npad, grid, image);
+  if (image && probe.off > ctx->budget) {
+    image = false;  // fall back to splitting A on the fly in every pass
+    probe = Carver{nullptr};
+    carve_lsqr(probe, m, ni, npad, grid, false);
+  }
   if ((s = ensure_ws(ctx, probe.off)) != LSQ_OK) return s;
   Carver cv{ctx->ws};
-  LsqrWork w = carve_lsqr(cv, m, ni, npad, grid);
+  LsqrWork w = carve_lsqr(cv, m, ni, npad, grid, image);
   if ((s = reset_small(ctx, st)) != LSQ_OK) return s;
   CK(transpose_square(M, ni, w.Mt, st));
   if (x != x0) CK(cudaMemcpyAsync(x, x0, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   if (maxit <= 0) maxit = 1000;
-  if ((s = run_lsqr(ctx, A, m, ni, lda, b, M, w.Mt, x, tol, maxit, 2, w, grid, npad, st)) != LSQ_OK) return s;
+  if ((s = run_lsqr(ctx, A, m, ni, lda, b, M, w.Mt, x, tol, maxit, 2, w, grid, npad, native, st)) != LSQ_OK)
+    return s;
   uint32_t bits = 0;
   double out[kOutSlots];
   if ((s = read_small(ctx, st, &bits, nullptr, out)) != LSQ_OK) return s;
@@ -396,7 +407,7 @@ lsq_status lsq_check(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_
   if ((s = reset_small(ctx, st)) != LSQ_OK) return s;
   if (M) CK(transpose_square(M, ni, w.Mt, st));
   if ((s = run_lsqr(ctx, A, m, ni, lda, b, M, M ? w.Mt : nullptr, const_cast<double*>(x), 0.0, 0, 1, w, grid, npad,
-                    st)) != LSQ_OK)
+                    true, st)) != LSQ_OK)
     return s;
   uint32_t bits = 0;
   double out[kOutSlots];
@@ -426,9 +437,14 @@ lsq_status lsq_solve(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts* o, dou
   const size_t yes = o->prec == LSQ_PREC_FP64 ? 8 : 4;
   const int64_t lda_dev = host ? n : lda;
   const bool vec = host ? (n % 2 == 0) : vec_ok(pr->A, lda);
-  const int grid = lsqr_grid(ni, vec, true, ctx->sms);
+  // host problems are copied into 256-byte aligned workspace with lda = n
+  const bool native = (o->flags & LSQ_FLAG_NATIVE_FP64) || !(host ? (n % 2 == 0 && n <= 512)
+                                                                  : lsqr_df_ok(pr->A, n, lda));
+  const int grid = lsqr_grid(ni, vec, native, ctx->sms);
+  if (grid < 1) return fail(ctx, LSQ_ERR_CUDA, "no launchable LSQR configuration");
   const int64_t maxit = o->maxit > 0 ? o->maxit : default_maxit(n, d, o->tol);
 
+  bool image = !native && !(o->flags & LSQ_FLAG_NO_IMAGE);
   auto carve = [&](Carver& cv, const double** A, const double** b, double** xd, void** Y, PrecondBuffers* pb,
                    double** R, double** M, LsqrWork* lw) {
     if (host) {
@@ -447,7 +463,7 @@ lsq_status lsq_solve(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts* o, dou
     pb->Mt = nullptr;
     *R = cv.take<double>((size_t)n * n);
     *M = cv.take<double>((size_t)n * n);
-    *lw = carve_lsqr(cv, m, ni, npad, grid);
+    *lw = carve_lsqr(cv, m, ni, npad, grid, image);
     pb->Mt = lw->Mt;
   };
   {
@@ -458,6 +474,11 @@ lsq_status lsq_solve(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts* o, dou
     PrecondBuffers pb0;
     LsqrWork lw0;
     carve(probe, &A0, &b0, &x0, &Y0, &pb0, &R0, &M0, &lw0);
+    if (image && probe.off > ctx->budget) {
+      image = false;  // no room for the float-pair image: split A on the fly
+      probe = Carver{nullptr};
+      carve(probe, &A0, &b0, &x0, &Y0, &pb0, &R0, &M0, &lw0);
+    }
     if ((s = ensure_ws(ctx, probe.off)) != LSQ_OK) return s;
   }
   Carver cv{ctx->ws};
@@ -507,7 +528,8 @@ lsq_status lsq_solve(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts* o, dou
     return s;
   }
   const int mode = (o->flags & LSQ_FLAG_NO_CHECK) ? 2 : 0;
-  if ((s = run_lsqr(ctx, A, m, ni, lda_dev, b, M, lw.Mt, xd, o->tol, maxit, mode, lw, grid, npad, st)) != LSQ_OK)
+  if ((s = run_lsqr(ctx, A, m, ni, lda_dev, b, M, lw.Mt, xd, o->tol, maxit, mode, lw, grid, npad, native, st)) !=
+      LSQ_OK)
     return s;
   if (timing) CK(cudaEventRecord(ev[4], st));
   if (host) CK(cudaMemcpyAsync(x, xd, sizeof(double) * n, cudaMemcpyDeviceToHost, st));

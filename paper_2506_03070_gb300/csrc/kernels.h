@@ -38,6 +38,7 @@ struct LsqrParams {
   int npad;
   int64_t lda;
   const double* b;
+  float2* asplit;    // m x n (hi, mid) float-pair image of A written by the first pass, or null
   const double* M;   // n x n row-major (upper triangular), may be null in check mode
   const double* Mt;  // transpose of M, row-major
   double* x;         // in: start, out: solution
@@ -47,7 +48,8 @@ struct LsqrParams {
   double* w;         // n
   double* wv;        // n
   double* g;         // n
-  double* gpart;     // grid * npad
+  double* gpart;     // gparts * npad partial sums of A^T y (per block or per warp)
+  int gparts;        // rows of gpart in use (set by the pass)
   double* part;      // grid * 4
   double tol;
   int64_t maxit;
@@ -71,6 +73,11 @@ enum {
   OUT_ANORM_EST,
   kOutSlots = 16
 };
+// True when the double-float LSQR kernel applies (n even and <= 512, lda
+// even, A 16-byte aligned); otherwise the native-FP64 kernel runs.
+bool lsqr_df_ok(const double* A, int64_t n, int64_t lda);
+// Rows of gpart the LSQR kernel needs for a grid (per-warp partials).
+int lsqr_gparts(int grid);
 // Grid size the LSQR kernel will use for n (co-resident blocks).
 int lsqr_grid(int n, bool vec, bool native, int sms);
 cudaError_t lsqr_run(const LsqrParams& p, bool vec, bool native, int grid, cudaStream_t st);

@@ -14,6 +14,7 @@
 // order, so all blocks take the same branch at the stopping test.  After the
 // loop the same pass structure computes r = b - A x, A^T r and ||A||_F (the
 // accuracy check) and the backward-error bounds.
+#include "dfloat.cuh"
 #include "kernels.h"
 
 namespace lsq {
@@ -22,6 +23,7 @@ namespace {
 
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
+constexpr int kNbuf = 3;  // bulk-copy ring depth per warp (rows in flight)
 
 // --------------------------------------------------------------------------
 // The pass over A.  Block `blk` owns rows [m*blk/G, m*(blk+1)/G); its warp k
@@ -119,13 +121,35 @@ __device__ void pass_native(const LsqrParams& p, const double* __restrict__ wvec
   __syncthreads();
 }
 
+template <int T, bool VEC>
+struct NativePass {
+  double* s_g;
+  double* s_scal;
+  __device__ void init(LsqrParams& p) {  // y = b - A x0 -> u; sum y^2, sum b^2
+    p.gparts = gridDim.x;
+    pass_native<T, VEC, false, true>(p, p.x, -1.0, p.b, -1.0, p.u, s_g, s_scal);
+  }
+  __device__ void iter(LsqrParams& p, double gamma) {  // y = A wv - gamma u -> u
+    p.gparts = gridDim.x;
+    pass_native<T, VEC, false, false>(p, p.wv, 1.0, p.u, gamma, p.u, s_g, s_scal);
+  }
+  __device__ void check(LsqrParams& p) {  // y = b - A x; sum y^2, b^2, A_ij^2
+    p.gparts = gridDim.x;
+    pass_native<T, VEC, true, true>(p, p.x, -1.0, p.b, -1.0, nullptr, s_g, s_scal);
+  }
+};
+
 // g[j] = sum over blocks of gpart[blk][j], block order.
+// Column j is summed by block j % G: thread t adds partials t, t+256, ...,
+// then a fixed-order block reduction (deterministic for a given grid).
 __device__ void reduce_g(const LsqrParams& p) {
+  __shared__ double scratch[32];
   const int G = gridDim.x;
-  for (int j = blockIdx.x * kThreads + threadIdx.x; j < p.n; j += G * kThreads) {
+  for (int j = blockIdx.x; j < p.n; j += G) {
     double s = 0.0;
-    for (int c = 0; c < G; ++c) s += p.gpart[(int64_t)c * p.npad + j];
-    p.g[j] = s;
+    for (int c = threadIdx.x; c < p.gparts; c += kThreads) s += p.gpart[(int64_t)c * p.npad + j];
+    s = block_sum(s, scratch);
+    if (threadIdx.x == 0) p.g[j] = s;
   }
 }
 
@@ -185,18 +209,255 @@ __device__ void m_apply_update(const LsqrParams& p, double ainv, double cx, doub
   }
 }
 
-template <int T, bool VEC>
-__global__ void __launch_bounds__(kThreads, 2) k_lsqr_native(LsqrParams p) {
-  __shared__ double s_g[kWarps * 64 * T];
-  __shared__ double s_scal[kWarps * 4];
+// --------------------------------------------------------------------------
+// The double-float pass (FP32/INT pipes only in the per-element and per-row
+// work).  Rows arrive through a per-warp ring of kNbuf shared-memory row
+// buffers filled by cp.async.bulk (one elected lane issues, an mbarrier per
+// buffer signals completion), so each warp keeps kNbuf rows in flight while it
+// computes.  Requires n even, lda even and A 16-byte aligned.
+//
+// Per row: lane l splits its 2T column pairs into (hi, mid) floats,
+// accumulates the row dot in kAcc independent float-pair accumulators, sums
+// them and butterflies the result over the warp (every lane ends with the
+// same pair), forms y = dot - gamma * u_i in pair arithmetic, stores y (the u
+// buffer holds float pairs in this kernel) and adds y * A_i into its column
+// accumulators.  Column pairs are renormalised every second row and flushed
+// into the warp's FP64 partial-sum row of gpart every 32 rows, so no pair sum
+// runs over more than 32 rows.  gpart holds one row per warp (grid * kWarps
+// rows).
+//
+// When the workspace allows (p.asplit != null) the first pass also stores
+// every split row as a (hi, mid) float-pair image of A (8 bytes per entry, as
+// FP64), and later passes stream that image instead of A: the values are
+// identical to the on-the-fly split, and the per-entry integer split leaves
+// the hot loop.
+// --------------------------------------------------------------------------
+template <int T>
+struct DfPass {
+  double* ring;     // dynamic shared memory [kWarps][kNbuf][n]
+  uint64_t* bars;   // [kWarps][kNbuf]
+  double* s_scal;
+  uint32_t seq;     // rows this warp has consumed so far (all passes)
+
+  // Row source: the FP64 matrix, or its (hi, mid) float-pair image (same bytes per row).
+  template <bool FROM_IMAGE>
+  __device__ void issue(const LsqrParams& p, int64_t r0, int wib, uint32_t j, double* myring, uint64_t* mybars) {
+    const int64_t row = r0 + (int64_t)wib + (int64_t)kWarps * j;
+    const uint32_t s = seq + j, b = s % kNbuf;
+    const uint32_t rb = (uint32_t)p.n * 8u;
+    const void* src = FROM_IMAGE ? (const void*)(p.asplit + row * p.n) : (const void*)(p.A + row * p.lda);
+    mbar_arrive_expect_tx(mybars + b, rb);
+    bulk_g2s(myring + (size_t)b * p.n, src, rb, mybars + b);
+  }
+
+  // Wait (bounded) for the buffer of row j.  Returns false on timeout (warp-uniform).
+  __device__ bool wait(uint32_t j, uint64_t* mybars) {
+    const uint32_t s = seq + j, b = s % kNbuf, par = (s / kNbuf) & 1u;
+    bool timed_out = false;
+    if (!mbar_try_wait(mybars + b, par)) {
+      const unsigned long long t0 = globaltimer_ns();
+      uint32_t it = 0;
+      while (!mbar_try_wait(mybars + b, par)) {
+        if ((++it & 255u) == 0 && globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+          timed_out = true;
+          break;
+        }
+      }
+    }
+    return !__any_sync(0xffffffffu, timed_out);
+  }
+
+  // FROM_IMAGE: rows come from the float-pair image; else from A (split on
+  // the fly) and, when WRITE_IMAGE, the split rows are stored to the image.
+  template <bool UIN_B, bool UIN2, bool STORE, bool FROM_IMAGE, bool WRITE_IMAGE>
+  __device__ void run(const LsqrParams& p, const double* __restrict__ wvec, double wsign, double gamma) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int G = gridDim.x, blk = blockIdx.x;
+    const int n = p.n;
+    const int64_t r0 = (p.m * blk) / G, r1 = (p.m * (blk + 1)) / G;
+    const int64_t nrows = r1 - r0;
+    const uint32_t count = nrows > wib ? (uint32_t)((nrows - wib + kWarps - 1) / kWarps) : 0u;
+    double* myring = ring + (size_t)wib * kNbuf * n;
+    uint64_t* mybars = bars + wib * kNbuf;
+    float2* ubuf = reinterpret_cast<float2*>(p.u);
+    double* gw = p.gpart + ((int64_t)blk * kWarps + wib) * p.npad;
+
+    df wv[2 * T], Gc[2 * T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = 2 * lane + 64 * t + h;
+        const double v = j < n ? wsign * wvec[j] : 0.0;
+        const float v1 = __double2float_rn(v);
+        wv[2 * t + h] = df{v1, __double2float_rn(v - (double)v1)};
+        Gc[2 * t + h] = df{0.f, 0.f};
+      }
+    }
+    const float g1 = __double2float_rn(gamma);
+    const df gdf{g1, __double2float_rn(gamma - (double)g1)};
+    df ss{0.f, 0.f}, bb{0.f, 0.f};
+    bool first_flush = true;
+
+    if (lane == 0) {
+      fence_proxy_async_smem();
+      for (uint32_t j = 0; j < count && j < (uint32_t)kNbuf; ++j) issue<FROM_IMAGE>(p, r0, wib, j, myring, mybars);
+    }
+    bool ok = true;
+    uint32_t j = 0;
+    for (; j < count; ++j) {
+      if (!wait(j, mybars)) {
+        ok = false;
+        break;
+      }
+      const int64_t row = r0 + (int64_t)wib + (int64_t)kWarps * j;
+      const double* buf = myring + (size_t)((seq + j) % kNbuf) * n;
+      float h[2 * T], mm[2 * T];
+#pragma unroll
+      for (int t = 0; t < T; ++t) {
+        const int c = 2 * lane + 64 * t;
+        if (FROM_IMAGE) {
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (c < n) v = *reinterpret_cast<const float4*>(buf + c);
+          h[2 * t] = v.x;
+          mm[2 * t] = v.y;
+          h[2 * t + 1] = v.z;
+          mm[2 * t + 1] = v.w;
+        } else {
+          double2 v = make_double2(0.0, 0.0);
+          if (c < n) v = *reinterpret_cast<const double2*>(buf + c);
+          split2(v.x, h[2 * t], mm[2 * t]);
+          split2(v.y, h[2 * t + 1], mm[2 * t + 1]);
+          if (WRITE_IMAGE && c < n)
+            *reinterpret_cast<float4*>(p.asplit + row * n + c) = make_float4(h[2 * t], mm[2 * t], h[2 * t + 1],
+                                                                             mm[2 * t + 1]);
+        }
+      }
+      __syncwarp();
+      if (lane == 0 && j + kNbuf < count) {
+        fence_proxy_async_smem();
+        issue<FROM_IMAGE>(p, r0, wib, j + kNbuf, myring, mybars);
+      }
+      // row dot: kAcc independent pair accumulators (short chains)
+      constexpr int kAcc = (2 * T) >= 2 ? 2 : 1;
+      df av[kAcc];
+#pragma unroll
+      for (int k = 0; k < kAcc; ++k) av[k] = df{0.f, 0.f};
+#pragma unroll
+      for (int q = 0; q < 2 * T; ++q) df_fma_acc(av[q % kAcc], h[q], mm[q], wv[q].hi, wv[q].lo);
+#pragma unroll
+      for (int k = 1; k < kAcc; k <<= 1) {
+#pragma unroll
+        for (int i = 0; i + k < kAcc; i += 2 * k) av[i] = df_add(av[i], av[i + k]);
+      }
+      df dot = av[0];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) dot = df_add_unnorm(dot, shfl_xor_df(dot, o));
+      dot = df_renorm(dot);
+      df ui;
+      if (UIN_B) {
+        ui = df_from_double(p.b[row]);
+      } else {
+        const float2 uu = ubuf[row];
+        ui = df{uu.x, uu.y};
+      }
+      const df y = df_add(dot, df_neg(df_mul(gdf, ui)));
+      if (STORE && lane == 0) ubuf[row] = make_float2(y.hi, y.lo);
+      ss = df_add(ss, df_mul(y, y));
+      if (UIN2) bb = df_add(bb, df_mul(ui, ui));
+#pragma unroll
+      for (int q = 0; q < 2 * T; ++q) {
+        df_fma_acc(Gc[q], h[q], mm[q], y.hi, y.lo);
+        if (j & 1u) Gc[q] = df_renorm(Gc[q]);
+      }
+      if ((j & 31u) == 31u) {
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+          const int c = 2 * lane + 64 * t;
+          if (c < n) {
+            double2 g = first_flush ? make_double2(0.0, 0.0) : *reinterpret_cast<const double2*>(gw + c);
+            g.x += df_to_double(Gc[2 * t]);
+            g.y += df_to_double(Gc[2 * t + 1]);
+            *reinterpret_cast<double2*>(gw + c) = g;
+          }
+          Gc[2 * t] = Gc[2 * t + 1] = df{0.f, 0.f};
+        }
+        first_flush = false;
+      }
+    }
+    if (!ok) {
+      // give up: flag, then let the copies already issued land before leaving
+      if (lane == 0) {
+        atomicOr(p.status, DS_TIMEOUT);
+        atomicExch(&p.bar->abort, 1u);
+      }
+      for (uint32_t k = j; k < count && k < j + kNbuf; ++k) wait(k, mybars);
+    }
+    seq += count;
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+      const int c = 2 * lane + 64 * t;
+      if (c < n) {
+        double2 g = first_flush ? make_double2(0.0, 0.0) : *reinterpret_cast<const double2*>(gw + c);
+        g.x += df_to_double(Gc[2 * t]);
+        g.y += df_to_double(Gc[2 * t + 1]);
+        *reinterpret_cast<double2*>(gw + c) = g;
+      }
+    }
+    if (lane == 0) {
+      s_scal[wib * 4 + 0] = df_to_double(ss);
+      s_scal[wib * 4 + 1] = df_to_double(bb);
+      s_scal[wib * 4 + 2] = 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      double sum = 0.0;
+      for (int w = 0; w < kWarps; ++w) sum += s_scal[w * 4 + threadIdx.x];
+      p.part[(int64_t)blk * 4 + threadIdx.x] = sum;
+    }
+    __syncthreads();
+  }
+
+  __device__ void init(LsqrParams& p) {
+    p.gparts = gridDim.x * kWarps;
+    if (p.asplit) {
+      run<true, true, true, false, true>(p, p.x, -1.0, -1.0);
+      // the image was written through the generic proxy and is read by bulk
+      // copies (async proxy) after the next grid barrier
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+    } else {
+      run<true, true, true, false, false>(p, p.x, -1.0, -1.0);
+    }
+  }
+  __device__ void iter(LsqrParams& p, double gamma) {
+    p.gparts = gridDim.x * kWarps;
+    if (p.asplit)
+      run<false, false, true, true, false>(p, p.wv, 1.0, gamma);
+    else
+      run<false, false, true, false, false>(p, p.wv, 1.0, gamma);
+  }
+  // The accuracy pass runs in native FP64 (A is aligned here, so the vector
+  // path applies) with per-block partials; the ring doubles as its
+  // block-reduction scratch.
+  __device__ void check(LsqrParams& p) {
+    p.gparts = gridDim.x;
+    pass_native<T, true, true, true>(p, p.x, -1.0, p.b, -1.0, nullptr, ring, s_scal);
+  }
+};
+
+// --------------------------------------------------------------------------
+// Algorithm 2 around a pass policy (see the file header for the order).
+// --------------------------------------------------------------------------
+template <class Pass>
+__device__ void lsqr_body(LsqrParams& p, Pass& pass, double* s_scal) {
   uint32_t* status = p.status;
   double alpha = 0.0, beta = 0.0, rhobar = 0.0, phibar = 0.0, anorm2 = 0.0, bnorm = 0.0, normal_rel = 0.0;
   int64_t iters = 0;
   int stop = 0;
 
   if (p.mode != 1) {
-    // ---- beta_1 u_1 = b - A x0 : pass with wvec = x0, wsign = -1, uin = b, gamma = -1
-    pass_native<T, VEC, false, true>(p, p.x, -1.0, p.b, -1.0, p.u, s_g, s_scal);
+    // ---- beta_1 u_1 = b - A x0
+    pass.init(p);
     if (!grid_sync(p.bar, status)) return;
     reduce_g(p);
     if (!grid_sync(p.bar, status)) return;
@@ -221,7 +482,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_native(LsqrParams p) {
       }
       ++iters;
       // uhat_{t+1} = A (M v_t) - alpha_t u_t = A wv - (alpha/beta) uhat_t
-      pass_native<T, VEC, false, false>(p, p.wv, 1.0, p.u, alpha / beta, p.u, s_g, s_scal);
+      pass.iter(p, alpha / beta);
       if (!grid_sync(p.bar, status)) return;
       reduce_g(p);
       if (!grid_sync(p.bar, status)) return;
@@ -261,7 +522,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_native(LsqrParams p) {
     return;
   }
   // ---- accuracy pass: y = b - A x, g = A^T y, ||A||_F
-  pass_native<T, VEC, true, true>(p, p.x, -1.0, p.b, -1.0, nullptr, s_g, s_scal);
+  pass.check(p);
   if (!grid_sync(p.bar, status)) return;
   reduce_g(p);
   if (!grid_sync(p.bar, status)) return;
@@ -300,7 +561,35 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_native(LsqrParams p) {
 }
 
 template <int T, bool VEC>
-int grid_for(int sms) {
+__global__ void __launch_bounds__(kThreads, 2) k_lsqr_native(LsqrParams p) {
+  __shared__ double s_g[kWarps * 64 * T];
+  __shared__ double s_scal[kWarps * 4];
+  NativePass<T, VEC> pass{s_g, s_scal};
+  lsqr_body(p, pass, s_scal);
+}
+
+template <int T>
+__global__ void __launch_bounds__(kThreads, 2) k_lsqr_df(LsqrParams p) {
+  extern __shared__ __align__(128) double s_ring[];
+  __shared__ __align__(8) uint64_t s_bars[kWarps * kNbuf];
+  __shared__ double s_scal[kWarps * 4];
+  if ((threadIdx.x & 31) == 0) {
+    for (int b = 0; b < kNbuf; ++b) mbar_init(&s_bars[(threadIdx.x >> 5) * kNbuf + b], 1u);
+    fence_proxy_async_smem();
+  }
+  __syncthreads();
+  DfPass<T> pass{s_ring, s_bars, s_scal, 0u};
+  lsqr_body(p, pass, s_scal);
+}
+
+size_t df_smem(int T, int n) {
+  const size_t ring = (size_t)kWarps * kNbuf * n * sizeof(double);
+  const size_t red = (size_t)kWarps * 64 * T * sizeof(double);
+  return ring > red ? ring : red;
+}
+
+template <int T, bool VEC>
+int grid_native(int sms) {
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lsqr_native<T, VEC>, kThreads, 0) != cudaSuccess ||
       per_sm < 1)
@@ -309,11 +598,34 @@ int grid_for(int sms) {
   return per_sm * sms;
 }
 
+template <int T>
+int grid_df(int n, int sms) {
+  const size_t smem = df_smem(T, n);
+  if (cudaFuncSetAttribute(k_lsqr_df<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lsqr_df<T>, kThreads, smem) != cudaSuccess ||
+      per_sm < 1)
+    return 0;
+  if (per_sm > 2) per_sm = 2;
+  return per_sm * sms;
+}
+
 template <int T, bool VEC>
-cudaError_t launch(const LsqrParams& p, int grid, cudaStream_t st) {
+cudaError_t launch_native(const LsqrParams& p, int grid, cudaStream_t st) {
   LsqrParams q = p;
   void* args[] = {&q};
   return cudaLaunchCooperativeKernel((const void*)k_lsqr_native<T, VEC>, grid, kThreads, args, 0, st);
+}
+
+template <int T>
+cudaError_t launch_df(const LsqrParams& p, int grid, cudaStream_t st) {
+  LsqrParams q = p;
+  void* args[] = {&q};
+  const size_t smem = df_smem(T, p.n);
+  cudaError_t e = cudaFuncSetAttribute(k_lsqr_df<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaLaunchCooperativeKernel((const void*)k_lsqr_df<T>, grid, kThreads, args, smem, st);
 }
 
 int chunks_for(int n) {
@@ -326,22 +638,46 @@ int chunks_for(int n) {
 
 }  // namespace
 
-int lsqr_grid(int n, bool vec, bool /*native*/, int sms) {
+int lsqr_gparts(int grid) { return grid * kWarps; }
+
+bool lsqr_df_ok(const double* A, int64_t n, int64_t lda) {
+  return n % 2 == 0 && lda % 2 == 0 && ((uintptr_t)A % 16 == 0) && chunks_for((int)n) > 0;
+}
+
+int lsqr_grid(int n, bool vec, bool native, int sms) {
+  if (!native) {
+    switch (chunks_for(n)) {
+      case 1: return grid_df<1>(n, sms);
+      case 2: return grid_df<2>(n, sms);
+      case 4: return grid_df<4>(n, sms);
+      case 8: return grid_df<8>(n, sms);
+      default: return 0;
+    }
+  }
   switch (chunks_for(n)) {
-    case 1: return vec ? grid_for<1, true>(sms) : grid_for<1, false>(sms);
-    case 2: return vec ? grid_for<2, true>(sms) : grid_for<2, false>(sms);
-    case 4: return vec ? grid_for<4, true>(sms) : grid_for<4, false>(sms);
-    case 8: return vec ? grid_for<8, true>(sms) : grid_for<8, false>(sms);
+    case 1: return vec ? grid_native<1, true>(sms) : grid_native<1, false>(sms);
+    case 2: return vec ? grid_native<2, true>(sms) : grid_native<2, false>(sms);
+    case 4: return vec ? grid_native<4, true>(sms) : grid_native<4, false>(sms);
+    case 8: return vec ? grid_native<8, true>(sms) : grid_native<8, false>(sms);
     default: return 0;
   }
 }
 
-cudaError_t lsqr_run(const LsqrParams& p, bool vec, bool /*native*/, int grid, cudaStream_t st) {
+cudaError_t lsqr_run(const LsqrParams& p, bool vec, bool native, int grid, cudaStream_t st) {
+  if (!native) {
+    switch (chunks_for(p.n)) {
+      case 1: return launch_df<1>(p, grid, st);
+      case 2: return launch_df<2>(p, grid, st);
+      case 4: return launch_df<4>(p, grid, st);
+      case 8: return launch_df<8>(p, grid, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (chunks_for(p.n)) {
-    case 1: return vec ? launch<1, true>(p, grid, st) : launch<1, false>(p, grid, st);
-    case 2: return vec ? launch<2, true>(p, grid, st) : launch<2, false>(p, grid, st);
-    case 4: return vec ? launch<4, true>(p, grid, st) : launch<4, false>(p, grid, st);
-    case 8: return vec ? launch<8, true>(p, grid, st) : launch<8, false>(p, grid, st);
+    case 1: return vec ? launch_native<1, true>(p, grid, st) : launch_native<1, false>(p, grid, st);
+    case 2: return vec ? launch_native<2, true>(p, grid, st) : launch_native<2, false>(p, grid, st);
+    case 4: return vec ? launch_native<4, true>(p, grid, st) : launch_native<4, false>(p, grid, st);
+    case 8: return vec ? launch_native<8, true>(p, grid, st) : launch_native<8, false>(p, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }

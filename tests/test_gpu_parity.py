@@ -242,3 +242,49 @@ def test_solve_consistent_system(ctx, orc):
     x, info = ctx.lsq_solve(_dev(A), _dev(b), 120, seed=2, tol=1e-12)
     assert info["status"] == 0
     assert np.linalg.norm(b - A @ x.cpu().numpy()) <= 1e-10 * np.linalg.norm(b)
+
+
+# ------------------------------------------- double-float vs native pass ---
+NATIVE = 4  # LSQ_FLAG_NATIVE_FP64
+NO_IMAGE = 8  # LSQ_FLAG_NO_IMAGE
+
+
+@pytest.mark.parametrize("m,n,lda_pad", [(20000, 200, 0), (1001, 64, 0), (150, 8, 0), (7001, 128, 2), (3000, 512, 6)])
+def test_lsqr_double_float_pass_matches_native_and_oracle(ctx, orc, m, n, lda_pad):
+    A, b, xt = _problem(m, n, 1e6, m + n)
+    d = 4 * n if 4 * n < m else n + 1
+    zeta = min(8, d)
+    Yo = orc.sketch_apply(A, b, d, zeta, 3)
+    Ro, _, _ = orc.householder_qr(Yo)
+    Mo = orc.tri_inverse(Ro[:n, :n])
+    x0 = Mo @ Ro[:n, n]
+    maxit = orc.default_maxit(n, d, 1e-12)
+    ref = orc.lsqr(A, b, Mo, x0, 1e-12, maxit)
+    if lda_pad:
+        Ap = np.zeros((m, n + lda_pad))
+        Ap[:, :n] = A
+        Ad = _dev(Ap)[:, :n]
+    else:
+        Ad = _dev(A)
+    x_df, info_df = ctx.lsq_lsqr(Ad, _dev(b), _dev(Mo), _dev(x0), 1e-12, maxit)
+    x_nv, info_nv = ctx.lsq_lsqr(Ad, _dev(b), _dev(Mo), _dev(x0), 1e-12, maxit, flags=NATIVE)
+    x_ni, info_ni = ctx.lsq_lsqr(Ad, _dev(b), _dev(Mo), _dev(x0), 1e-12, maxit, flags=NO_IMAGE)
+    bn = np.linalg.norm(b)
+    # the float-pair image holds exactly the values the on-the-fly split makes
+    assert np.array_equal(x_df.cpu().numpy(), x_ni.cpu().numpy())
+    for x, info in ((x_df, info_df), (x_nv, info_nv)):
+        x = x.cpu().numpy()
+        assert abs(info["iters"] - ref["iters"]) <= 2, (info["iters"], ref["iters"])
+        assert np.linalg.norm(A @ (x - ref["x"])) <= 1e-10 * bn
+        assert orc.backward_error_kw(A, b, x) <= 1e-10
+
+
+def test_solve_double_float_repeatable(ctx):
+    """The LSQR kernel reduces in a fixed order, so solving the same problem
+    twice gives the same iterations; x differs only through the sketch's
+    atomic summation order."""
+    A, b, _ = _problem(30000, 100, 1e6, 77)
+    x1, i1 = ctx.lsq_solve(_dev(A), _dev(b), 400, seed=9, tol=1e-12)
+    x2, i2 = ctx.lsq_solve(_dev(A), _dev(b), 400, seed=9, tol=1e-12)
+    assert abs(i1["iters"] - i2["iters"]) <= 1
+    assert np.linalg.norm(A @ (x1.cpu().numpy() - x2.cpu().numpy())) <= 1e-11 * np.linalg.norm(b)
