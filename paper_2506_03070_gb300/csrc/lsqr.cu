@@ -153,11 +153,14 @@ __device__ void reduce_g(const LsqrParams& p) {
   }
 }
 
-// sum over blocks of part[blk][slot], block order (same value in every thread).
-__device__ __forceinline__ double sum_part(const LsqrParams& p, int slot) {
+// Sum over blocks of part[blk][slot]: thread t adds blocks t, t+256, ...,
+// then a fixed-order block reduction.  Every thread of every block calls it
+// and gets the same value.
+__device__ double sum_part(const LsqrParams& p, int slot) {
+  __shared__ double scratch[32];
   double s = 0.0;
-  for (int c = 0; c < (int)gridDim.x; ++c) s += p.part[(int64_t)c * 4 + slot];
-  return s;
+  for (int c = threadIdx.x; c < (int)gridDim.x; c += kThreads) s += p.part[(int64_t)c * 4 + slot];
+  return block_sum(s, scratch);
 }
 
 // vhat_k = (M^T g)_k * ginv - cv * v_k, one warp per k; per-block sum of
@@ -312,6 +315,13 @@ struct DfPass {
       }
       const int64_t row = r0 + (int64_t)wib + (int64_t)kWarps * j;
       const double* buf = myring + (size_t)((seq + j) % kNbuf) * n;
+      // u_i (or b_i) is needed only after the row dot: load it first
+      double bi = 0.0;
+      float2 uu = make_float2(0.f, 0.f);
+      if (UIN_B)
+        bi = p.b[row];
+      else
+        uu = ubuf[row];
       float h[2 * T], mm[2 * T];
 #pragma unroll
       for (int t = 0; t < T; ++t) {
@@ -354,13 +364,7 @@ struct DfPass {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) dot = df_add_unnorm(dot, shfl_xor_df(dot, o));
       dot = df_renorm(dot);
-      df ui;
-      if (UIN_B) {
-        ui = df_from_double(p.b[row]);
-      } else {
-        const float2 uu = ubuf[row];
-        ui = df{uu.x, uu.y};
-      }
+      const df ui = UIN_B ? df_from_double(bi) : df{uu.x, uu.y};
       const df y = df_add(dot, df_neg(df_mul(gdf, ui)));
       if (STORE && lane == 0) ubuf[row] = make_float2(y.hi, y.lo);
       ss = df_add(ss, df_mul(y, y));
@@ -490,7 +494,8 @@ __device__ void lsqr_body(LsqrParams& p, Pass& pass, double* s_scal) {
       // vhat_{t+1} = M^T A^T uhat / beta_{t+1} - beta_{t+1} v_t
       mt_apply(p, beta1 > 0.0 ? 1.0 / beta1 : 0.0, beta1, 2, s_scal);
       if (!grid_sync(p.bar, status)) return;
-      const double alpha1 = beta1 > 0.0 ? sqrt(sum_part(p, 2)) : 0.0;
+      const double a2 = sum_part(p, 2);
+      const double alpha1 = beta1 > 0.0 ? sqrt(a2) : 0.0;
       // Givens rotation
       const double rho = sqrt(fma(rhobar, rhobar, beta1 * beta1));
       const double c = rhobar / rho, s = beta1 / rho;
@@ -537,11 +542,11 @@ __device__ void lsqr_body(LsqrParams& p, Pass& pass, double* s_scal) {
     }
     gx = block_sum(gx, scratch);
     xx = block_sum(xx, scratch);
+    const double rnorm = sqrt(sum_part(p, 0));
+    const double bn = sqrt(sum_part(p, 1));
+    const double fro = sqrt(sum_part(p, 2));
+    const double marn = p.M ? sqrt(sum_part(p, 3)) : 0.0;
     if (threadIdx.x == 0) {
-      const double rnorm = sqrt(sum_part(p, 0));
-      const double bn = sqrt(sum_part(p, 1));
-      const double fro = sqrt(sum_part(p, 2));
-      const double marn = p.M ? sqrt(sum_part(p, 3)) : 0.0;
       const double arn = sqrt(gx), xn = sqrt(xx);
       p.out[OUT_ITERS] = (double)iters;
       p.out[OUT_STOP] = (double)stop;
