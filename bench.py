@@ -304,7 +304,7 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": dict(_workload(p, args.prec), parallelism="replicas" if world > 1 else "single"),
-        "roofline": {"bound": "hbm", "kernel": "k_lsqr_native", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": "k_lsqr_native" if args.native else "k_lsqr_df", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                      "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
                      else "fallback 6.8 TB/s"},
