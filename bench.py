@@ -92,11 +92,12 @@ def _dist():
     return world, rank, local
 
 
-def make_problem(config, device, m=None, n=None):
+def make_problem(config, device, m=None, n=None, cond=1e10, coherent=0.01):
     from paper_2506_03070_gb300 import synth
     if m and n:
-        p = synth.dense_problem(m, n, 1e10, resid_norm=1e-6, coherent_frac=0.01, seed=10, device=device)
-        p.update(d=4 * n, zeta=8, tol=1e-12, seed_sketch=43, name=f"dense_{m}x{n}_cond1e10_coherent")
+        p = synth.dense_problem(m, n, cond, resid_norm=1e-6, coherent_frac=coherent, seed=10, device=device)
+        tag = "_coherent" if coherent > 0 else ""
+        p.update(d=4 * n, zeta=8, tol=1e-12, seed_sketch=43, name=f"dense_{m}x{n}_cond{cond:.0e}{tag}")
         return p
     if config == 0:
         p = synth.config0(device=device)
@@ -216,7 +217,7 @@ def run_gpu(args):
     import paper_2506_03070_gb300 as P
 
     ctx = P.Context(local)
-    p = make_problem(args.config, f"cuda:{local}", args.m, args.n)
+    p = make_problem(args.config, f"cuda:{local}", args.m, args.n, args.cond, args.coherent)
     A, b = p["A"], p["b"]
     m, n = A.shape
     d, zeta, tol, seed = p["d"], p["zeta"], p["tol"], p["seed_sketch"]
@@ -348,6 +349,8 @@ def main():
     ap.add_argument("--native", action="store_true", help="LSQR matvecs on the native FP64 pipe")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--m", type=int, default=0, help="custom problem rows (profiling runs)")
+    ap.add_argument("--cond", type=float, default=1e10, help="condition number of a custom problem")
+    ap.add_argument("--coherent", type=float, default=0.01, help="fraction of rows scaled x1e4 (custom problem)")
     ap.add_argument("--n", type=int, default=0, help="custom problem columns (profiling runs)")
     ap.add_argument("--maxit", type=int, default=0, help="cap LSQR iterations (profiling runs)")
     ap.add_argument("--no-check", action="store_true", help="skip the accuracy pass (profiling runs)")

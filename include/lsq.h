@@ -91,6 +91,8 @@ typedef struct {
 #define LSQ_FLAG_NATIVE_FP64 4 /* run the LSQR matvecs on the native FP64 pipe */
 #define LSQ_FLAG_NO_IMAGE 8    /* do not keep the 8 B/entry float-pair image of A (saves
                                   m*n*8 bytes of workspace; each pass splits A itself) */
+#define LSQ_FLAG_NO_FALLBACK 16 /* mixed form: report LSQ_ERR_NOCONV instead of re-solving
+                                   in FP64 when the FP32 preconditioner stalls LSQR */
 
 typedef struct {
   int32_t status;          /* status of the solve (same as the return value) */
@@ -101,7 +103,8 @@ typedef struct {
   double backward_error_pre; /* ||M^T A^T r|| / (||A||_F ||x||): preconditioned bound */
   double rnorm, arnorm, anorm_fro, xnorm, bnorm;
   int32_t sketch_rounds_max; /* most rejection-sampling redraw rounds any column used */
-  int32_t reserved;
+  int32_t precond_fallback;  /* 1: the mixed form's preconditioner stalled LSQR and the
+                                plain form solved the problem again */
   float t_sketch_ms, t_precond_ms, t_lsqr_ms, t_check_ms, t_h2d_ms, t_d2h_ms;
 } lsq_info;
 
@@ -179,7 +182,13 @@ lsq_status lsq_check_noalloc(const double* A, int64_t m, int64_t n, int64_t lda,
 
 /* Algorithm 1 end to end: sketch, precondition, LSQR, accuracy pass.
  * x: n doubles, device memory for LSQ_MEM_DEVICE problems, host memory for
- * LSQ_MEM_HOST problems.  info may be NULL. */
+ * LSQ_MEM_HOST problems.  info may be NULL.
+ * prec = LSQ_PREC_MIXED accumulates the sketch and factors it in FP32; that
+ * preconditioner is good while cond(A) * 6e-8 * sqrt(m zeta / d) << 1.  The
+ * mixed LSQR is capped at twice the iterations the Sec. 4.3 rate estimate
+ * predicts (2 ceil(log(tol)/log(sqrt(n/d))) + 5); if it stalls, the problem is
+ * solved again in the plain form (info->precond_fallback = 1) unless
+ * LSQ_FLAG_NO_FALLBACK is set. */
 lsq_status lsq_solve(lsq_ctx* ctx, const lsq_problem* problem, const lsq_opts* opts, double* x, lsq_info* info,
                      void* stream);
 

@@ -27,7 +27,7 @@ STATUS = {0: "LSQ_OK", 1: "LSQ_PENDING", -1: "LSQ_ERR_ARG", -2: "LSQ_ERR_CUDA", 
 LSQ_ERR_NOCONV = -7
 PREC_FP64, PREC_MIXED = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
-FLAG_TIMING, FLAG_NO_CHECK, FLAG_NATIVE_FP64, FLAG_NO_IMAGE = 1, 2, 4, 8
+FLAG_TIMING, FLAG_NO_CHECK, FLAG_NATIVE_FP64, FLAG_NO_IMAGE, FLAG_NO_FALLBACK = 1, 2, 4, 8, 16
 
 EXPORTS = ("lsq_create", "lsq_destroy", "lsq_last_error", "lsq_status_string", "lsq_workspace_bytes",
            "lsq_sketch_indices", "lsq_sketch", "lsq_precond", "lsq_lsqr", "lsq_check", "lsq_solve",
@@ -56,7 +56,7 @@ class Info(ctypes.Structure):
                 ("normal_rel_est", ctypes.c_double), ("backward_error_ne", ctypes.c_double),
                 ("backward_error_pre", ctypes.c_double), ("rnorm", ctypes.c_double), ("arnorm", ctypes.c_double),
                 ("anorm_fro", ctypes.c_double), ("xnorm", ctypes.c_double), ("bnorm", ctypes.c_double),
-                ("sketch_rounds_max", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("sketch_rounds_max", ctypes.c_int32), ("precond_fallback", ctypes.c_int32),
                 ("t_sketch_ms", ctypes.c_float), ("t_precond_ms", ctypes.c_float), ("t_lsqr_ms", ctypes.c_float),
                 ("t_check_ms", ctypes.c_float), ("t_h2d_ms", ctypes.c_float), ("t_d2h_ms", ctypes.c_float)]
 
@@ -170,21 +170,27 @@ class Context:
                                                 _stream(stream)))
         return (idx, sgn, rnd) if with_rounds else (idx, sgn)
 
-    def lsq_sketch(self, A, b, d, zeta, seed, prec=PREC_FP64, stream=None):
+    def lsq_sketch(self, A, b, d, zeta, seed, prec=PREC_FP64, stream=None, ldy=None):
+        """Y = S [A | b]; returns a (d, n+1) view.  ldy (default: n+1 for FP64,
+        n+1 rounded up to 4 for FP32, which enables 4-wide reductions)."""
         import torch
         _dev_f64(A, "A")
         m, n, lda = _rowmajor(A)
         if b is not None:
             _dev_f64(b, "b")
         ncol = n + (b is not None)
-        Y = torch.empty((d, ncol), dtype=torch.float64 if prec == PREC_FP64 else torch.float32, device=A.device)
-        self._check(self.lib.lsq_sketch(self.h, _ptr(A), m, n, lda, _ptr(b), d, zeta, seed, prec, _ptr(Y), ncol,
+        if ldy is None:
+            ldy = ncol if prec == PREC_FP64 else (ncol + 3) // 4 * 4
+        Y = torch.empty((d, ldy), dtype=torch.float64 if prec == PREC_FP64 else torch.float32, device=A.device)
+        self._check(self.lib.lsq_sketch(self.h, _ptr(A), m, n, lda, _ptr(b), d, zeta, seed, prec, _ptr(Y), ldy,
                                         _stream(stream)))
-        return Y
+        return Y[:, :ncol]
 
-    def lsq_precond(self, Y, n, has_b=True, prec=PREC_FP64, want_R=True, stream=None):
+    def lsq_precond(self, Y, n, has_b=True, prec=None, want_R=True, stream=None):
         import torch
         d, ldy = Y.shape[0], Y.stride(0)
+        if prec is None:
+            prec = PREC_FP64 if Y.dtype == torch.float64 else PREC_MIXED
         dev = Y.device
         R = torch.empty((n, n), dtype=torch.float64, device=dev) if want_R else None
         M = torch.empty((n, n), dtype=torch.float64, device=dev)

@@ -335,7 +335,7 @@ lsq_status lsq_precond(lsq_ctx* ctx, const void* Y, int64_t d, int64_t n, int64_
   if ((s = ensure_ws(ctx, probe.off)) != LSQ_OK) return s;
   Carver cv{ctx->ws};
   PrecondBuffers buf;
-  buf.W = cv.take<double>((size_t)ncol * d);
+  buf.W = cv.take<double>((size_t)ncol * d);  // large enough for either precision
   buf.rdiag = cv.take<double>(n);
   buf.R = cv.take<double>((size_t)n * n);
   buf.Mt = cv.take<double>((size_t)n * n);
@@ -417,8 +417,8 @@ lsq_status lsq_check(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_
   return s;
 }
 
-lsq_status lsq_solve(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts* o, double* x, lsq_info* info,
-                     void* stream) {
+static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts* o, double* x, lsq_info* info,
+                             void* stream) {
   lsq_status s;
   if ((s = check_ctx(ctx)) != LSQ_OK) return s;
   if (!pr || !o || !x) return fail(ctx, LSQ_ERR_ARG, "null problem, options or x");
@@ -433,7 +433,8 @@ lsq_status lsq_solve(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts* o, dou
   const bool host = pr->mem == LSQ_MEM_HOST;
   const bool timing = (o->flags & LSQ_FLAG_TIMING) != 0;
   const int ni = (int)n, npad = (int)((n + 31) / 32 * 32);
-  const int64_t ncol = n + 1, ldy = ncol;
+  // the mixed form's 4-wide FP32 reductions want rows of Y padded to 4 floats
+  const int64_t ncol = n + 1, ldy = o->prec == LSQ_PREC_MIXED ? (ncol + 3) / 4 * 4 : ncol;
   const size_t yes = o->prec == LSQ_PREC_FP64 ? 8 : 4;
   const int64_t lda_dev = host ? n : lda;
   const bool vec = host ? (n % 2 == 0) : vec_ok(pr->A, lda);
@@ -552,6 +553,27 @@ lsq_status lsq_solve(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts* o, dou
   }
   if (timing)
     for (auto& e : ev) cudaEventDestroy(e);
+  return s;
+}
+
+// Mixed form: FP32 sketch and QR give a good preconditioner only while
+// cond(A) * u_fp32 * sqrt(m zeta / d) stays well below 1.  The mixed solve is
+// therefore capped at twice the iteration count the Sec. 4.3 rate estimate
+// predicts; if the cap is hit, the plain FP64 form solves the problem again.
+lsq_status lsq_solve(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts* o, double* x, lsq_info* info,
+                     void* stream) {
+  if (!o || o->prec != LSQ_PREC_MIXED || (o->flags & LSQ_FLAG_NO_FALLBACK) || !pr)
+    return solve_once(ctx, pr, o, x, info, stream);
+  lsq_opts om = *o;
+  const int64_t full = o->maxit > 0 ? o->maxit : default_maxit(pr->n, o->d, o->tol);
+  const int64_t cap = 2 * (default_maxit(pr->n, o->d, o->tol) / 10) + 5;
+  om.maxit = cap < full ? cap : full;
+  lsq_status s = solve_once(ctx, pr, &om, x, info, stream);
+  if (s != LSQ_ERR_NOCONV || om.maxit == full) return s;
+  lsq_opts op = *o;
+  op.prec = LSQ_PREC_FP64;
+  s = solve_once(ctx, pr, &op, x, info, stream);
+  if (info) info->precond_fallback = 1;
   return s;
 }
 

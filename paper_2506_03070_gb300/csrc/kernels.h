@@ -17,7 +17,7 @@ cudaError_t sketch_apply(const double* A, int64_t m, int64_t n, int64_t lda, con
 
 // Preconditioner (qr.cu).  W: FP64 column-major working copy, ncol x d.
 struct PrecondBuffers {
-  double* W;       // ncol * d
+  void* W;         // ncol * d working copy (double, or float for the mixed form)
   double* rdiag;   // n
   double* R;       // n * n, row-major R when the caller passes none
   double* Mt;      // n * n, row-major transpose of M (working buffer)

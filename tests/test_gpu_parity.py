@@ -66,13 +66,56 @@ def test_sketch_apply_fp64(ctx, orc, m, n, d, zeta, has_b):
     assert np.max(np.abs(Y - Yo)) <= tol, np.max(np.abs(Y - Yo))
 
 
-def test_sketch_apply_mixed_fp32(ctx, orc):
+@pytest.mark.parametrize("ldy_pad", [None, 201])
+def test_sketch_apply_mixed_fp32(ctx, orc, ldy_pad):
+    """FP32 accumulation (mixed form): 4-wide vector reductions when rows of Y
+    are padded to 4 floats (default), scalar reductions otherwise."""
     A, b, _ = _problem(20000, 200, 1e8, 3)
-    Y = ctx.lsq_sketch(_dev(A), _dev(b), 800, 8, 9, prec=1).cpu().numpy().astype(np.float64)
+    Y = ctx.lsq_sketch(_dev(A), _dev(b), 800, 8, 9, prec=1, ldy=ldy_pad).cpu().numpy().astype(np.float64)
     Yo = orc.sketch_apply(A, b, 800, 8, 9)
     # FP32 accumulation of ~200 terms: relative error ~ 200 * 6e-8 of the entry scale
     scale = np.abs(Yo).max()
     assert np.max(np.abs(Y - Yo)) <= 2e-5 * scale
+
+
+def test_precond_fp32_from_fp32_sketch(ctx, orc):
+    """Mixed form: FP32 sketch and FP32 Householder QR still precondition a
+    cond-1e6 problem to cond(AM) near the FP64 value (same iterations +-2)."""
+    A, b, _ = _problem(6000, 64, 1e6, 31)
+    Y32 = ctx.lsq_sketch(_dev(A), _dev(b), 256, 8, 5, prec=1)
+    R, M, x0 = ctx.lsq_precond(Y32, 64, has_b=True)
+    M = M.cpu().numpy()
+    sv = np.linalg.svd(A @ M, compute_uv=False)
+    Yo = orc.sketch_apply(A, b, 256, 8, 5)
+    Ro, _, _ = orc.householder_qr(Yo)
+    svo = np.linalg.svd(A @ orc.tri_inverse(Ro[:64, :64]), compute_uv=False)
+    assert sv[0] / sv[-1] <= 1.05 * svo[0] / svo[-1]
+    Mo = orc.tri_inverse(Ro[:64, :64])
+    assert np.linalg.norm(A @ (x0.cpu().numpy() - Mo @ Ro[:64, 64])) <= 1e-5 * np.linalg.norm(b)
+
+
+def test_solve_mixed_falls_back_when_fp32_sketch_is_too_coarse(ctx, orc):
+    """cond 1e12: the FP32 sketch cannot precondition; the mixed solve stalls,
+    re-solves in FP64 and still meets the accuracy bar."""
+    A, b, xt = _problem(20000, 64, 1e12, 43)
+    x, info = ctx.lsq_solve(_dev(A), _dev(b), 256, seed=3, tol=1e-12, prec=1)
+    assert info["status"] == 0 and info["precond_fallback"] == 1
+    assert orc.backward_error_kw(A, b, x.cpu().numpy()) <= 1e-10
+    import paper_2506_03070_gb300 as P
+    with pytest.raises(P.LsqError) as e:
+        ctx.lsq_solve(_dev(A), _dev(b), 256, seed=3, tol=1e-12, prec=1, flags=P.FLAG_NO_FALLBACK)
+    assert e.value.status == -7
+
+
+def test_solve_mixed_matches_plain(ctx, orc):
+    A, b, xt = _problem(30000, 128, 1e7, 41)
+    xp, ip = ctx.lsq_solve(_dev(A), _dev(b), 512, seed=3, tol=1e-12, prec=0)
+    xm, im = ctx.lsq_solve(_dev(A), _dev(b), 512, seed=3, tol=1e-12, prec=1)
+    assert im["precond_fallback"] == 0
+    bn = np.linalg.norm(b)
+    assert abs(ip["iters"] - im["iters"]) <= 2
+    assert np.linalg.norm(A @ (xm.cpu().numpy() - xp.cpu().numpy())) <= 1e-10 * bn
+    assert orc.backward_error_kw(A, b, xm.cpu().numpy()) <= 1e-10
 
 
 def test_sketch_apply_row_stride(ctx, orc):
