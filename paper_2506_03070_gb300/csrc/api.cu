@@ -137,7 +137,7 @@ struct LsqrWork {
 
 LsqrWork carve_lsqr(Carver& cv, int64_t m, int n, int npad, int grid, bool image = false) {
   LsqrWork w;
-  w.image = image ? cv.take<float2>((size_t)m * n) : nullptr;
+  w.image = image ? cv.take<float2>((size_t)m * ((n + 1) / 2 * 2)) : nullptr;
   w.u = cv.take<double>((size_t)m);
   w.v = cv.take<double>(npad);
   w.vhat = cv.take<double>(npad);
@@ -179,6 +179,9 @@ lsq_status run_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int n, int64_t lda
   p.lda = lda;
   p.b = b;
   p.asplit = native ? nullptr : w.image;
+  p.ldi = (n + 1) / 2 * 2;
+  p.vec = vec_ok(A, lda);
+  p.a_ring = p.vec && (n % 2 == 0);
   p.M = M;
   p.Mt = Mt;
   p.x = x;
@@ -361,14 +364,22 @@ lsq_status lsq_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t
   if (n > 512) return fail(ctx, LSQ_ERR_UNSUPPORTED, "LSQR kernel built for n <= 512");
   cudaStream_t st = (cudaStream_t)stream;
   const int ni = (int)n, npad = (int)((n + 31) / 32 * 32);
-  const bool native = (flags & LSQ_FLAG_NATIVE_FP64) || !lsqr_df_ok(A, n, lda);
-  const int grid = lsqr_grid(ni, vec_ok(A, lda), native, ctx->sms);
+  bool native = (flags & LSQ_FLAG_NATIVE_FP64) || !lsqr_df_ok(A, n, lda);
+  int grid = lsqr_grid(ni, vec_ok(A, lda), native, ctx->sms);
   if (grid < 1) return fail(ctx, LSQ_ERR_CUDA, "no launchable LSQR configuration");
   bool image = !native && !(flags & LSQ_FLAG_NO_IMAGE);
   Carver probe{nullptr};
   carve_lsqr(probe, m, ni, npad, grid, image);
   if (image && probe.off > ctx->budget) {
     image = false;  // fall back to splitting A on the fly in every pass
+    probe = Carver{nullptr};
+    carve_lsqr(probe, m, ni, npad, grid, false);
+  }
+  if (!native && !image && !(vec_ok(A, lda) && n % 2 == 0)) {
+    // without the image every pass streams A through the bulk-copy ring,
+    // which needs even n and lda and an aligned A
+    native = true;
+    grid = lsqr_grid(ni, vec_ok(A, lda), native, ctx->sms);
     probe = Carver{nullptr};
     carve_lsqr(probe, m, ni, npad, grid, false);
   }
@@ -439,9 +450,8 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
   const int64_t lda_dev = host ? n : lda;
   const bool vec = host ? (n % 2 == 0) : vec_ok(pr->A, lda);
   // host problems are copied into 256-byte aligned workspace with lda = n
-  const bool native = (o->flags & LSQ_FLAG_NATIVE_FP64) || !(host ? (n % 2 == 0 && n <= 512)
-                                                                  : lsqr_df_ok(pr->A, n, lda));
-  const int grid = lsqr_grid(ni, vec, native, ctx->sms);
+  bool native = (o->flags & LSQ_FLAG_NATIVE_FP64) || !lsqr_df_ok(pr->A, n, lda);
+  int grid = lsqr_grid(ni, vec, native, ctx->sms);
   if (grid < 1) return fail(ctx, LSQ_ERR_CUDA, "no launchable LSQR configuration");
   const int64_t maxit = o->maxit > 0 ? o->maxit : default_maxit(n, d, o->tol);
 
@@ -477,6 +487,17 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
     carve(probe, &A0, &b0, &x0, &Y0, &pb0, &R0, &M0, &lw0);
     if (image && probe.off > ctx->budget) {
       image = false;  // no room for the float-pair image: split A on the fly
+      if (!(vec && n % 2 == 0)) {
+        // every pass would stream A through the bulk-copy ring: needs even n, lda
+        native = true;
+        grid = lsqr_grid(ni, vec, native, ctx->sms);
+      }
+      probe = Carver{nullptr};
+      carve(probe, &A0, &b0, &x0, &Y0, &pb0, &R0, &M0, &lw0);
+    }
+    if (!native && !image && !(vec && n % 2 == 0)) {
+      native = true;
+      grid = lsqr_grid(ni, vec, native, ctx->sms);
       probe = Carver{nullptr};
       carve(probe, &A0, &b0, &x0, &Y0, &pb0, &R0, &M0, &lw0);
     }

@@ -38,7 +38,10 @@ struct LsqrParams {
   int npad;
   int64_t lda;
   const double* b;
-  float2* asplit;    // m x n (hi, mid) float-pair image of A written by the first pass, or null
+  float2* asplit;    // m x ldi (hi, mid) float-pair image of A written by the first pass, or null
+  int64_t ldi;       // image row length: n rounded up to even
+  bool a_ring;       // A rows can come through bulk copies (n even, lda even, A 16-byte aligned)
+  bool vec;          // A rows allow 16-byte vector loads (lda even, A aligned)
   const double* M;   // n x n row-major (upper triangular), may be null in check mode
   const double* Mt;  // transpose of M, row-major
   double* x;         // in: start, out: solution
@@ -54,6 +57,7 @@ struct LsqrParams {
   double tol;
   int64_t maxit;
   int mode;          // 0 = LSQR then check, 1 = check only, 2 = LSQR only
+  int gidx, gcount;  // this block's index among the blocks sharing the problem (set in-kernel)
   GridBarrier* bar;
   uint32_t* status;
   double* out;       // kOutSlots doubles of results

@@ -25,6 +25,16 @@ constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 constexpr int kNbuf = 3;  // bulk-copy ring depth per warp (rows in flight)
 
+// Barrier over the blocks that share one problem: the whole grid (grid
+// barrier with timeout) or a single block (batched problems).
+__device__ __forceinline__ bool group_sync(const LsqrParams& p) {
+  if (p.gcount == 1) {
+    __syncthreads();
+    return true;
+  }
+  return grid_sync(p.bar, p.status);
+}
+
 // --------------------------------------------------------------------------
 // The pass over A.  Block `blk` owns rows [m*blk/G, m*(blk+1)/G); its warp k
 // takes rows start+k, start+k+8, ...  Lane l holds columns 2l+64t, 2l+64t+1
@@ -38,7 +48,7 @@ __device__ void pass_native(const LsqrParams& p, const double* __restrict__ wvec
                             const double* __restrict__ uin, double gamma, double* __restrict__ uout, double* s_g,
                             double* s_scal) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int G = gridDim.x, blk = blockIdx.x;
+  const int G = p.gcount, blk = p.gidx;
   const int n = p.n;
   const int64_t r0 = (p.m * blk) / G, r1 = (p.m * (blk + 1)) / G;
   double wr[2 * T], g[2 * T];
@@ -126,15 +136,15 @@ struct NativePass {
   double* s_g;
   double* s_scal;
   __device__ void init(LsqrParams& p) {  // y = b - A x0 -> u; sum y^2, sum b^2
-    p.gparts = gridDim.x;
+    p.gparts = p.gcount;
     pass_native<T, VEC, false, true>(p, p.x, -1.0, p.b, -1.0, p.u, s_g, s_scal);
   }
   __device__ void iter(LsqrParams& p, double gamma) {  // y = A wv - gamma u -> u
-    p.gparts = gridDim.x;
+    p.gparts = p.gcount;
     pass_native<T, VEC, false, false>(p, p.wv, 1.0, p.u, gamma, p.u, s_g, s_scal);
   }
   __device__ void check(LsqrParams& p) {  // y = b - A x; sum y^2, b^2, A_ij^2
-    p.gparts = gridDim.x;
+    p.gparts = p.gcount;
     pass_native<T, VEC, true, true>(p, p.x, -1.0, p.b, -1.0, nullptr, s_g, s_scal);
   }
 };
@@ -144,8 +154,8 @@ struct NativePass {
 // then a fixed-order block reduction (deterministic for a given grid).
 __device__ void reduce_g(const LsqrParams& p) {
   __shared__ double scratch[32];
-  const int G = gridDim.x;
-  for (int j = blockIdx.x; j < p.n; j += G) {
+  const int G = p.gcount;
+  for (int j = p.gidx; j < p.n; j += G) {
     double s = 0.0;
     for (int c = threadIdx.x; c < p.gparts; c += kThreads) s += p.gpart[(int64_t)c * p.npad + j];
     s = block_sum(s, scratch);
@@ -159,7 +169,7 @@ __device__ void reduce_g(const LsqrParams& p) {
 __device__ double sum_part(const LsqrParams& p, int slot) {
   __shared__ double scratch[32];
   double s = 0.0;
-  for (int c = threadIdx.x; c < (int)gridDim.x; c += kThreads) s += p.part[(int64_t)c * 4 + slot];
+  for (int c = threadIdx.x; c < p.gcount; c += kThreads) s += p.part[(int64_t)c * 4 + slot];
   return block_sum(s, scratch);
 }
 
@@ -167,7 +177,7 @@ __device__ double sum_part(const LsqrParams& p, int slot) {
 // vhat_k^2 into part[blk][slot].  M^T g uses rows of Mt (contiguous).
 __device__ void mt_apply(const LsqrParams& p, double ginv, double cv, int slot, double* s_scal) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int gw = blockIdx.x * kWarps + wib, nw = gridDim.x * kWarps;
+  const int gw = p.gidx * kWarps + wib, nw = p.gcount * kWarps;
   double acc = 0.0;
   for (int k = gw; k < p.n; k += nw) {
     const double* mk = p.Mt + (int64_t)k * p.n;
@@ -183,7 +193,7 @@ __device__ void mt_apply(const LsqrParams& p, double ginv, double cv, int slot, 
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < kWarps; ++w) s += s_scal[w];
-    p.part[(int64_t)blockIdx.x * 4 + slot] = s;
+    p.part[(int64_t)p.gidx * 4 + slot] = s;
   }
   __syncthreads();
 }
@@ -191,7 +201,7 @@ __device__ void mt_apply(const LsqrParams& p, double ginv, double cv, int slot, 
 // v = vhat * ainv; wv = M v; x += cx * w; w = wv - cw * w  (one warp per row i)
 __device__ void m_apply_update(const LsqrParams& p, double ainv, double cx, double cw, bool first) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int gw = blockIdx.x * kWarps + wib, nw = gridDim.x * kWarps;
+  const int gw = p.gidx * kWarps + wib, nw = p.gcount * kWarps;
   for (int i = gw; i < p.n; i += nw) {
     const double* mi = p.M + (int64_t)i * p.n;
     double s = 0.0;
@@ -242,15 +252,16 @@ struct DfPass {
   double* s_scal;
   uint32_t seq;     // rows this warp has consumed so far (all passes)
 
-  // Row source: the FP64 matrix, or its (hi, mid) float-pair image (same bytes per row).
+  // Row source: the FP64 matrix (n even, lda even, A aligned), or its
+  // (hi, mid) float-pair image (ldi entries per row, ldi even).
   template <bool FROM_IMAGE>
   __device__ void issue(const LsqrParams& p, int64_t r0, int wib, uint32_t j, double* myring, uint64_t* mybars) {
     const int64_t row = r0 + (int64_t)wib + (int64_t)kWarps * j;
     const uint32_t s = seq + j, b = s % kNbuf;
-    const uint32_t rb = (uint32_t)p.n * 8u;
-    const void* src = FROM_IMAGE ? (const void*)(p.asplit + row * p.n) : (const void*)(p.A + row * p.lda);
+    const uint32_t rb = (uint32_t)(FROM_IMAGE ? p.ldi : p.n) * 8u;
+    const void* src = FROM_IMAGE ? (const void*)(p.asplit + row * p.ldi) : (const void*)(p.A + row * p.lda);
     mbar_arrive_expect_tx(mybars + b, rb);
-    bulk_g2s(myring + (size_t)b * p.n, src, rb, mybars + b);
+    bulk_g2s(myring + (size_t)b * p.ldi, src, rb, mybars + b);
   }
 
   // Wait (bounded) for the buffer of row j.  Returns false on timeout (warp-uniform).
@@ -270,17 +281,20 @@ struct DfPass {
     return !__any_sync(0xffffffffu, timed_out);
   }
 
-  // FROM_IMAGE: rows come from the float-pair image; else from A (split on
-  // the fly) and, when WRITE_IMAGE, the split rows are stored to the image.
+  // FROM_IMAGE: rows come from the float-pair image through the ring; else
+  // from A (split on the fly) -- through the ring when p.a_ring, by direct
+  // loads otherwise (odd n or lda, unaligned A) -- and, when WRITE_IMAGE, the
+  // split rows are stored to the image.
   template <bool UIN_B, bool UIN2, bool STORE, bool FROM_IMAGE, bool WRITE_IMAGE>
   __device__ void run(const LsqrParams& p, const double* __restrict__ wvec, double wsign, double gamma) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int G = gridDim.x, blk = blockIdx.x;
+    const int G = p.gcount, blk = p.gidx;
     const int n = p.n;
     const int64_t r0 = (p.m * blk) / G, r1 = (p.m * (blk + 1)) / G;
     const int64_t nrows = r1 - r0;
     const uint32_t count = nrows > wib ? (uint32_t)((nrows - wib + kWarps - 1) / kWarps) : 0u;
-    double* myring = ring + (size_t)wib * kNbuf * n;
+    const bool use_ring = FROM_IMAGE || p.a_ring;
+    double* myring = ring + (size_t)wib * kNbuf * p.ldi;
     uint64_t* mybars = bars + wib * kNbuf;
     float2* ubuf = reinterpret_cast<float2*>(p.u);
     double* gw = p.gpart + ((int64_t)blk * kWarps + wib) * p.npad;
@@ -302,19 +316,19 @@ struct DfPass {
     df ss{0.f, 0.f}, bb{0.f, 0.f};
     bool first_flush = true;
 
-    if (lane == 0) {
+    if (lane == 0 && use_ring) {
       fence_proxy_async_smem();
       for (uint32_t j = 0; j < count && j < (uint32_t)kNbuf; ++j) issue<FROM_IMAGE>(p, r0, wib, j, myring, mybars);
     }
     bool ok = true;
     uint32_t j = 0;
     for (; j < count; ++j) {
-      if (!wait(j, mybars)) {
+      if (use_ring && !wait(j, mybars)) {
         ok = false;
         break;
       }
       const int64_t row = r0 + (int64_t)wib + (int64_t)kWarps * j;
-      const double* buf = myring + (size_t)((seq + j) % kNbuf) * n;
+      const double* buf = myring + (size_t)((seq + j) % kNbuf) * p.ldi;
       // u_i (or b_i) is needed only after the row dot: load it first
       double bi = 0.0;
       float2 uu = make_float2(0.f, 0.f);
@@ -335,16 +349,22 @@ struct DfPass {
           mm[2 * t + 1] = v.w;
         } else {
           double2 v = make_double2(0.0, 0.0);
-          if (c < n) v = *reinterpret_cast<const double2*>(buf + c);
+          if (p.a_ring) {
+            if (c < n) v = *reinterpret_cast<const double2*>(buf + c);
+          } else {
+            const double* Ar = p.A + row * p.lda;
+            if (c < n) v.x = __ldcs(Ar + c);
+            if (c + 1 < n) v.y = __ldcs(Ar + c + 1);
+          }
           split2(v.x, h[2 * t], mm[2 * t]);
           split2(v.y, h[2 * t + 1], mm[2 * t + 1]);
           if (WRITE_IMAGE && c < n)
-            *reinterpret_cast<float4*>(p.asplit + row * n + c) = make_float4(h[2 * t], mm[2 * t], h[2 * t + 1],
-                                                                             mm[2 * t + 1]);
+            *reinterpret_cast<float4*>(p.asplit + row * p.ldi + c) = make_float4(h[2 * t], mm[2 * t], h[2 * t + 1],
+                                                                                 mm[2 * t + 1]);
         }
       }
       __syncwarp();
-      if (lane == 0 && j + kNbuf < count) {
+      if (lane == 0 && use_ring && j + kNbuf < count) {
         fence_proxy_async_smem();
         issue<FROM_IMAGE>(p, r0, wib, j + kNbuf, myring, mybars);
       }
@@ -397,7 +417,7 @@ struct DfPass {
       }
       for (uint32_t k = j; k < count && k < j + kNbuf; ++k) wait(k, mybars);
     }
-    seq += count;
+    if (use_ring) seq += count;  // ring phases advance only when rows went through it
 #pragma unroll
     for (int t = 0; t < T; ++t) {
       const int c = 2 * lane + 64 * t;
@@ -423,7 +443,7 @@ struct DfPass {
   }
 
   __device__ void init(LsqrParams& p) {
-    p.gparts = gridDim.x * kWarps;
+    p.gparts = p.gcount * kWarps;
     if (p.asplit) {
       run<true, true, true, false, true>(p, p.x, -1.0, -1.0);
       // the image was written through the generic proxy and is read by bulk
@@ -434,7 +454,7 @@ struct DfPass {
     }
   }
   __device__ void iter(LsqrParams& p, double gamma) {
-    p.gparts = gridDim.x * kWarps;
+    p.gparts = p.gcount * kWarps;
     if (p.asplit)
       run<false, false, true, true, false>(p, p.wv, 1.0, gamma);
     else
@@ -444,8 +464,11 @@ struct DfPass {
   // path applies) with per-block partials; the ring doubles as its
   // block-reduction scratch.
   __device__ void check(LsqrParams& p) {
-    p.gparts = gridDim.x;
-    pass_native<T, true, true, true>(p, p.x, -1.0, p.b, -1.0, nullptr, ring, s_scal);
+    p.gparts = p.gcount;
+    if (p.vec)
+      pass_native<T, true, true, true>(p, p.x, -1.0, p.b, -1.0, nullptr, ring, s_scal);
+    else
+      pass_native<T, false, true, true>(p, p.x, -1.0, p.b, -1.0, nullptr, ring, s_scal);
   }
 };
 
@@ -462,14 +485,14 @@ __device__ void lsqr_body(LsqrParams& p, Pass& pass, double* s_scal) {
   if (p.mode != 1) {
     // ---- beta_1 u_1 = b - A x0
     pass.init(p);
-    if (!grid_sync(p.bar, status)) return;
+    if (!group_sync(p)) return;
     reduce_g(p);
-    if (!grid_sync(p.bar, status)) return;
+    if (!group_sync(p)) return;
     beta = sqrt(sum_part(p, 0));
     bnorm = sqrt(sum_part(p, 1));
     // ---- alpha_1 v_1 = M^T A^T u_1
     mt_apply(p, beta > 0.0 ? 1.0 / beta : 0.0, 0.0, 2, s_scal);
-    if (!grid_sync(p.bar, status)) return;
+    if (!group_sync(p)) return;
     alpha = sqrt(sum_part(p, 2));
     // ---- w_1 = M v_1
     m_apply_update(p, alpha > 0.0 ? 1.0 / alpha : 0.0, 0.0, 0.0, true);
@@ -477,7 +500,7 @@ __device__ void lsqr_body(LsqrParams& p, Pass& pass, double* s_scal) {
     phibar = beta;
     anorm2 = alpha * alpha;
     if (beta == 0.0 || alpha == 0.0) stop = 4;
-    if (!grid_sync(p.bar, status)) return;
+    if (!group_sync(p)) return;
 
     while (stop == 0) {
       if (iters >= p.maxit) {
@@ -487,13 +510,13 @@ __device__ void lsqr_body(LsqrParams& p, Pass& pass, double* s_scal) {
       ++iters;
       // uhat_{t+1} = A (M v_t) - alpha_t u_t = A wv - (alpha/beta) uhat_t
       pass.iter(p, alpha / beta);
-      if (!grid_sync(p.bar, status)) return;
+      if (!group_sync(p)) return;
       reduce_g(p);
-      if (!grid_sync(p.bar, status)) return;
+      if (!group_sync(p)) return;
       const double beta1 = sqrt(sum_part(p, 0));
       // vhat_{t+1} = M^T A^T uhat / beta_{t+1} - beta_{t+1} v_t
       mt_apply(p, beta1 > 0.0 ? 1.0 / beta1 : 0.0, beta1, 2, s_scal);
-      if (!grid_sync(p.bar, status)) return;
+      if (!group_sync(p)) return;
       const double a2 = sum_part(p, 2);
       const double alpha1 = beta1 > 0.0 ? sqrt(a2) : 0.0;
       // Givens rotation
@@ -511,12 +534,12 @@ __device__ void lsqr_body(LsqrParams& p, Pass& pass, double* s_scal) {
       if (normal_rel <= p.tol) stop = 1;
       else if (phibar <= p.tol * bnorm) stop = 2;
       else if (beta == 0.0 || alpha == 0.0) stop = 4;
-      if (!grid_sync(p.bar, status)) return;
+      if (!group_sync(p)) return;
     }
   }
 
   if (p.mode == 2) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (p.gidx == 0 && threadIdx.x == 0) {
       p.out[OUT_ITERS] = (double)iters;
       p.out[OUT_STOP] = (double)stop;
       p.out[OUT_NORMAL_REL] = normal_rel;
@@ -528,12 +551,12 @@ __device__ void lsqr_body(LsqrParams& p, Pass& pass, double* s_scal) {
   }
   // ---- accuracy pass: y = b - A x, g = A^T y, ||A||_F
   pass.check(p);
-  if (!grid_sync(p.bar, status)) return;
+  if (!group_sync(p)) return;
   reduce_g(p);
-  if (!grid_sync(p.bar, status)) return;
+  if (!group_sync(p)) return;
   if (p.M) mt_apply(p, 1.0, 0.0, 3, s_scal);
-  if (!grid_sync(p.bar, status)) return;
-  if (blockIdx.x == 0) {
+  if (!group_sync(p)) return;
+  if (p.gidx == 0) {
     __shared__ double scratch[32];
     double gx = 0.0, xx = 0.0;
     for (int j = threadIdx.x; j < p.n; j += kThreads) {
@@ -570,6 +593,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_native(LsqrParams p) {
   __shared__ double s_g[kWarps * 64 * T];
   __shared__ double s_scal[kWarps * 4];
   NativePass<T, VEC> pass{s_g, s_scal};
+  p.gidx = blockIdx.x;
+  p.gcount = gridDim.x;
   lsqr_body(p, pass, s_scal);
 }
 
@@ -584,11 +609,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_df(LsqrParams p) {
   }
   __syncthreads();
   DfPass<T> pass{s_ring, s_bars, s_scal, 0u};
+  p.gidx = blockIdx.x;
+  p.gcount = gridDim.x;
   lsqr_body(p, pass, s_scal);
 }
 
 size_t df_smem(int T, int n) {
-  const size_t ring = (size_t)kWarps * kNbuf * n * sizeof(double);
+  const size_t ring = (size_t)kWarps * kNbuf * (size_t)((n + 1) / 2 * 2) * sizeof(double);
   const size_t red = (size_t)kWarps * 64 * T * sizeof(double);
   return ring > red ? ring : red;
 }
@@ -646,7 +673,9 @@ int chunks_for(int n) {
 int lsqr_gparts(int grid) { return grid * kWarps; }
 
 bool lsqr_df_ok(const double* A, int64_t n, int64_t lda) {
-  return n % 2 == 0 && lda % 2 == 0 && ((uintptr_t)A % 16 == 0) && chunks_for((int)n) > 0;
+  (void)A;
+  (void)lda;
+  return chunks_for((int)n) > 0;
 }
 
 int lsqr_grid(int n, bool vec, bool native, int sms) {
