@@ -192,6 +192,39 @@ lsq_status lsq_check_noalloc(const double* A, int64_t m, int64_t n, int64_t lda,
 lsq_status lsq_solve(lsq_ctx* ctx, const lsq_problem* problem, const lsq_opts* opts, double* x, lsq_info* info,
                      void* stream);
 
+/* ---- Batched solves -------------------------------------------------------
+ * Many independent problems in one persistent launch: every block takes whole
+ * problems from a device work counter (largest m*n first) and runs all of
+ * Algorithm 1 for each by itself (sketch, Householder QR, M, x0, LSQR with
+ * block barriers).  A, b and x of every item are device pointers; x receives
+ * the solution.  Limits per item: 1 <= n <= 512, n+1 <= d, 1 <= zeta <= 8.
+ * The LSQR pass processes 32/L rows per warp with L lanes per row; L is picked
+ * per n-range by the context's autotuner (LSQ_FLAG_AUTOTUNE times the
+ * candidate shapes on the largest problems of the batch the first time an
+ * n-range is seen, and keeps the fastest).  results may be NULL. */
+typedef struct {
+  const double* A;
+  const double* b;
+  double* x;
+  int64_t m, n, lda;
+  int64_t d;
+  int32_t zeta;
+  int32_t reserved;
+  uint64_t seed;
+} lsq_batch_item;
+
+typedef struct {
+  int32_t status; /* per-problem lsq_status */
+  int32_t stop;
+  int64_t iters;
+  double backward_error_ne, rnorm, anorm_fro, xnorm, bnorm;
+} lsq_batch_result;
+
+#define LSQ_FLAG_AUTOTUNE 32 /* lsq_solve_batch: tune the LSQR pass shape for new n-ranges */
+
+lsq_status lsq_solve_batch(lsq_ctx* ctx, const lsq_batch_item* items, int64_t count, double tol, int64_t maxit,
+                           int32_t flags, lsq_batch_result* results, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

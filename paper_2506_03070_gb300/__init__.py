@@ -31,7 +31,7 @@ FLAG_TIMING, FLAG_NO_CHECK, FLAG_NATIVE_FP64, FLAG_NO_IMAGE, FLAG_NO_FALLBACK = 
 
 EXPORTS = ("lsq_create", "lsq_destroy", "lsq_last_error", "lsq_status_string", "lsq_workspace_bytes",
            "lsq_sketch_indices", "lsq_sketch", "lsq_precond", "lsq_lsqr", "lsq_check", "lsq_solve",
-           "lsq_check_noalloc")
+           "lsq_check_noalloc", "lsq_solve_batch")
 
 
 class LsqError(RuntimeError):
@@ -64,6 +64,23 @@ class Info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("b", ctypes.c_void_p), ("x", ctypes.c_void_p), ("m", ctypes.c_int64),
+                ("n", ctypes.c_int64), ("lda", ctypes.c_int64), ("d", ctypes.c_int64), ("zeta", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class BatchResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("stop", ctypes.c_int32), ("iters", ctypes.c_int64),
+                ("backward_error_ne", ctypes.c_double), ("rnorm", ctypes.c_double), ("anorm_fro", ctypes.c_double),
+                ("xnorm", ctypes.c_double), ("bnorm", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+FLAG_AUTOTUNE = 32
+
 _lib = None
 
 
@@ -92,6 +109,8 @@ def load(path: str = LIB_PATH):
     L.lsq_solve.argtypes = [P, ctypes.POINTER(Problem), ctypes.POINTER(Opts), P, ctypes.POINTER(Info), P]
     L.lsq_check_noalloc.argtypes = [P, i64, i64, i64, P, P, P, ctypes.POINTER(Info), P]
     L.lsq_check_noalloc.restype = i32
+    L.lsq_solve_batch.argtypes = [P, ctypes.POINTER(BatchItem), i64, f64, i64, i32, ctypes.POINTER(BatchResult), P]
+    L.lsq_solve_batch.restype = i32
     for name in ("lsq_create", "lsq_destroy", "lsq_sketch_indices", "lsq_sketch", "lsq_precond", "lsq_lsqr",
                  "lsq_check", "lsq_solve"):
         getattr(L, name).restype = i32
@@ -218,6 +237,17 @@ class Context:
                                        _stream(stream)))
         return info.as_dict()
 
+    def lsq_solve_batch(self, problems, tol=1e-12, maxit=0, flags=0, stream=None, raise_on_error=True):
+        """Solve many problems in one persistent launch.  problems: list of
+        dicts with CUDA float64 tensors A (m x n, row-major), b and optional d
+        (default 4n), zeta (default 8), seed, x.  Returns (xs, results)."""
+        items, xs = _batch_items(problems)
+        res = (BatchResult * len(problems))()
+        st = self.lib.lsq_solve_batch(self.h, items, len(problems), tol, maxit, flags, res, _stream(stream))
+        if raise_on_error:
+            self._check(st)
+        return xs, [r.as_dict() for r in res]
+
     def lsq_solve(self, A, b, d, zeta=8, seed=0, tol=1e-12, maxit=0, prec=PREC_FP64, flags=0, x=None, stream=None,
                   allow_noconv=False):
         """Algorithm 1 end to end.  A, b: CUDA float64 tensors (device
@@ -263,6 +293,24 @@ def lsq_check_noalloc(A, b, x, M=None, stream=None):
     if st != LSQ_OK:
         raise LsqError(st, "lsq_check_noalloc failed (n > 512 or CUDA error)")
     return info.as_dict()
+
+
+def _batch_items(problems):
+    import torch
+    items = (BatchItem * len(problems))()
+    xs = []
+    for i, pr in enumerate(problems):
+        A, b = pr["A"], pr["b"]
+        _dev_f64(A, "A")
+        _dev_f64(b, "b")
+        m, n, lda = _rowmajor(A)
+        x = pr.get("x")
+        if x is None:
+            x = torch.empty((n,), dtype=torch.float64, device=A.device)
+        xs.append(x)
+        items[i] = BatchItem(_ptr(A), _ptr(b), _ptr(x), m, n, lda, pr.get("d", 4 * n), pr.get("zeta", 8), 0,
+                             pr.get("seed", 0))
+    return items, xs
 
 
 _default = {}

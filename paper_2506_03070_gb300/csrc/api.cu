@@ -1,8 +1,10 @@
 // api.cu -- the C ABI declared in include/lsq.h: context, workspace under an
 // HBM budget, argument checking, status mapping and the Algorithm 1 chain
 // sketch -> preconditioner -> LSQR -> accuracy pass on one stream.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <vector>
 #include <cstring>
 #include <string>
 
@@ -25,6 +27,8 @@ struct lsq_ctx {
   double* d_out = nullptr;
   // pinned host mirror of the small words
   void* h_small = nullptr;
+  // batched solves: tuned LSQR pass shapes per n-range
+  BatchTuning* tuning = nullptr;
 };
 
 namespace {
@@ -182,6 +186,7 @@ lsq_status run_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int n, int64_t lda
   p.ldi = (n + 1) / 2 * 2;
   p.vec = vec_ok(A, lda);
   p.a_ring = p.vec && (n % 2 == 0);
+  p.check_df = false;
   p.M = M;
   p.Mt = Mt;
   p.x = x;
@@ -244,6 +249,7 @@ lsq_status lsq_create(lsq_ctx** out, int device, size_t hbm_budget_bytes) {
     return LSQ_ERR_OOM;
   }
   cudaMemset(small, 0, kSmallBytes);
+  ctx->tuning = batch_tuning_new();
   *out = ctx;
   return LSQ_OK;
 }
@@ -254,6 +260,7 @@ lsq_status lsq_destroy(lsq_ctx* ctx) {
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->h_small) cudaFreeHost(ctx->h_small);
+  if (ctx->tuning) batch_tuning_free(ctx->tuning);
   delete ctx;
   return LSQ_OK;
 }
@@ -596,6 +603,135 @@ lsq_status lsq_solve(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts* o, dou
   s = solve_once(ctx, pr, &op, x, info, stream);
   if (info) info->precond_fallback = 1;
   return s;
+}
+
+lsq_status lsq_solve_batch(lsq_ctx* ctx, const lsq_batch_item* items, int64_t count, double tol, int64_t maxit,
+                           int32_t flags, lsq_batch_result* results, void* stream) {
+  lsq_status s;
+  if ((s = check_ctx(ctx)) != LSQ_OK) return s;
+  if (count < 0 || (count > 0 && !items)) return fail(ctx, LSQ_ERR_ARG, "bad batch");
+  if (count == 0) return LSQ_OK;
+  if (count > 2147483647LL) return fail(ctx, LSQ_ERR_ARG, "too many problems");
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t m_max = 0;
+  int n_max = 0, d_max = 0, ring_elems = 0;
+  for (int64_t i = 0; i < count; ++i) {
+    const lsq_batch_item& it = items[i];
+    if (it.m < 1 || it.n < 1 || it.n > 512 || it.lda < it.n || it.d < it.n + 1 || it.d > (1 << 20) || it.zeta < 1 ||
+        it.zeta > 8 || it.zeta > it.d || !it.A || !it.b || !it.x)
+      return fail(ctx, LSQ_ERR_ARG, "batch item " + std::to_string(i) +
+                                        ": need 1 <= n <= 512, lda >= n, n+1 <= d, 1 <= zeta <= min(8, d), pointers");
+    m_max = std::max(m_max, it.m);
+    n_max = std::max(n_max, (int)it.n);
+    ring_elems = std::max(ring_elems, batch_ring_elems((int)it.n));
+    d_max = std::max(d_max, (int)it.d);
+  }
+  const BatchLayout L = batch_layout(m_max, n_max, d_max);
+  const int grid = batch_grid(ring_elems, ctx->sms);
+  if (grid < 1) return fail(ctx, LSQ_ERR_CUDA, "batch kernel does not fit on the device");
+  const size_t ib = batch_item_bytes();
+  Carver probe{nullptr};
+  probe.take<char>((size_t)grid * L.slab);
+  probe.take<char>((size_t)count * ib);
+  probe.take<int32_t>((size_t)count);
+  probe.take<double>((size_t)count * kOutSlots);
+  probe.take<uint32_t>((size_t)count);
+  probe.take<int32_t>(1);
+  if ((s = ensure_ws(ctx, probe.off)) != LSQ_OK) return s;
+  Carver cv{ctx->ws};
+  char* ws = cv.take<char>((size_t)grid * L.slab);
+  void* items_dev = cv.take<char>((size_t)count * ib);
+  int32_t* order_dev = cv.take<int32_t>((size_t)count);
+  double* out_dev = cv.take<double>((size_t)count * kOutSlots);
+  uint32_t* status_dev = cv.take<uint32_t>((size_t)count);
+  int32_t* next_dev = cv.take<int32_t>(1);
+
+  std::vector<char> host_items((size_t)count * ib);
+  std::vector<int32_t> order((size_t)count);
+  for (int64_t i = 0; i < count; ++i) order[i] = (int32_t)i;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return items[a].m * items[a].n > items[b].m * items[b].n;
+  });
+  const int mode = (flags & LSQ_FLAG_NO_CHECK) ? 2 : 0;
+  if ((s = reset_small(ctx, st)) != LSQ_OK) return s;
+
+  // ---- autotuner: time each candidate shape on the largest problems of an untuned n-range
+  if (flags & LSQ_FLAG_AUTOTUNE) {
+    for (int bk = 0; bk < 5; ++bk) {
+      if (batch_get_shape(ctx->tuning, bk) >= 0) continue;
+      std::vector<int32_t> sub;
+      for (int32_t i : order)
+        if (batch_bucket_of((int)items[i].n) == bk && (int)sub.size() < grid) sub.push_back(i);
+      if (sub.empty()) continue;
+      std::vector<int> cand;
+      batch_shape_candidates((int)items[sub[0]].n, cand);
+      if (cand.size() == 1) {
+        batch_set_shape(ctx->tuning, bk, cand[0]);
+        continue;
+      }
+      float best_ms = 1e30f;
+      int best = cand.back();
+      cudaEvent_t e0, e1;
+      CK(cudaEventCreate(&e0));
+      CK(cudaEventCreate(&e1));
+      for (int shp : cand) {
+        batch_items_fill(host_items.data(), items, count, nullptr);
+        for (int32_t i : sub) batch_set_item_shape(host_items.data(), i, shp);
+        CK(cudaMemcpyAsync(items_dev, host_items.data(), host_items.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(order_dev, sub.data(), sub.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(status_dev, 0, (size_t)count * sizeof(uint32_t), st));
+        CK(cudaEventRecord(e0, st));
+        CK(batch_launch(items_dev, order_dev, (int)sub.size(), next_dev, ws, L, tol, maxit, 2, out_dev, status_dev,
+                        ctx->d_bar, grid, ring_elems, st));
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = shp;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      batch_set_shape(ctx->tuning, bk, best);
+    }
+  }
+
+  batch_items_fill(host_items.data(), items, count, ctx->tuning);
+  CK(cudaMemcpyAsync(items_dev, host_items.data(), host_items.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(order_dev, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(status_dev, 0, (size_t)count * sizeof(uint32_t), st));
+  CK(batch_launch(items_dev, order_dev, (int)count, next_dev, ws, L, tol, maxit, mode, out_dev, status_dev,
+                  ctx->d_bar, grid, ring_elems, st));
+  std::vector<double> hout((size_t)count * kOutSlots);
+  std::vector<uint32_t> hst((size_t)count);
+  CK(cudaMemcpyAsync(hout.data(), out_dev, hout.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hst.data(), status_dev, hst.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  lsq_status worst = LSQ_OK;
+  std::string msg;
+  for (int64_t i = 0; i < count; ++i) {
+    const lsq_status si = status_from_bits(nullptr, hst[i]);
+    if (si != LSQ_OK && worst == LSQ_OK) {
+      worst = si;
+      msg = "batch item " + std::to_string(i) + ": " + lsq_status_string(si);
+    }
+    if (results) {
+      lsq_batch_result& r = results[i];
+      const double* o = hout.data() + (size_t)i * kOutSlots;
+      r.status = si;
+      r.stop = (int32_t)o[OUT_STOP];
+      r.iters = (int64_t)o[OUT_ITERS];
+      r.backward_error_ne = o[OUT_ETA_NE];
+      r.rnorm = o[OUT_RNORM];
+      r.anorm_fro = o[OUT_FRO];
+      r.xnorm = o[OUT_XNORM];
+      r.bnorm = o[OUT_BNORM];
+    }
+  }
+  if (worst != LSQ_OK) return fail(ctx, worst, msg);
+  return LSQ_OK;
 }
 
 }  // extern "C"

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace lsq {
@@ -42,6 +44,7 @@ struct LsqrParams {
   int64_t ldi;       // image row length: n rounded up to even
   bool a_ring;       // A rows can come through bulk copies (n even, lda even, A 16-byte aligned)
   bool vec;          // A rows allow 16-byte vector loads (lda even, A aligned)
+  bool check_df;     // accuracy pass in pair arithmetic on the image (batched problems)
   const double* M;   // n x n row-major (upper triangular), may be null in check mode
   const double* Mt;  // transpose of M, row-major
   double* x;         // in: start, out: solution
@@ -85,5 +88,27 @@ int lsqr_gparts(int grid);
 // Grid size the LSQR kernel will use for n (co-resident blocks).
 int lsqr_grid(int n, bool vec, bool native, int sms);
 cudaError_t lsqr_run(const LsqrParams& p, bool vec, bool native, int grid, cudaStream_t st);
+
+// Batched solves (batch.cu).
+struct BatchTuning;
+BatchTuning* batch_tuning_new();
+void batch_tuning_free(BatchTuning* t);
+struct BatchLayout {
+  size_t oY, oW, oR, oM, oMt, oRd, oU, oVec, oGpart, oPart, oImg, slab;
+  int npad_max;
+};
+BatchLayout batch_layout(int64_t m_max, int n_max, int d_max);
+int batch_ring_elems(int n);
+int batch_grid(int ring_elems, int sms);
+size_t batch_item_bytes();
+void batch_items_fill(void* dst, const lsq_batch_item* src, int64_t count, const BatchTuning* tune);
+cudaError_t batch_launch(const void* items_dev, const int32_t* order_dev, int count, int32_t* next_dev, char* ws,
+                         const BatchLayout& L, double tol, int64_t maxit, int mode, double* out, uint32_t* status,
+                         GridBarrier* bar, int grid, int ring_elems, cudaStream_t st);
+void batch_shape_candidates(int n, std::vector<int>& out);
+int batch_bucket_of(int n);
+void batch_set_shape(BatchTuning* t, int bucket, int shape);
+int batch_get_shape(const BatchTuning* t, int bucket);
+void batch_set_item_shape(void* items, int64_t i, int shape);
 
 }  // namespace lsq

@@ -14,579 +14,11 @@
 // order, so all blocks take the same branch at the stopping test.  After the
 // loop the same pass structure computes r = b - A x, A^T r and ||A||_F (the
 // accuracy check) and the backward-error bounds.
-#include "dfloat.cuh"
-#include "kernels.h"
+#include "lsqr_device.cuh"
 
 namespace lsq {
 
 namespace {
-
-constexpr int kWarps = 8;
-constexpr int kThreads = kWarps * 32;
-constexpr int kNbuf = 3;  // bulk-copy ring depth per warp (rows in flight)
-
-// Barrier over the blocks that share one problem: the whole grid (grid
-// barrier with timeout) or a single block (batched problems).
-__device__ __forceinline__ bool group_sync(const LsqrParams& p) {
-  if (p.gcount == 1) {
-    __syncthreads();
-    return true;
-  }
-  return grid_sync(p.bar, p.status);
-}
-
-// --------------------------------------------------------------------------
-// The pass over A.  Block `blk` owns rows [m*blk/G, m*(blk+1)/G); its warp k
-// takes rows start+k, start+k+8, ...  Lane l holds columns 2l+64t, 2l+64t+1
-// (t < T) of the current row and of the vector wvec.  For each row:
-//   y_i = wsign * (A_i . wvec) - gamma * uin_i;  uout_i = y_i (optional)
-//   sum y_i^2, sum uin_i^2 (optional), sum A_ij^2 (optional), g += y_i A_i
-// Per-block results: gpart[blk][0..n), part[blk][slot...].
-// --------------------------------------------------------------------------
-template <int T, bool VEC, bool FRO, bool UIN2>
-__device__ void pass_native(const LsqrParams& p, const double* __restrict__ wvec, double wsign,
-                            const double* __restrict__ uin, double gamma, double* __restrict__ uout, double* s_g,
-                            double* s_scal) {
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int G = p.gcount, blk = p.gidx;
-  const int n = p.n;
-  const int64_t r0 = (p.m * blk) / G, r1 = (p.m * (blk + 1)) / G;
-  double wr[2 * T], g[2 * T];
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const int j = 2 * lane + 64 * t;
-    wr[2 * t] = j < n ? wsign * wvec[j] : 0.0;
-    wr[2 * t + 1] = j + 1 < n ? wsign * wvec[j + 1] : 0.0;
-    g[2 * t] = g[2 * t + 1] = 0.0;
-  }
-  double ss = 0.0, bb = 0.0, fro = 0.0;
-  for (int64_t i = r0 + wib; i < r1; i += kWarps) {
-    const double* Ai = p.A + i * p.lda;
-    double2 a[T];
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-      const int j = 2 * lane + 64 * t;
-      if (j + 1 < n) {
-        if (VEC) {
-          a[t] = __ldcs(reinterpret_cast<const double2*>(Ai + j));
-        } else {
-          a[t].x = __ldcs(Ai + j);
-          a[t].y = __ldcs(Ai + j + 1);
-        }
-      } else if (j < n) {
-        a[t].x = __ldcs(Ai + j);
-        a[t].y = 0.0;
-      } else {
-        a[t].x = a[t].y = 0.0;
-      }
-    }
-    double dot = 0.0;
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-      dot = fma(a[t].x, wr[2 * t], dot);
-      dot = fma(a[t].y, wr[2 * t + 1], dot);
-    }
-    dot = warp_allreduce_sum(dot);
-    const double ui = uin[i];
-    const double y = fma(-gamma, ui, dot);
-    if (uout && lane == 0) uout[i] = y;
-    ss = fma(y, y, ss);
-    if (UIN2) bb = fma(ui, ui, bb);
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-      g[2 * t] = fma(y, a[t].x, g[2 * t]);
-      g[2 * t + 1] = fma(y, a[t].y, g[2 * t + 1]);
-      if (FRO) {
-        fro = fma(a[t].x, a[t].x, fro);
-        fro = fma(a[t].y, a[t].y, fro);
-      }
-    }
-  }
-  // block reduction of g (warp order), ss, bb, fro
-  double* sg = s_g + wib * (64 * T);
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    sg[2 * lane + 64 * t] = g[2 * t];
-    sg[2 * lane + 64 * t + 1] = g[2 * t + 1];
-  }
-  if (FRO) fro = warp_allreduce_sum(fro);
-  if (lane == 0) {
-    s_scal[wib * 4 + 0] = ss;
-    s_scal[wib * 4 + 1] = bb;
-    s_scal[wib * 4 + 2] = fro;
-  }
-  __syncthreads();
-  double* gp = p.gpart + (int64_t)blk * p.npad;
-  for (int j = threadIdx.x; j < n; j += kThreads) {
-    double s = 0.0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) s += s_g[w * (64 * T) + j];
-    gp[j] = s;
-  }
-  if (threadIdx.x < 3) {
-    double s = 0.0;
-    for (int w = 0; w < kWarps; ++w) s += s_scal[w * 4 + threadIdx.x];
-    p.part[(int64_t)blk * 4 + threadIdx.x] = s;
-  }
-  __syncthreads();
-}
-
-template <int T, bool VEC>
-struct NativePass {
-  double* s_g;
-  double* s_scal;
-  __device__ void init(LsqrParams& p) {  // y = b - A x0 -> u; sum y^2, sum b^2
-    p.gparts = p.gcount;
-    pass_native<T, VEC, false, true>(p, p.x, -1.0, p.b, -1.0, p.u, s_g, s_scal);
-  }
-  __device__ void iter(LsqrParams& p, double gamma) {  // y = A wv - gamma u -> u
-    p.gparts = p.gcount;
-    pass_native<T, VEC, false, false>(p, p.wv, 1.0, p.u, gamma, p.u, s_g, s_scal);
-  }
-  __device__ void check(LsqrParams& p) {  // y = b - A x; sum y^2, b^2, A_ij^2
-    p.gparts = p.gcount;
-    pass_native<T, VEC, true, true>(p, p.x, -1.0, p.b, -1.0, nullptr, s_g, s_scal);
-  }
-};
-
-// g[j] = sum over blocks of gpart[blk][j], block order.
-// Column j is summed by block j % G: thread t adds partials t, t+256, ...,
-// then a fixed-order block reduction (deterministic for a given grid).
-__device__ void reduce_g(const LsqrParams& p) {
-  __shared__ double scratch[32];
-  const int G = p.gcount;
-  for (int j = p.gidx; j < p.n; j += G) {
-    double s = 0.0;
-    for (int c = threadIdx.x; c < p.gparts; c += kThreads) s += p.gpart[(int64_t)c * p.npad + j];
-    s = block_sum(s, scratch);
-    if (threadIdx.x == 0) p.g[j] = s;
-  }
-}
-
-// Sum over blocks of part[blk][slot]: thread t adds blocks t, t+256, ...,
-// then a fixed-order block reduction.  Every thread of every block calls it
-// and gets the same value.
-__device__ double sum_part(const LsqrParams& p, int slot) {
-  __shared__ double scratch[32];
-  double s = 0.0;
-  for (int c = threadIdx.x; c < p.gcount; c += kThreads) s += p.part[(int64_t)c * 4 + slot];
-  return block_sum(s, scratch);
-}
-
-// vhat_k = (M^T g)_k * ginv - cv * v_k, one warp per k; per-block sum of
-// vhat_k^2 into part[blk][slot].  M^T g uses rows of Mt (contiguous).
-__device__ void mt_apply(const LsqrParams& p, double ginv, double cv, int slot, double* s_scal) {
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int gw = p.gidx * kWarps + wib, nw = p.gcount * kWarps;
-  double acc = 0.0;
-  for (int k = gw; k < p.n; k += nw) {
-    const double* mk = p.Mt + (int64_t)k * p.n;
-    double s = 0.0;
-    for (int i = lane; i <= k; i += 32) s = fma(mk[i], p.g[i], s);
-    s = warp_allreduce_sum(s);
-    const double vh = cv != 0.0 ? fma(s, ginv, -cv * p.v[k]) : s * ginv;
-    if (lane == 0) p.vhat[k] = vh;
-    acc = fma(vh, vh, acc);
-  }
-  if (lane == 0) s_scal[wib] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < kWarps; ++w) s += s_scal[w];
-    p.part[(int64_t)p.gidx * 4 + slot] = s;
-  }
-  __syncthreads();
-}
-
-// v = vhat * ainv; wv = M v; x += cx * w; w = wv - cw * w  (one warp per row i)
-__device__ void m_apply_update(const LsqrParams& p, double ainv, double cx, double cw, bool first) {
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int gw = p.gidx * kWarps + wib, nw = p.gcount * kWarps;
-  for (int i = gw; i < p.n; i += nw) {
-    const double* mi = p.M + (int64_t)i * p.n;
-    double s = 0.0;
-    for (int k = i + lane; k < p.n; k += 32) s = fma(mi[k], p.vhat[k], s);
-    s = warp_allreduce_sum(s);
-    if (lane == 0) {
-      const double wvi = s * ainv;
-      p.v[i] = p.vhat[i] * ainv;
-      p.wv[i] = wvi;
-      if (first) {
-        p.w[i] = wvi;
-      } else {
-        const double wi = p.w[i];
-        p.x[i] = fma(cx, wi, p.x[i]);
-        p.w[i] = fma(-cw, wi, wvi);
-      }
-    }
-  }
-}
-
-// --------------------------------------------------------------------------
-// The double-float pass (FP32/INT pipes only in the per-element and per-row
-// work).  Rows arrive through a per-warp ring of kNbuf shared-memory row
-// buffers filled by cp.async.bulk (one elected lane issues, an mbarrier per
-// buffer signals completion), so each warp keeps kNbuf rows in flight while it
-// computes.  Requires n even, lda even and A 16-byte aligned.
-//
-// Per row: lane l splits its 2T column pairs into (hi, mid) floats,
-// accumulates the row dot in kAcc independent float-pair accumulators, sums
-// them and butterflies the result over the warp (every lane ends with the
-// same pair), forms y = dot - gamma * u_i in pair arithmetic, stores y (the u
-// buffer holds float pairs in this kernel) and adds y * A_i into its column
-// accumulators.  Column pairs are renormalised every second row and flushed
-// into the warp's FP64 partial-sum row of gpart every 32 rows, so no pair sum
-// runs over more than 32 rows.  gpart holds one row per warp (grid * kWarps
-// rows).
-//
-// When the workspace allows (p.asplit != null) the first pass also stores
-// every split row as a (hi, mid) float-pair image of A (8 bytes per entry, as
-// FP64), and later passes stream that image instead of A: the values are
-// identical to the on-the-fly split, and the per-entry integer split leaves
-// the hot loop.
-// --------------------------------------------------------------------------
-template <int T>
-struct DfPass {
-  double* ring;     // dynamic shared memory [kWarps][kNbuf][n]
-  uint64_t* bars;   // [kWarps][kNbuf]
-  double* s_scal;
-  uint32_t seq;     // rows this warp has consumed so far (all passes)
-
-  // Row source: the FP64 matrix (n even, lda even, A aligned), or its
-  // (hi, mid) float-pair image (ldi entries per row, ldi even).
-  template <bool FROM_IMAGE>
-  __device__ void issue(const LsqrParams& p, int64_t r0, int wib, uint32_t j, double* myring, uint64_t* mybars) {
-    const int64_t row = r0 + (int64_t)wib + (int64_t)kWarps * j;
-    const uint32_t s = seq + j, b = s % kNbuf;
-    const uint32_t rb = (uint32_t)(FROM_IMAGE ? p.ldi : p.n) * 8u;
-    const void* src = FROM_IMAGE ? (const void*)(p.asplit + row * p.ldi) : (const void*)(p.A + row * p.lda);
-    mbar_arrive_expect_tx(mybars + b, rb);
-    bulk_g2s(myring + (size_t)b * p.ldi, src, rb, mybars + b);
-  }
-
-  // Wait (bounded) for the buffer of row j.  Returns false on timeout (warp-uniform).
-  __device__ bool wait(uint32_t j, uint64_t* mybars) {
-    const uint32_t s = seq + j, b = s % kNbuf, par = (s / kNbuf) & 1u;
-    bool timed_out = false;
-    if (!mbar_try_wait(mybars + b, par)) {
-      const unsigned long long t0 = globaltimer_ns();
-      uint32_t it = 0;
-      while (!mbar_try_wait(mybars + b, par)) {
-        if ((++it & 255u) == 0 && globaltimer_ns() - t0 > kBarrierTimeoutNs) {
-          timed_out = true;
-          break;
-        }
-      }
-    }
-    return !__any_sync(0xffffffffu, timed_out);
-  }
-
-  // FROM_IMAGE: rows come from the float-pair image through the ring; else
-  // from A (split on the fly) -- through the ring when p.a_ring, by direct
-  // loads otherwise (odd n or lda, unaligned A) -- and, when WRITE_IMAGE, the
-  // split rows are stored to the image.
-  template <bool UIN_B, bool UIN2, bool STORE, bool FROM_IMAGE, bool WRITE_IMAGE>
-  __device__ void run(const LsqrParams& p, const double* __restrict__ wvec, double wsign, double gamma) {
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int G = p.gcount, blk = p.gidx;
-    const int n = p.n;
-    const int64_t r0 = (p.m * blk) / G, r1 = (p.m * (blk + 1)) / G;
-    const int64_t nrows = r1 - r0;
-    const uint32_t count = nrows > wib ? (uint32_t)((nrows - wib + kWarps - 1) / kWarps) : 0u;
-    const bool use_ring = FROM_IMAGE || p.a_ring;
-    double* myring = ring + (size_t)wib * kNbuf * p.ldi;
-    uint64_t* mybars = bars + wib * kNbuf;
-    float2* ubuf = reinterpret_cast<float2*>(p.u);
-    double* gw = p.gpart + ((int64_t)blk * kWarps + wib) * p.npad;
-
-    df wv[2 * T], Gc[2 * T];
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int j = 2 * lane + 64 * t + h;
-        const double v = j < n ? wsign * wvec[j] : 0.0;
-        const float v1 = __double2float_rn(v);
-        wv[2 * t + h] = df{v1, __double2float_rn(v - (double)v1)};
-        Gc[2 * t + h] = df{0.f, 0.f};
-      }
-    }
-    const float g1 = __double2float_rn(gamma);
-    const df gdf{g1, __double2float_rn(gamma - (double)g1)};
-    df ss{0.f, 0.f}, bb{0.f, 0.f};
-    bool first_flush = true;
-
-    if (lane == 0 && use_ring) {
-      fence_proxy_async_smem();
-      for (uint32_t j = 0; j < count && j < (uint32_t)kNbuf; ++j) issue<FROM_IMAGE>(p, r0, wib, j, myring, mybars);
-    }
-    bool ok = true;
-    uint32_t j = 0;
-    for (; j < count; ++j) {
-      if (use_ring && !wait(j, mybars)) {
-        ok = false;
-        break;
-      }
-      const int64_t row = r0 + (int64_t)wib + (int64_t)kWarps * j;
-      const double* buf = myring + (size_t)((seq + j) % kNbuf) * p.ldi;
-      // u_i (or b_i) is needed only after the row dot: load it first
-      double bi = 0.0;
-      float2 uu = make_float2(0.f, 0.f);
-      if (UIN_B)
-        bi = p.b[row];
-      else
-        uu = ubuf[row];
-      float h[2 * T], mm[2 * T];
-#pragma unroll
-      for (int t = 0; t < T; ++t) {
-        const int c = 2 * lane + 64 * t;
-        if (FROM_IMAGE) {
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (c < n) v = *reinterpret_cast<const float4*>(buf + c);
-          h[2 * t] = v.x;
-          mm[2 * t] = v.y;
-          h[2 * t + 1] = v.z;
-          mm[2 * t + 1] = v.w;
-        } else {
-          double2 v = make_double2(0.0, 0.0);
-          if (p.a_ring) {
-            if (c < n) v = *reinterpret_cast<const double2*>(buf + c);
-          } else {
-            const double* Ar = p.A + row * p.lda;
-            if (c < n) v.x = __ldcs(Ar + c);
-            if (c + 1 < n) v.y = __ldcs(Ar + c + 1);
-          }
-          split2(v.x, h[2 * t], mm[2 * t]);
-          split2(v.y, h[2 * t + 1], mm[2 * t + 1]);
-          if (WRITE_IMAGE && c < n)
-            *reinterpret_cast<float4*>(p.asplit + row * p.ldi + c) = make_float4(h[2 * t], mm[2 * t], h[2 * t + 1],
-                                                                                 mm[2 * t + 1]);
-        }
-      }
-      __syncwarp();
-      if (lane == 0 && use_ring && j + kNbuf < count) {
-        fence_proxy_async_smem();
-        issue<FROM_IMAGE>(p, r0, wib, j + kNbuf, myring, mybars);
-      }
-      // row dot: kAcc independent pair accumulators (short chains)
-      constexpr int kAcc = (2 * T) >= 2 ? 2 : 1;
-      df av[kAcc];
-#pragma unroll
-      for (int k = 0; k < kAcc; ++k) av[k] = df{0.f, 0.f};
-#pragma unroll
-      for (int q = 0; q < 2 * T; ++q) df_fma_acc(av[q % kAcc], h[q], mm[q], wv[q].hi, wv[q].lo);
-#pragma unroll
-      for (int k = 1; k < kAcc; k <<= 1) {
-#pragma unroll
-        for (int i = 0; i + k < kAcc; i += 2 * k) av[i] = df_add(av[i], av[i + k]);
-      }
-      df dot = av[0];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) dot = df_add_unnorm(dot, shfl_xor_df(dot, o));
-      dot = df_renorm(dot);
-      const df ui = UIN_B ? df_from_double(bi) : df{uu.x, uu.y};
-      const df y = df_add(dot, df_neg(df_mul(gdf, ui)));
-      if (STORE && lane == 0) ubuf[row] = make_float2(y.hi, y.lo);
-      ss = df_add(ss, df_mul(y, y));
-      if (UIN2) bb = df_add(bb, df_mul(ui, ui));
-#pragma unroll
-      for (int q = 0; q < 2 * T; ++q) {
-        df_fma_acc(Gc[q], h[q], mm[q], y.hi, y.lo);
-        if (j & 1u) Gc[q] = df_renorm(Gc[q]);
-      }
-      if ((j & 31u) == 31u) {
-#pragma unroll
-        for (int t = 0; t < T; ++t) {
-          const int c = 2 * lane + 64 * t;
-          if (c < n) {
-            double2 g = first_flush ? make_double2(0.0, 0.0) : *reinterpret_cast<const double2*>(gw + c);
-            g.x += df_to_double(Gc[2 * t]);
-            g.y += df_to_double(Gc[2 * t + 1]);
-            *reinterpret_cast<double2*>(gw + c) = g;
-          }
-          Gc[2 * t] = Gc[2 * t + 1] = df{0.f, 0.f};
-        }
-        first_flush = false;
-      }
-    }
-    if (!ok) {
-      // give up: flag, then let the copies already issued land before leaving
-      if (lane == 0) {
-        atomicOr(p.status, DS_TIMEOUT);
-        atomicExch(&p.bar->abort, 1u);
-      }
-      for (uint32_t k = j; k < count && k < j + kNbuf; ++k) wait(k, mybars);
-    }
-    if (use_ring) seq += count;  // ring phases advance only when rows went through it
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-      const int c = 2 * lane + 64 * t;
-      if (c < n) {
-        double2 g = first_flush ? make_double2(0.0, 0.0) : *reinterpret_cast<const double2*>(gw + c);
-        g.x += df_to_double(Gc[2 * t]);
-        g.y += df_to_double(Gc[2 * t + 1]);
-        *reinterpret_cast<double2*>(gw + c) = g;
-      }
-    }
-    if (lane == 0) {
-      s_scal[wib * 4 + 0] = df_to_double(ss);
-      s_scal[wib * 4 + 1] = df_to_double(bb);
-      s_scal[wib * 4 + 2] = 0.0;
-    }
-    __syncthreads();
-    if (threadIdx.x < 3) {
-      double sum = 0.0;
-      for (int w = 0; w < kWarps; ++w) sum += s_scal[w * 4 + threadIdx.x];
-      p.part[(int64_t)blk * 4 + threadIdx.x] = sum;
-    }
-    __syncthreads();
-  }
-
-  __device__ void init(LsqrParams& p) {
-    p.gparts = p.gcount * kWarps;
-    if (p.asplit) {
-      run<true, true, true, false, true>(p, p.x, -1.0, -1.0);
-      // the image was written through the generic proxy and is read by bulk
-      // copies (async proxy) after the next grid barrier
-      asm volatile("fence.proxy.async.global;" ::: "memory");
-    } else {
-      run<true, true, true, false, false>(p, p.x, -1.0, -1.0);
-    }
-  }
-  __device__ void iter(LsqrParams& p, double gamma) {
-    p.gparts = p.gcount * kWarps;
-    if (p.asplit)
-      run<false, false, true, true, false>(p, p.wv, 1.0, gamma);
-    else
-      run<false, false, true, false, false>(p, p.wv, 1.0, gamma);
-  }
-  // The accuracy pass runs in native FP64 (A is aligned here, so the vector
-  // path applies) with per-block partials; the ring doubles as its
-  // block-reduction scratch.
-  __device__ void check(LsqrParams& p) {
-    p.gparts = p.gcount;
-    if (p.vec)
-      pass_native<T, true, true, true>(p, p.x, -1.0, p.b, -1.0, nullptr, ring, s_scal);
-    else
-      pass_native<T, false, true, true>(p, p.x, -1.0, p.b, -1.0, nullptr, ring, s_scal);
-  }
-};
-
-// --------------------------------------------------------------------------
-// Algorithm 2 around a pass policy (see the file header for the order).
-// --------------------------------------------------------------------------
-template <class Pass>
-__device__ void lsqr_body(LsqrParams& p, Pass& pass, double* s_scal) {
-  uint32_t* status = p.status;
-  double alpha = 0.0, beta = 0.0, rhobar = 0.0, phibar = 0.0, anorm2 = 0.0, bnorm = 0.0, normal_rel = 0.0;
-  int64_t iters = 0;
-  int stop = 0;
-
-  if (p.mode != 1) {
-    // ---- beta_1 u_1 = b - A x0
-    pass.init(p);
-    if (!group_sync(p)) return;
-    reduce_g(p);
-    if (!group_sync(p)) return;
-    beta = sqrt(sum_part(p, 0));
-    bnorm = sqrt(sum_part(p, 1));
-    // ---- alpha_1 v_1 = M^T A^T u_1
-    mt_apply(p, beta > 0.0 ? 1.0 / beta : 0.0, 0.0, 2, s_scal);
-    if (!group_sync(p)) return;
-    alpha = sqrt(sum_part(p, 2));
-    // ---- w_1 = M v_1
-    m_apply_update(p, alpha > 0.0 ? 1.0 / alpha : 0.0, 0.0, 0.0, true);
-    rhobar = alpha;
-    phibar = beta;
-    anorm2 = alpha * alpha;
-    if (beta == 0.0 || alpha == 0.0) stop = 4;
-    if (!group_sync(p)) return;
-
-    while (stop == 0) {
-      if (iters >= p.maxit) {
-        stop = 3;
-        break;
-      }
-      ++iters;
-      // uhat_{t+1} = A (M v_t) - alpha_t u_t = A wv - (alpha/beta) uhat_t
-      pass.iter(p, alpha / beta);
-      if (!group_sync(p)) return;
-      reduce_g(p);
-      if (!group_sync(p)) return;
-      const double beta1 = sqrt(sum_part(p, 0));
-      // vhat_{t+1} = M^T A^T uhat / beta_{t+1} - beta_{t+1} v_t
-      mt_apply(p, beta1 > 0.0 ? 1.0 / beta1 : 0.0, beta1, 2, s_scal);
-      if (!group_sync(p)) return;
-      const double a2 = sum_part(p, 2);
-      const double alpha1 = beta1 > 0.0 ? sqrt(a2) : 0.0;
-      // Givens rotation
-      const double rho = sqrt(fma(rhobar, rhobar, beta1 * beta1));
-      const double c = rhobar / rho, s = beta1 / rho;
-      const double theta = s * alpha1;
-      rhobar = -c * alpha1;
-      const double phi = c * phibar;
-      phibar = s * phibar;
-      m_apply_update(p, alpha1 > 0.0 ? 1.0 / alpha1 : 0.0, phi / rho, theta / rho, false);
-      anorm2 += alpha1 * alpha1 + beta1 * beta1;
-      normal_rel = alpha1 * fabs(c) / sqrt(anorm2);
-      alpha = alpha1;
-      beta = beta1;
-      if (normal_rel <= p.tol) stop = 1;
-      else if (phibar <= p.tol * bnorm) stop = 2;
-      else if (beta == 0.0 || alpha == 0.0) stop = 4;
-      if (!group_sync(p)) return;
-    }
-  }
-
-  if (p.mode == 2) {
-    if (p.gidx == 0 && threadIdx.x == 0) {
-      p.out[OUT_ITERS] = (double)iters;
-      p.out[OUT_STOP] = (double)stop;
-      p.out[OUT_NORMAL_REL] = normal_rel;
-      p.out[OUT_BNORM] = bnorm;
-      p.out[OUT_ANORM_EST] = sqrt(anorm2);
-      if (stop == 3) atomicOr(status, DS_NOCONV);
-    }
-    return;
-  }
-  // ---- accuracy pass: y = b - A x, g = A^T y, ||A||_F
-  pass.check(p);
-  if (!group_sync(p)) return;
-  reduce_g(p);
-  if (!group_sync(p)) return;
-  if (p.M) mt_apply(p, 1.0, 0.0, 3, s_scal);
-  if (!group_sync(p)) return;
-  if (p.gidx == 0) {
-    __shared__ double scratch[32];
-    double gx = 0.0, xx = 0.0;
-    for (int j = threadIdx.x; j < p.n; j += kThreads) {
-      gx = fma(p.g[j], p.g[j], gx);
-      xx = fma(p.x[j], p.x[j], xx);
-    }
-    gx = block_sum(gx, scratch);
-    xx = block_sum(xx, scratch);
-    const double rnorm = sqrt(sum_part(p, 0));
-    const double bn = sqrt(sum_part(p, 1));
-    const double fro = sqrt(sum_part(p, 2));
-    const double marn = p.M ? sqrt(sum_part(p, 3)) : 0.0;
-    if (threadIdx.x == 0) {
-      const double arn = sqrt(gx), xn = sqrt(xx);
-      p.out[OUT_ITERS] = (double)iters;
-      p.out[OUT_STOP] = (double)stop;
-      p.out[OUT_NORMAL_REL] = normal_rel;
-      p.out[OUT_RNORM] = rnorm;
-      p.out[OUT_ARNORM] = arn;
-      p.out[OUT_FRO] = fro;
-      p.out[OUT_XNORM] = xn;
-      p.out[OUT_BNORM] = bn;
-      p.out[OUT_ETA_NE] = (fro > 0.0 && rnorm > 0.0) ? arn / (fro * rnorm) : 0.0;
-      p.out[OUT_ETA_PRE] = (fro > 0.0 && xn > 0.0) ? marn / (fro * xn) : 0.0;
-      p.out[OUT_MARNORM] = marn;
-      p.out[OUT_ANORM_EST] = sqrt(anorm2);
-      if (stop == 3) atomicOr(status, DS_NOCONV);
-    }
-  }
-}
 
 template <int T, bool VEC>
 __global__ void __launch_bounds__(kThreads, 2) k_lsqr_native(LsqrParams p) {
@@ -608,14 +40,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_df(LsqrParams p) {
     fence_proxy_async_smem();
   }
   __syncthreads();
-  DfPass<T> pass{s_ring, s_bars, s_scal, 0u};
+  DfPass<32, T> pass{s_ring, s_bars, s_scal, 0u};
   p.gidx = blockIdx.x;
   p.gcount = gridDim.x;
   lsqr_body(p, pass, s_scal);
 }
 
 size_t df_smem(int T, int n) {
-  const size_t ring = (size_t)kWarps * kNbuf * (size_t)((n + 1) / 2 * 2) * sizeof(double);
+  const size_t ring = (size_t)kWarps * kNbuf * (size_t)((n + 1) / 2 * 2) * sizeof(double);  // one row per step
   const size_t red = (size_t)kWarps * 64 * T * sizeof(double);
   return ring > red ? ring : red;
 }

@@ -103,6 +103,11 @@ extern "C" lsq_status lsq_check_noalloc(const double* A, int64_t m, int64_t n, i
   p.tol = 0.0;
   p.maxit = 0;
   p.mode = 1;
+  p.asplit = nullptr;
+  p.ldi = (n + 1) / 2 * 2;
+  p.vec = vec;
+  p.a_ring = false;
+  p.check_df = false;
   p.bar = bar;
   p.status = status;
   p.out = out;
