@@ -203,6 +203,73 @@ class _Scaled:
         return self.sample[key]
 
 
+def make_batch(count, device, seed=2024, m_lo=2000, m_hi=50000, n_lo=16, n_hi=128):
+    """Config 3: independent problems, m ~ U[m_lo, m_hi], n ~ U[n_lo, n_hi],
+    log10 cond ~ U[2, 10], d = 4n, zeta = 8 (cheap construction of synth)."""
+    import numpy as np
+
+    from paper_2506_03070_gb300 import synth
+    rng = np.random.default_rng(seed)
+    probs = []
+    for k in range(count):
+        m = int(rng.integers(m_lo, m_hi + 1))
+        n = int(rng.integers(n_lo, n_hi + 1))
+        cond = float(10.0 ** rng.uniform(2, 10))
+        p = synth.batched_problem(m, n, cond, seed=seed * 100003 + k, device=device)
+        probs.append({"A": p["A"], "b": p["b"], "d": 4 * n, "zeta": 8, "seed": k})
+    return probs
+
+
+def run_batch(args):
+    import torch
+
+    import paper_2506_03070_gb300 as P
+    import __graft_entry__
+    __graft_entry__.build()
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    ctx = P.Context(local)
+    probs = make_batch(args.batch, f"cuda:{local}")
+    elems = sum(p["A"].numel() for p in probs)
+    stream = torch.cuda.current_stream()
+    flags = P.FLAG_AUTOTUNE
+    for _ in range(args.warmup):
+        xs, res = ctx.lsq_solve_batch(probs, tol=1e-12, flags=flags, stream=stream)
+    times = []
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xs, res = ctx.lsq_solve_batch(probs, tol=1e-12, flags=flags, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    clocks = sampler.stop()
+    import oracle
+    worst = 0.0
+    for k in range(0, len(probs), max(1, len(probs) // 16)):
+        worst = max(worst, oracle.backward_error_kw(probs[k]["A"], probs[k]["b"], xs[k]))
+    iters = [r["iters"] for r in res]
+    t = statistics.mean(times)
+    passes = sum(r["iters"] + 2 for r in res)
+    # bytes: every pass reads each problem's A (8 B/entry) once
+    abytes = sum(p["A"].numel() * 8 * (r["iters"] + 2) for p, r in zip(probs, res))
+    peaks, peak_src = _peaks()
+    line = {"metric": "ls_solves_per_sec", "value": len(probs) / (t / 1e3), "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"batched_{len(probs)}_m2000-50000_n16-128_cond1e2-1e10_d4n_zeta8_tol1e-12",
+                       "problems": len(probs), "total_A_GB": elems * 8 / 1e9},
+            "lsqr_iters_mean": statistics.mean(iters), "lsqr_iters_max": max(iters),
+            "hbm_gbs_A_stream": abytes / (t / 1e3) / 1e9, "hbm_peak_gbs": float(peaks["hbm_gbs"]),
+            "accuracy": {"backward_error_kw_max_sampled": worst,
+                         "statuses": sorted(set(r["status"] for r in res))},
+            "clocks": clocks}
+    print(json.dumps(line))
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -344,7 +411,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--config", type=int, default=1, choices=[0, 1, 3])
+    ap.add_argument("--batch", type=int, default=4096, help="problems in the batched config")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--native", action="store_true", help="LSQR matvecs on the native FP64 pipe")
     ap.add_argument("--no-e2e", action="store_true")
@@ -358,6 +426,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == 3:
+        run_batch(args)
     else:
         run_gpu(args)
 

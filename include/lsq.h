@@ -197,7 +197,8 @@ lsq_status lsq_solve(lsq_ctx* ctx, const lsq_problem* problem, const lsq_opts* o
  * problems from a device work counter (largest m*n first) and runs all of
  * Algorithm 1 for each by itself (sketch, Householder QR, M, x0, LSQR with
  * block barriers).  A, b and x of every item are device pointers; x receives
- * the solution.  Limits per item: 1 <= n <= 512, n+1 <= d, 1 <= zeta <= 8.
+ * the solution.  Limits per item: 1 <= n <= 256, n+1 <= d, 1 <= zeta <= 8
+ * (larger problems belong to lsq_solve, which uses the whole GPU).
  * The LSQR pass processes 32/L rows per warp with L lanes per row; L is picked
  * per n-range by the context's autotuner (LSQ_FLAG_AUTOTUNE times the
  * candidate shapes on the largest problems of the batch the first time an

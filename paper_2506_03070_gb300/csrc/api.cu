@@ -187,6 +187,7 @@ lsq_status run_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int n, int64_t lda
   p.vec = vec_ok(A, lda);
   p.a_ring = p.vec && (n % 2 == 0);
   p.check_df = false;
+  p.ring_k = 1;
   p.M = M;
   p.Mt = Mt;
   p.x = x;
@@ -617,10 +618,10 @@ lsq_status lsq_solve_batch(lsq_ctx* ctx, const lsq_batch_item* items, int64_t co
   int n_max = 0, d_max = 0, ring_elems = 0;
   for (int64_t i = 0; i < count; ++i) {
     const lsq_batch_item& it = items[i];
-    if (it.m < 1 || it.n < 1 || it.n > 512 || it.lda < it.n || it.d < it.n + 1 || it.d > (1 << 20) || it.zeta < 1 ||
+    if (it.m < 1 || it.n < 1 || it.n > 256 || it.lda < it.n || it.d < it.n + 1 || it.d > (1 << 20) || it.zeta < 1 ||
         it.zeta > 8 || it.zeta > it.d || !it.A || !it.b || !it.x)
       return fail(ctx, LSQ_ERR_ARG, "batch item " + std::to_string(i) +
-                                        ": need 1 <= n <= 512, lda >= n, n+1 <= d, 1 <= zeta <= min(8, d), pointers");
+                                        ": need 1 <= n <= 256, lda >= n, n+1 <= d, 1 <= zeta <= min(8, d), pointers");
     m_max = std::max(m_max, it.m);
     n_max = std::max(n_max, (int)it.n);
     ring_elems = std::max(ring_elems, batch_ring_elems((int)it.n));
@@ -657,7 +658,7 @@ lsq_status lsq_solve_batch(lsq_ctx* ctx, const lsq_batch_item* items, int64_t co
 
   // ---- autotuner: time each candidate shape on the largest problems of an untuned n-range
   if (flags & LSQ_FLAG_AUTOTUNE) {
-    for (int bk = 0; bk < 5; ++bk) {
+    for (int bk = 0; bk < 4; ++bk) {
       if (batch_get_shape(ctx->tuning, bk) >= 0) continue;
       std::vector<int32_t> sub;
       for (int32_t i : order)

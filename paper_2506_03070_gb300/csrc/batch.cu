@@ -143,20 +143,28 @@ __device__ void householder_block(double* W, int d, int n, int ncol, double* rdi
   }
 }
 
+// Doubles of ring per buffer in the batched kernel: chunks of about 4 KB.
+constexpr int kBatchChunk = 512;
+
 template <int S>
-__device__ void lsqr_shape(LsqrParams& p, double* ring, uint64_t* bars, double* s_scal, uint32_t& seq) {
-  DfPass<shape_L(S), shape_P(S)> pass{ring, bars, s_scal, seq};
+__device__ void lsqr_shape(LsqrParams& p, double* ring, uint64_t* bars, double* s_scal, uint32_t& seq,
+                           float2* s_w) {
+  constexpr int R = 32 / shape_L(S);
+  const int kk = kBatchChunk / (R * (int)p.ldi);
+  p.ring_k = kk > 1 ? kk : 1;
+  DfPass<shape_L(S), shape_P(S), true> pass{ring, bars, s_scal, seq, s_w};
   lsqr_body(p, pass, s_scal);
   seq = pass.seq;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) k_batch(BatchParams bp) {
+__global__ void __launch_bounds__(kThreads, 2) k_batch(BatchParams bp) {
   extern __shared__ __align__(128) double s_ring[];
   __shared__ __align__(8) uint64_t s_bars[kWarps * kNbuf];
   __shared__ double s_scal[kWarps * 4];
   __shared__ double scratch[32];
   __shared__ uint64_t s_sgn[kWarps * 32];
   __shared__ int s_prob;
+  __shared__ __align__(16) float2 s_w[512];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   if (lane == 0) {
     for (int b = 0; b < kNbuf; ++b) mbar_init(&s_bars[wib * kNbuf + b], 1u);
@@ -273,13 +281,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_batch(BatchParams bp) {
     p.status = status;
     p.out = bp.out + (int64_t)idx * kOutSlots;
     switch (it.shape) {
-      case 0: lsqr_shape<0>(p, s_ring, s_bars, s_scal, seq); break;
-      case 1: lsqr_shape<1>(p, s_ring, s_bars, s_scal, seq); break;
-      case 2: lsqr_shape<2>(p, s_ring, s_bars, s_scal, seq); break;
-      case 3: lsqr_shape<3>(p, s_ring, s_bars, s_scal, seq); break;
-      case 4: lsqr_shape<4>(p, s_ring, s_bars, s_scal, seq); break;
-      case 5: lsqr_shape<5>(p, s_ring, s_bars, s_scal, seq); break;
-      default: lsqr_shape<6>(p, s_ring, s_bars, s_scal, seq); break;
+      case 0: lsqr_shape<0>(p, s_ring, s_bars, s_scal, seq, s_w); break;
+      case 1: lsqr_shape<1>(p, s_ring, s_bars, s_scal, seq, s_w); break;
+      case 2: lsqr_shape<2>(p, s_ring, s_bars, s_scal, seq, s_w); break;
+      case 3: lsqr_shape<3>(p, s_ring, s_bars, s_scal, seq, s_w); break;
+      case 4: lsqr_shape<4>(p, s_ring, s_bars, s_scal, seq, s_w); break;
+      default: lsqr_shape<5>(p, s_ring, s_bars, s_scal, seq, s_w); break;
     }
     __syncthreads();
   }
@@ -291,10 +298,9 @@ void shape_candidates(int n, std::vector<int>& out) {
   if (n <= 32) out = {0, 2};
   else if (n <= 64) out = {1, 2};
   else if (n <= 128) out = {3, 4};
-  else if (n <= 256) out = {5};
-  else out = {6};
+  else out = {5};
 }
-int bucket_of(int n) { return n <= 32 ? 0 : n <= 64 ? 1 : n <= 128 ? 2 : n <= 256 ? 3 : 4; }
+int bucket_of(int n) { return n <= 32 ? 0 : n <= 64 ? 1 : n <= 128 ? 2 : 3; }
 
 }  // namespace
 
@@ -309,13 +315,12 @@ struct BatchTuning {
 BatchTuning* batch_tuning_new() { return new BatchTuning(); }
 void batch_tuning_free(BatchTuning* t) { delete t; }
 
-// Ring doubles one warp step of a problem with n columns can need, over the
-// shapes the autotuner may pick for n (rows per step x padded row length).
+// Ring doubles per buffer a problem with n columns can need: a chunk of
+// about kBatchChunk doubles, or one step (rows per step x padded row) if larger.
 int batch_ring_elems(int n) {
   const int ldi = (n + 1) / 2 * 2;
-  if (n <= 64) return 4 * ldi;
-  if (n <= 128) return 2 * ldi;
-  return ldi;
+  const int step = (n <= 64 ? 4 : n <= 128 ? 2 : 1) * ldi;
+  return step > kBatchChunk ? step : kBatchChunk;
 }
 
 size_t batch_smem_bytes(int ring_elems) {

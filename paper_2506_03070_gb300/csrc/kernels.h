@@ -45,6 +45,7 @@ struct LsqrParams {
   bool a_ring;       // A rows can come through bulk copies (n even, lda even, A 16-byte aligned)
   bool vec;          // A rows allow 16-byte vector loads (lda even, A aligned)
   bool check_df;     // accuracy pass in pair arithmetic on the image (batched problems)
+  int ring_k;        // consecutive row steps per ring buffer (1 for the single-problem kernel)
   const double* M;   // n x n row-major (upper triangular), may be null in check mode
   const double* Mt;  // transpose of M, row-major
   double* x;         // in: start, out: solution

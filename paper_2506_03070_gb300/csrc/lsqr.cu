@@ -35,12 +35,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_df(LsqrParams p) {
   extern __shared__ __align__(128) double s_ring[];
   __shared__ __align__(8) uint64_t s_bars[kWarps * kNbuf];
   __shared__ double s_scal[kWarps * 4];
+  __shared__ __align__(16) float2 s_w[64 * T];
   if ((threadIdx.x & 31) == 0) {
     for (int b = 0; b < kNbuf; ++b) mbar_init(&s_bars[(threadIdx.x >> 5) * kNbuf + b], 1u);
     fence_proxy_async_smem();
   }
   __syncthreads();
-  DfPass<32, T> pass{s_ring, s_bars, s_scal, 0u};
+  DfPass<32, T> pass{s_ring, s_bars, s_scal, 0u, s_w};
   p.gidx = blockIdx.x;
   p.gcount = gridDim.x;
   lsqr_body(p, pass, s_scal);

@@ -235,35 +235,42 @@ __device__ void m_apply_update(const LsqrParams& p, double ainv, double cx, doub
 // each, as FP64); later passes stream the image: identical values, and the
 // per-entry integer split leaves the hot loop.
 // --------------------------------------------------------------------------
-template <int L, int PPL>
+template <int L, int PPL, bool CHUNKED = false>
 struct DfPass {
   static constexpr int R = 32 / L;
-  double* ring;     // dynamic shared memory [kWarps][kNbuf][R][ldi]
+  double* ring;     // dynamic shared memory [kWarps][kNbuf][p.ring_k * R * ldi]
   uint64_t* bars;   // [kWarps][kNbuf]
   double* s_scal;
-  uint32_t seq;     // warp steps this warp has taken through the ring (all passes)
+  uint32_t seq;     // ring buffers this warp has consumed (all passes)
+  float2* s_w;      // shared [>= ldi]: the pass vector as float pairs
 
+  // Chunk c of the group's rows: K = p.ring_k consecutive steps of R rows.
   template <bool FROM_IMAGE>
-  __device__ void issue(const LsqrParams& p, int64_t r0, int64_t r1, int wib, uint32_t j, double* myring,
+  __device__ void issue(const LsqrParams& p, int64_t r0, int64_t r1, int wib, uint32_t jc, double* myring,
                         uint64_t* mybars) {
-    const int64_t row0 = r0 + ((int64_t)wib + (int64_t)kWarps * j) * R;
-    const int rows = (int)min((int64_t)R, r1 - row0);
-    const uint32_t b = (seq + j) % kNbuf;
-    double* dst = myring + (size_t)b * R * p.ldi;
+    const int K = CHUNKED ? p.ring_k : 1;
+    const int64_t crow = r0 + ((int64_t)wib + (int64_t)kWarps * jc) * K * R;
+    const int rows = (int)min((int64_t)K * R, r1 - crow);
+    const uint32_t b = (seq + jc) % kNbuf;
+    double* dst = myring + (size_t)b * K * R * p.ldi;
     if (FROM_IMAGE) {
       const uint32_t bytes = (uint32_t)(rows * p.ldi) * 8u;
       mbar_arrive_expect_tx(mybars + b, bytes);
-      bulk_g2s(dst, p.asplit + row0 * p.ldi, bytes, mybars + b);
+      bulk_g2s(dst, p.asplit + crow * p.ldi, bytes, mybars + b);
+    } else if (p.lda == p.n) {
+      const uint32_t bytes = (uint32_t)(rows * p.n) * 8u;
+      mbar_arrive_expect_tx(mybars + b, bytes);
+      bulk_g2s(dst, p.A + crow * p.lda, bytes, mybars + b);
     } else {
       const uint32_t rb = (uint32_t)p.n * 8u;
       mbar_arrive_expect_tx(mybars + b, rb * (uint32_t)rows);
-      for (int r = 0; r < rows; ++r) bulk_g2s(dst + (size_t)r * p.ldi, p.A + (row0 + r) * p.lda, rb, mybars + b);
+      for (int r = 0; r < rows; ++r) bulk_g2s(dst + (size_t)r * p.ldi, p.A + (crow + r) * p.lda, rb, mybars + b);
     }
   }
 
-  // Wait (bounded) for the buffer of step j.  Returns false on timeout (warp-uniform).
-  __device__ bool wait(uint32_t j, uint64_t* mybars) {
-    const uint32_t s = seq + j, b = s % kNbuf, par = (s / kNbuf) & 1u;
+  // Wait (bounded) for the buffer of chunk jc.  Returns false on timeout (warp-uniform).
+  __device__ bool wait(uint32_t jc, uint64_t* mybars) {
+    const uint32_t s = seq + jc, b = s % kNbuf, par = (s / kNbuf) & 1u;
     bool timed_out = false;
     if (!mbar_try_wait(mybars + b, par)) {
       const unsigned long long t0 = globaltimer_ns();
@@ -305,125 +312,138 @@ struct DfPass {
   // FROM_IMAGE: rows come from the image through the ring; else from A (split
   // on the fly) -- through the ring when p.a_ring, by direct loads otherwise --
   // and, when WRITE_IMAGE, the split rows are stored to the image.  FRO adds
-  // sum A_ij^2 (in pair arithmetic) to slot 2.
+  // sum A_ij^2 (in pair arithmetic) to slot 2.  Warp w takes chunks
+  // w, w+8, ... of K steps (K*R consecutive rows), one ring buffer per chunk.
   template <bool UIN_B, bool UIN2, bool STORE, bool FROM_IMAGE, bool WRITE_IMAGE, bool FRO>
   __device__ void run(const LsqrParams& p, const double* __restrict__ wvec, double wsign, double gamma) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int seg = lane / L, cl = lane % L;
     const int G = p.gcount, blk = p.gidx;
-    const int n = p.n;
+    const int n = p.n, K = CHUNKED ? p.ring_k : 1;
     const int64_t r0 = (p.m * blk) / G, r1 = (p.m * (blk + 1)) / G;
-    const int64_t nsteps = (r1 - r0 + R - 1) / R;
-    const uint32_t count = nsteps > wib ? (uint32_t)((nsteps - wib + kWarps - 1) / kWarps) : 0u;
+    const int64_t crows = (int64_t)K * R;
+    const int64_t nchunks = (r1 - r0 + crows - 1) / crows;
+    const uint32_t count = nchunks > wib ? (uint32_t)((nchunks - wib + kWarps - 1) / kWarps) : 0u;
     const bool use_ring = FROM_IMAGE || p.a_ring;
-    double* myring = ring + (size_t)wib * kNbuf * R * p.ldi;
+    double* myring = ring + (size_t)wib * kNbuf * crows * p.ldi;
     uint64_t* mybars = bars + wib * kNbuf;
     float2* ubuf = reinterpret_cast<float2*>(p.u);
     double* gw = p.gpart + ((int64_t)blk * kWarps + wib) * p.npad;
 
-    df wv[2 * PPL], Gc[2 * PPL];
-#pragma unroll
-    for (int t = 0; t < PPL; ++t) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int c = 2 * cl + 2 * L * t + h;
-        const double v = c < n ? wsign * wvec[c] : 0.0;
-        const float v1 = __double2float_rn(v);
-        wv[2 * t + h] = df{v1, __double2float_rn(v - (double)v1)};
-        Gc[2 * t + h] = df{0.f, 0.f};
-      }
+    // the pass vector as float pairs in shared memory (read per entry)
+    for (int c = threadIdx.x; c < p.ldi; c += kThreads) {
+      const double v = c < n ? wsign * wvec[c] : 0.0;
+      const float v1 = __double2float_rn(v);
+      s_w[c] = make_float2(v1, __double2float_rn(v - (double)v1));
     }
+    __syncthreads();
+    df Gc[2 * PPL];
+#pragma unroll
+    for (int q = 0; q < 2 * PPL; ++q) Gc[q] = df{0.f, 0.f};
     const float g1 = __double2float_rn(gamma);
     const df gdf{g1, __double2float_rn(gamma - (double)g1)};
     df ss{0.f, 0.f}, bb{0.f, 0.f}, fro{0.f, 0.f};
     bool first_flush = true;
+    uint32_t steps = 0;
 
     if (lane == 0 && use_ring) {
       fence_proxy_async_smem();
-      for (uint32_t j = 0; j < count && j < (uint32_t)kNbuf; ++j)
-        issue<FROM_IMAGE>(p, r0, r1, wib, j, myring, mybars);
+      for (uint32_t jc = 0; jc < count && jc < (uint32_t)kNbuf; ++jc)
+        issue<FROM_IMAGE>(p, r0, r1, wib, jc, myring, mybars);
     }
     bool ok = true;
-    uint32_t j = 0;
-    for (; j < count; ++j) {
-      if (use_ring && !wait(j, mybars)) {
+    uint32_t jc = 0;
+    for (; jc < count; ++jc) {
+      if (use_ring && !wait(jc, mybars)) {
         ok = false;
         break;
       }
-      const int64_t row = r0 + ((int64_t)wib + (int64_t)kWarps * j) * R + seg;
-      const bool valid = row < r1;
-      const double* buf = myring + ((size_t)((seq + j) % kNbuf) * R + seg) * p.ldi;
-      // u_i (or b_i) is needed only after the row dot: load it first
-      double bi = 0.0;
-      float2 uu = make_float2(0.f, 0.f);
-      if (valid) {
-        if (UIN_B)
-          bi = p.b[row];
-        else
-          uu = ubuf[row];
-      }
-      float h[2 * PPL], mm[2 * PPL];
-#pragma unroll
-      for (int t = 0; t < PPL; ++t) {
-        const int c = 2 * cl + 2 * L * t;
-        const bool in = valid && c < n;
-        if (FROM_IMAGE) {
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (in) v = *reinterpret_cast<const float4*>(buf + c);
-          h[2 * t] = v.x;
-          mm[2 * t] = v.y;
-          h[2 * t + 1] = v.z;
-          mm[2 * t + 1] = v.w;
-        } else {
-          double2 v = make_double2(0.0, 0.0);
-          if (p.a_ring) {
-            if (in) v = *reinterpret_cast<const double2*>(buf + c);
-          } else if (in) {
-            const double* Ar = p.A + row * p.lda;
-            v.x = __ldcs(Ar + c);
-            if (c + 1 < n) v.y = __ldcs(Ar + c + 1);
-          }
-          split2(v.x, h[2 * t], mm[2 * t]);
-          split2(v.y, h[2 * t + 1], mm[2 * t + 1]);
-          if (WRITE_IMAGE && in)
-            *reinterpret_cast<float4*>(p.asplit + row * p.ldi + c) = make_float4(h[2 * t], mm[2 * t], h[2 * t + 1],
-                                                                                 mm[2 * t + 1]);
+      const int64_t crow = r0 + ((int64_t)wib + (int64_t)kWarps * jc) * crows;
+      const double* cbuf = myring + (size_t)((seq + jc) % kNbuf) * crows * p.ldi;
+      for (int s = 0; s < K; ++s, ++steps) {
+        const int64_t row = crow + (int64_t)s * R + seg;
+        // unchunked single-row steps: every issued step is a real row
+        const bool valid = (CHUNKED || R > 1) ? row < r1 : true;
+        if (CHUNKED && !__any_sync(0xffffffffu, valid)) break;  // past the end of the group's rows
+        const double* buf = cbuf + (size_t)(s * R + seg) * p.ldi;
+        // u_i (or b_i) is needed only after the row dot: load it first
+        double bi = 0.0;
+        float2 uu = make_float2(0.f, 0.f);
+        if (valid) {
+          if (UIN_B)
+            bi = p.b[row];
+          else
+            uu = ubuf[row];
         }
+        float h[2 * PPL], mm[2 * PPL];
+#pragma unroll
+        for (int t = 0; t < PPL; ++t) {
+          const int c = 2 * cl + 2 * L * t;
+          const bool in = valid && c < n;
+          if (FROM_IMAGE) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (in) v = *reinterpret_cast<const float4*>(buf + c);
+            h[2 * t] = v.x;
+            mm[2 * t] = v.y;
+            h[2 * t + 1] = v.z;
+            mm[2 * t + 1] = v.w;
+          } else {
+            double2 v = make_double2(0.0, 0.0);
+            if (p.a_ring) {
+              if (in) v = *reinterpret_cast<const double2*>(buf + c);
+            } else if (in) {
+              const double* Ar = p.A + row * p.lda;
+              v.x = __ldcs(Ar + c);
+              if (c + 1 < n) v.y = __ldcs(Ar + c + 1);
+            }
+            split2(v.x, h[2 * t], mm[2 * t]);
+            split2(v.y, h[2 * t + 1], mm[2 * t + 1]);
+            if (WRITE_IMAGE && in)
+              *reinterpret_cast<float4*>(p.asplit + row * p.ldi + c) =
+                  make_float4(h[2 * t], mm[2 * t], h[2 * t + 1], mm[2 * t + 1]);
+          }
+        }
+        // row dot: two independent pair accumulators (short chains)
+        constexpr int kAcc = (2 * PPL) >= 2 ? 2 : 1;
+        df av[kAcc];
+#pragma unroll
+        for (int k = 0; k < kAcc; ++k) av[k] = df{0.f, 0.f};
+#pragma unroll
+        for (int t = 0; t < PPL; ++t) {
+          const int c = 2 * cl + 2 * L * t;
+          float4 ww = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (c < n) ww = *reinterpret_cast<const float4*>(s_w + c);
+          df_fma_acc(av[(2 * t) % kAcc], h[2 * t], mm[2 * t], ww.x, ww.y);
+          df_fma_acc(av[(2 * t + 1) % kAcc], h[2 * t + 1], mm[2 * t + 1], ww.z, ww.w);
+        }
+        df dot = av[0];
+#pragma unroll
+        for (int k = 1; k < kAcc; ++k) dot = df_add(dot, av[k]);
+#pragma unroll
+        for (int o = L / 2; o > 0; o >>= 1) dot = df_add_unnorm(dot, shfl_xor_df(dot, o));
+        dot = df_renorm(dot);
+        df y{0.f, 0.f};
+        if (valid) {
+          const df ui = UIN_B ? df_from_double(bi) : df{uu.x, uu.y};
+          y = df_add(dot, df_neg(df_mul(gdf, ui)));
+          if (STORE && cl == 0) ubuf[row] = make_float2(y.hi, y.lo);
+          ss = df_add(ss, df_mul(y, y));
+          if (UIN2) bb = df_add(bb, df_mul(ui, ui));
+        }
+#pragma unroll
+        for (int q = 0; q < 2 * PPL; ++q) {
+          df_fma_acc(Gc[q], h[q], mm[q], y.hi, y.lo);
+          if (steps & 1u) Gc[q] = df_renorm(Gc[q]);
+          if (FRO) df_fma_acc(fro, h[q], mm[q], h[q], mm[q]);
+        }
+        if (FRO) fro = df_renorm(fro);
+        if ((steps & 31u) == 31u) flush(Gc, gw, cl, seg, n, first_flush);
       }
       __syncwarp();
-      if (lane == 0 && use_ring && j + kNbuf < count) {
+      if (lane == 0 && use_ring && jc + kNbuf < count) {
         fence_proxy_async_smem();
-        issue<FROM_IMAGE>(p, r0, r1, wib, j + kNbuf, myring, mybars);
+        issue<FROM_IMAGE>(p, r0, r1, wib, jc + kNbuf, myring, mybars);
       }
-      // row dot: two independent pair accumulators (short chains)
-      constexpr int kAcc = (2 * PPL) >= 2 ? 2 : 1;
-      df av[kAcc];
-#pragma unroll
-      for (int k = 0; k < kAcc; ++k) av[k] = df{0.f, 0.f};
-#pragma unroll
-      for (int q = 0; q < 2 * PPL; ++q) df_fma_acc(av[q % kAcc], h[q], mm[q], wv[q].hi, wv[q].lo);
-      df dot = av[0];
-#pragma unroll
-      for (int k = 1; k < kAcc; ++k) dot = df_add(dot, av[k]);
-#pragma unroll
-      for (int o = L / 2; o > 0; o >>= 1) dot = df_add_unnorm(dot, shfl_xor_df(dot, o));
-      dot = df_renorm(dot);
-      df y{0.f, 0.f};
-      if (valid) {
-        const df ui = UIN_B ? df_from_double(bi) : df{uu.x, uu.y};
-        y = df_add(dot, df_neg(df_mul(gdf, ui)));
-        if (STORE && cl == 0) ubuf[row] = make_float2(y.hi, y.lo);
-        ss = df_add(ss, df_mul(y, y));
-        if (UIN2) bb = df_add(bb, df_mul(ui, ui));
-      }
-#pragma unroll
-      for (int q = 0; q < 2 * PPL; ++q) {
-        df_fma_acc(Gc[q], h[q], mm[q], y.hi, y.lo);
-        if (j & 1u) Gc[q] = df_renorm(Gc[q]);
-        if (FRO) df_fma_acc(fro, h[q], mm[q], h[q], mm[q]);
-      }
-      if (FRO) fro = df_renorm(fro);
-      if ((j & 31u) == 31u) flush(Gc, gw, cl, seg, n, first_flush);
     }
     if (!ok) {
       // give up: flag, then let the copies already issued land before leaving
@@ -431,7 +451,7 @@ struct DfPass {
         atomicOr(p.status, DS_TIMEOUT);
         atomicExch(&p.bar->abort, 1u);
       }
-      for (uint32_t k = j; k < count && k < j + kNbuf; ++k) wait(k, mybars);
+      for (uint32_t k = jc; k < count && k < jc + kNbuf; ++k) wait(k, mybars);
     }
     if (use_ring) seq += count;  // ring phases advance only when rows went through it
     flush(Gc, gw, cl, seg, n, first_flush);
@@ -478,7 +498,7 @@ struct DfPass {
   // Accuracy pass: native FP64 on the original A (single-problem kernel), or
   // in pair arithmetic on the image (batched problems, p.check_df).
   __device__ void check(LsqrParams& p) {
-    if (p.check_df && p.asplit) {
+    if (CHUNKED && p.check_df && p.asplit) {
       p.gparts = p.gcount * kWarps;
       run<true, true, false, true, false, true>(p, p.x, -1.0, -1.0);
       return;

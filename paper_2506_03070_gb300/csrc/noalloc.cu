@@ -108,6 +108,7 @@ extern "C" lsq_status lsq_check_noalloc(const double* A, int64_t m, int64_t n, i
   p.vec = vec;
   p.a_ring = false;
   p.check_df = false;
+  p.ring_k = 1;
   p.bar = bar;
   p.status = status;
   p.out = out;

@@ -34,7 +34,7 @@ def _dev(a):
 
 
 SHAPES = [(3000, 16), (2001, 17), (5000, 33), (1500, 64), (4099, 65), (2500, 100), (3001, 128), (800, 1),
-          (6000, 129), (2000, 200), (1200, 301), (5000, 512), (900, 2), (4000, 127)]
+          (6000, 129), (2000, 200), (1200, 255), (5000, 256), (900, 2), (4000, 127)]
 
 
 def test_batch_matches_standalone_and_oracle(ctx, orc):
@@ -100,6 +100,9 @@ def test_batch_item_errors(ctx):
     assert e.value.status == -1
     with pytest.raises(P.LsqError):
         ctx.lsq_solve_batch([dict(good, d=10)])
+    big = torch.zeros((600, 257), dtype=torch.float64, device="cuda")
+    with pytest.raises(P.LsqError):
+        ctx.lsq_solve_batch([{"A": big, "b": torch.zeros(600, dtype=torch.float64, device="cuda")}])
     # a rank-deficient item reports LSQ_ERR_RANK; the others still solve
     Ar = A.copy()
     Ar[:, 4] = 0.0
