@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -270,6 +271,193 @@ def run_batch(args):
     print(json.dumps(line))
 
 
+def make_bank(count, bank_bytes, device, seed=4040, m_lo=1e4, m_hi=2e6, n_lo=32, n_hi=1000):
+    """Serving workload bodies: `count` problems whose (m, n, cond) form a
+    Latin hypercube over log-uniform m in [m_lo, m_hi], n in [n_lo, n_hi] and
+    cond in [1e2, 1e10] (cheap construction of synth, d = 4n, zeta = 8),
+    trimmed from the largest down until the bodies fit in bank_bytes."""
+    import math
+
+    import numpy as np
+
+    from paper_2506_03070_gb300 import synth
+    rng = np.random.default_rng(seed)
+    strata = [rng.permutation(count) for _ in range(3)]
+    specs = []
+    for k in range(count):
+        q = [(strata[a][k] + rng.uniform()) / count for a in range(3)]
+        m = int(round(math.exp(math.log(m_lo) + q[0] * (math.log(m_hi) - math.log(m_lo)))))
+        n = int(round(math.exp(math.log(n_lo) + q[1] * (math.log(n_hi) - math.log(n_lo)))))
+        cond = 10.0 ** (2 + 8 * q[2])
+        specs.append((m, n, cond))
+    while sum(8 * m * n for m, n, _ in specs) > bank_bytes:
+        specs.remove(max(specs, key=lambda s: s[0] * s[1]))
+    import torch
+    bank = []
+    for k, (m, n, cond) in enumerate(specs):
+        p = synth.batched_problem(m, n, cond, seed=seed * 1009 + k, device=device)
+        bank.append({"A": p["A"], "b": p["b"], "m": m, "n": n, "d": 4 * n})
+        del p
+    torch.cuda.empty_cache()
+    return bank
+
+
+def _oracle_cost_model():
+    """Oracle seconds per request from unit costs timed on one bounded
+    problem (20000 x 200, d = 800): sketch per entry of [A|b], Householder QR
+    per flop 2 d (n+1)^2, one LSQR pass per entry of A."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    from paper_2506_03070_gb300 import synth
+    m, n, d = 20000, 200, 800
+    p = synth.batched_problem(m, n, 1e6, seed=3, device="cpu")
+    A, b = p["A"].numpy(), p["b"].numpy()
+    t0 = time.perf_counter()
+    Y = oracle.sketch_apply(A, b, d, 8, 1)
+    t_sk = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    R, _, _ = oracle.householder_qr(Y)
+    M = oracle.tri_inverse(R[:n, :n])
+    t_qr = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.lsqr(A, b, M, M @ R[:n, n], 0.0, 3)
+    t_l = time.perf_counter() - t0
+    return {"sketch_per_entry": t_sk / (m * (n + 1)), "qr_per_flop": t_qr / (2.0 * d * (n + 1) ** 2),
+            "pass_per_entry": t_l / (1 + 2 * 3) / (m * n),
+            "sample": "oracle timed on one 20000x200 problem (sketch d=800, QR+inverse, 3 LSQR iterations); "
+                      "per-request time = sketch + QR + (2 iters + 2) passes from those unit costs"}
+
+
+def run_serve(args):
+    """Config 4: Poisson arrivals of least-squares problems through
+    lsq_submit / lsq_poll.  Latency runs from each request's scheduled
+    arrival to the library's completion time stamp."""
+    import numpy as np
+    import torch
+
+    import paper_2506_03070_gb300 as P
+    import __graft_entry__
+    __graft_entry__.build()
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    bank = make_bank(args.bank_count, int(args.bank_gb * 1e9), dev)
+    ctx = P.Context(local)
+    ctx.lsq_serve_config(arena_bytes=int(args.arena_gb * 1e9))
+    # the autotuner picks the small-problem pass shapes (untimed)
+    small = [dict(A=bk["A"], b=bk["b"], d=bk["d"], seed=1) for bk in bank if bk["n"] <= 256][:64]
+    if small:
+        ctx.lsq_solve_batch(small, tol=1e-12, flags=P.FLAG_AUTOTUNE)
+    rng = np.random.default_rng(args.serve_seed)
+
+    def stream_run(nreq, rate, tag):
+        body = rng.integers(0, len(bank), nreq)
+        gaps = rng.exponential(1.0 / rate, nreq)
+        arrive = np.cumsum(gaps) - gaps[0]
+        xs = [torch.empty(bank[k]["n"], dtype=torch.float64, device=dev) for k in body]
+        torch.cuda.synchronize()
+        out = [None] * nreq
+        open_t = {}
+        t0 = time.monotonic() + 0.05
+        nxt = 0
+        ndone = 0
+        while ndone < nreq:
+            now = time.monotonic()
+            while nxt < nreq and t0 + arrive[nxt] <= now:
+                bk = bank[body[nxt]]
+                open_t[nxt] = ctx.lsq_submit(bk["A"], bk["b"], bk["d"], seed=nxt + 1, tol=1e-12, x=xs[nxt])
+                nxt += 1
+            for i in list(open_t)[:256]:
+                r = ctx.lsq_poll(open_t[i])
+                if r is not None:
+                    out[i] = r
+                    del open_t[i]
+                    ndone += 1
+            if not open_t:
+                time.sleep(min(1e-4, max(0.0, t0 + arrive[nxt] - time.monotonic()) if nxt < nreq else 1e-4))
+        lat = np.array([out[i][2]["t_done_s"] - (t0 + arrive[i]) for i in range(nreq)]) * 1e3
+        t_end = max(out[i][2]["t_done_s"] for i in range(nreq))
+        span = t_end - t0
+        statuses = sorted(set(int(o[0]) for o in out))
+        abytes = sum(8.0 * bank[body[i]]["m"] * bank[body[i]]["n"] * (out[i][2]["iters"] + 2) for i in range(nreq))
+        # accuracy on a sample (outside the timed region)
+        import oracle
+        worst = 0.0
+        for i in range(0, nreq, max(1, nreq // 12)):
+            bk = bank[body[i]]
+            if 8 * bk["m"] * bk["n"] <= 2e9:  # the check itself needs a copy of A
+                worst = max(worst, oracle.backward_error_kw(bk["A"], bk["b"], out[i][1]))
+        groups = [o[2]["group_blocks"] for o in out]
+        return {"tag": tag, "requests": nreq, "rate_per_s": rate, "solves_per_s": nreq / span, "span_s": span,
+                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                               "mean": float(lat.mean()), "max": float(lat.max())},
+                "hbm_gbs_A_stream": abytes / span / 1e9, "statuses": statuses,
+                "backward_error_kw_max_sampled": worst,
+                "group_blocks": {"min": min(groups), "median": float(np.median(groups)), "max": max(groups)},
+                "lsqr_iters_mean": float(np.mean([o[2]["iters"] for o in out])), "body": body}
+
+    # warm-up: a few requests through the server
+    warm = stream_run(min(32, args.requests), args.rate, "warmup")
+    launches0 = ctx.lsq_serve_stats()["server_launches"]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    sat = stream_run(args.requests, args.rate, "saturated")
+    clocks = sampler.stop()
+    stats = ctx.lsq_serve_stats()
+    launches = stats["server_launches"] - launches0
+    sub = stream_run(args.sub_requests, args.sub_rate, "sub_saturation") if args.sub_requests > 0 else None
+    # sequential plain solves (whole-GPU lsq_solve, one problem at a time) on
+    # the same request mix, a bounded sample
+    seq_idx = sat["body"][: args.seq_sample]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j, k in enumerate(seq_idx):
+        bk = bank[k]
+        ctx.lsq_solve(bk["A"], bk["b"], bk["d"], seed=j + 1, tol=1e-12)
+    t_seq = time.perf_counter() - t0
+    seq_rate = len(seq_idx) / t_seq
+    peaks, peak_src = _peaks()
+    peak = float(peaks["hbm_gbs"])
+    for r in (warm, sat, sub):
+        if r is not None:
+            r.pop("body", None)
+    line = {"metric": "ls_solves_per_sec", "value": sat["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+            "steps": args.requests, "warmup": warm["requests"], "ms_per_step": 1e3 / sat["solves_per_s"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"serving_poisson{args.rate:g}_{args.requests}req_m1e4-2e6_n32-1000"
+                                   f"_cond1e2-1e10_d4n_zeta8_tol1e-12",
+                       "bank_bodies": len(bank), "bank_GB": sum(8 * b["m"] * b["n"] for b in bank) / 1e9,
+                       "arena_GB": args.arena_gb,
+                       "l2_policy": "inputs larger than L2 (bodies up to %.1f GB)" %
+                                    (max(8 * b["m"] * b["n"] for b in bank) / 1e9)},
+            "latency_ms": sat["latency_ms"],
+            "roofline": {"bound": "hbm", "kernel": "k_serve", "achieved": sat["hbm_gbs_A_stream"], "peak": peak,
+                         "unit": "GB/s", "frac": sat["hbm_gbs_A_stream"] / peak, "traffic": None,
+                         "peak_source": f"{peak_src} hbm_gbs", "note": "A-stream bytes (8mn per pass) / wall span"},
+            "gpu_launches": launches,
+            "saturated": sat, "sub_saturation": sub,
+            "sequential_plain_solves": {"solves_per_s": seq_rate, "sample": len(seq_idx),
+                                        "serving_over_sequential": sat["solves_per_s"] / seq_rate},
+            "serve_stats": stats, "clocks": clocks}
+    if not args.no_cpu_baseline:
+        cm = _oracle_cost_model()
+        tot = 0.0
+        for k in seq_idx:
+            bk = bank[k]
+            m, n, d = bk["m"], bk["n"], bk["d"]
+            it = 2 * (10 * math.ceil(math.log(1e-12) / math.log(math.sqrt(n / d)))) // 10
+            tot += (cm["sketch_per_entry"] * m * (n + 1) + cm["qr_per_flop"] * 2.0 * d * (n + 1) ** 2
+                    + cm["pass_per_entry"] * m * n * (2 * it + 2))
+        line["cpu_baseline"] = {"value": len(seq_idx) / tot, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                "sample": cm["sample"] + f"; applied to the first {len(seq_idx)} requests "
+                                          "(an extrapolation)"}
+    print(json.dumps(line))
+    ctx.close()
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -411,7 +599,16 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=1, choices=[0, 1, 3])
+    ap.add_argument("--config", type=int, default=1, choices=[0, 1, 3, 4])
+    ap.add_argument("--requests", type=int, default=10000, help="serving: requests in the Poisson stream")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean arrival rate (1/s)")
+    ap.add_argument("--sub-requests", type=int, default=1000, help="serving: requests of the extra sub-saturation run")
+    ap.add_argument("--sub-rate", type=float, default=150.0, help="serving: arrival rate of the extra run")
+    ap.add_argument("--bank-count", type=int, default=64, help="serving: problem bodies (Latin hypercube)")
+    ap.add_argument("--bank-gb", type=float, default=60.0, help="serving: device memory for problem bodies")
+    ap.add_argument("--arena-gb", type=float, default=150.0, help="serving: HBM budget for admitted requests")
+    ap.add_argument("--seq-sample", type=int, default=100, help="serving: requests timed as sequential solves")
+    ap.add_argument("--serve-seed", type=int, default=7)
     ap.add_argument("--batch", type=int, default=4096, help="problems in the batched config")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--native", action="store_true", help="LSQR matvecs on the native FP64 pipe")
@@ -428,6 +625,8 @@ def main():
         run_reference(args)
     elif args.config == 3:
         run_batch(args)
+    elif args.config == 4:
+        run_serve(args)
     else:
         run_gpu(args)
 

@@ -106,6 +106,12 @@ typedef struct {
   int32_t precond_fallback;  /* 1: the mixed form's preconditioner stalled LSQR and the
                                 plain form solved the problem again */
   float t_sketch_ms, t_precond_ms, t_lsqr_ms, t_check_ms, t_h2d_ms, t_d2h_ms;
+  /* lsq_submit / lsq_poll only: host monotonic clock (CLOCK_MONOTONIC) in
+   * seconds when the request was submitted, handed to the device, and seen
+   * complete; and the number of blocks that solved it together. */
+  double t_submit_s, t_start_s, t_done_s;
+  int32_t group_blocks;
+  int32_t reserved;
 } lsq_info;
 
 /* Context on `device` with a workspace budget of hbm_budget_bytes (0 = 90% of
@@ -152,14 +158,19 @@ lsq_status lsq_precond(lsq_ctx* ctx, const void* Y, int64_t d, int64_t n, int64_
  * App. D.5.1.  A, b, x0, x device.  x receives the final iterate.  Stops when
  * ||(AM)^T r|| <= tol ||AM||_est ||r|| (Paige-Saunders test 2 on the
  * preconditioned problem), ||r|| <= tol ||b||, or at maxit (LSQ_ERR_NOCONV).
- * info may be NULL. */
+ * info may be NULL.  Limits: n <= 4096 (LSQ_ERR_UNSUPPORTED beyond);
+ * LSQ_FLAG_NATIVE_FP64 only for n <= 512.  The same limits hold for
+ * lsq_solve and lsq_check. */
 lsq_status lsq_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
                     const double* M, const double* x0, double tol, int64_t maxit, int32_t flags, double* x,
                     lsq_info* info, void* stream);
 
 /* Accuracy of a candidate solution: one pass over A computing r = b - A x,
  * A^T r, ||A||_F and the two backward-error bounds of lsq_info (M may be NULL;
- * then backward_error_pre is 0).  All device pointers. */
+ * then backward_error_pre is 0).  All device pointers.  For n <= 512 the pass
+ * runs on the FP64 pipe; wider rows are summed in double-float arithmetic on
+ * A's entries split to 47 significant bits, which moves the reported backward
+ * error by at most 2^-47 (it is the backward error for A + E, |E| <= 2^-47 |A|). */
 lsq_status lsq_check(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
                      const double* x, const double* M, lsq_info* info, void* stream);
 
@@ -225,6 +236,53 @@ typedef struct {
 
 lsq_status lsq_solve_batch(lsq_ctx* ctx, const lsq_batch_item* items, int64_t count, double tol, int64_t maxit,
                            int32_t flags, lsq_batch_result* results, void* stream);
+
+/* ---- Serving: asynchronous solves of problems that arrive over time -----
+ * lsq_submit queues a problem and returns at once with a ticket; lsq_poll
+ * reports LSQ_PENDING until the solve is complete, then its final status
+ * (and fills info), after which the ticket is gone.
+ *
+ * Behind it runs a persistent request loop: one cooperative kernel keeps
+ * every block of the GPU resident and takes requests from a queue in mapped
+ * host memory as they arrive.  A request is solved by a group of G blocks
+ * (G from the problem's size: 1 for small problems, up to the whole grid for
+ * the largest), which claim it in arrival order, so requests that arrive
+ * while others are on the GPU start as soon as blocks free up and run beside
+ * them.  Each group runs Algorithm 1 end to end (sketch, Householder QR,
+ * M = R^{-1}, x0, LSQR, accuracy pass) with barriers over its own blocks.
+ * Small problems (n <= 256) use the LSQR pass shape the context's autotuner
+ * picked for their n-range (see lsq_solve_batch, LSQ_FLAG_AUTOTUNE).
+ * A host thread admits queued requests in arrival order while their device
+ * memory (sketch, R, M, LSQR vectors, the float-pair image of A, and A, b, x
+ * themselves for host problems) fits in the serving arena: the budget is the
+ * admission limit, and A, R and the LSQR state stay on the device for the
+ * whole solve.  While requests are in flight the server occupies the GPU:
+ * synchronous calls on the same device run after it drains.
+ *
+ * Limits: FP64 form only, 1 <= n <= 1024, n+1 <= d, 1 <= zeta <= 8.
+ * A, b (and x) must stay valid until lsq_poll reports completion; for
+ * LSQ_MEM_HOST problems they are host memory (pinned memory copies fastest),
+ * A and b are copied in when the request is admitted and x is copied out when
+ * it completes.  Returns LSQ_ERR_BUDGET only if the problem alone does not
+ * fit the arena.  Several host threads may submit and poll concurrently. */
+typedef int64_t lsq_ticket;
+
+lsq_status lsq_submit(lsq_ctx* ctx, const lsq_problem* problem, const lsq_opts* opts, double* x, lsq_ticket* out);
+lsq_status lsq_poll(lsq_ctx* ctx, lsq_ticket ticket, lsq_info* info);
+
+/* Serving configuration; takes effect only before the first lsq_submit.
+ * arena_bytes: device memory for admitted requests (0 = the context's budget
+ * minus the synchronous workspace it holds); cta_bytes: bytes of A per block
+ * when sizing a request's group (0 = 4 MiB). */
+lsq_status lsq_serve_config(lsq_ctx* ctx, size_t arena_bytes, double cta_bytes);
+
+typedef struct {
+  int64_t submitted, completed, pending, in_flight;
+  int64_t server_launches;  /* launches of the persistent server kernel */
+  int64_t grid_blocks;      /* blocks of one launch */
+  size_t arena_bytes, arena_peak_bytes;
+} lsq_serve_stats;
+lsq_status lsq_serve_stats_get(lsq_ctx* ctx, lsq_serve_stats* out);
 
 #ifdef __cplusplus
 }

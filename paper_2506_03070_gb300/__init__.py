@@ -8,7 +8,8 @@ the library's CUDA kernels; this module only marshals arguments: torch tensors
 the calls raise.
 
 Functions carry the C names: ``lsq_sketch_indices``, ``lsq_sketch``,
-``lsq_precond``, ``lsq_lsqr``, ``lsq_check``, ``lsq_solve``.
+``lsq_precond``, ``lsq_lsqr``, ``lsq_check``, ``lsq_solve``,
+``lsq_solve_batch``, ``lsq_submit``, ``lsq_poll``.
 """
 from __future__ import annotations
 
@@ -24,14 +25,15 @@ LSQ_OK, LSQ_PENDING = 0, 1
 STATUS = {0: "LSQ_OK", 1: "LSQ_PENDING", -1: "LSQ_ERR_ARG", -2: "LSQ_ERR_CUDA", -3: "LSQ_ERR_OOM",
           -4: "LSQ_ERR_BUDGET", -5: "LSQ_ERR_SKETCH", -6: "LSQ_ERR_RANK", -7: "LSQ_ERR_NOCONV",
           -8: "LSQ_ERR_TIMEOUT", -9: "LSQ_ERR_NONFINITE", -10: "LSQ_ERR_UNSUPPORTED"}
-LSQ_ERR_NOCONV = -7
+LSQ_ERR_ARG, LSQ_ERR_NOCONV = -1, -7
 PREC_FP64, PREC_MIXED = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
 FLAG_TIMING, FLAG_NO_CHECK, FLAG_NATIVE_FP64, FLAG_NO_IMAGE, FLAG_NO_FALLBACK = 1, 2, 4, 8, 16
 
 EXPORTS = ("lsq_create", "lsq_destroy", "lsq_last_error", "lsq_status_string", "lsq_workspace_bytes",
            "lsq_sketch_indices", "lsq_sketch", "lsq_precond", "lsq_lsqr", "lsq_check", "lsq_solve",
-           "lsq_check_noalloc", "lsq_solve_batch")
+           "lsq_check_noalloc", "lsq_solve_batch", "lsq_submit", "lsq_poll", "lsq_serve_config",
+           "lsq_serve_stats_get")
 
 
 class LsqError(RuntimeError):
@@ -58,7 +60,9 @@ class Info(ctypes.Structure):
                 ("anorm_fro", ctypes.c_double), ("xnorm", ctypes.c_double), ("bnorm", ctypes.c_double),
                 ("sketch_rounds_max", ctypes.c_int32), ("precond_fallback", ctypes.c_int32),
                 ("t_sketch_ms", ctypes.c_float), ("t_precond_ms", ctypes.c_float), ("t_lsqr_ms", ctypes.c_float),
-                ("t_check_ms", ctypes.c_float), ("t_h2d_ms", ctypes.c_float), ("t_d2h_ms", ctypes.c_float)]
+                ("t_check_ms", ctypes.c_float), ("t_h2d_ms", ctypes.c_float), ("t_d2h_ms", ctypes.c_float),
+                ("t_submit_s", ctypes.c_double), ("t_start_s", ctypes.c_double), ("t_done_s", ctypes.c_double),
+                ("group_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -80,6 +84,15 @@ class BatchResult(ctypes.Structure):
 
 
 FLAG_AUTOTUNE = 32
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("pending", ctypes.c_int64),
+                ("in_flight", ctypes.c_int64), ("server_launches", ctypes.c_int64), ("grid_blocks", ctypes.c_int64),
+                ("arena_bytes", ctypes.c_size_t), ("arena_peak_bytes", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 _lib = None
 
@@ -111,8 +124,12 @@ def load(path: str = LIB_PATH):
     L.lsq_check_noalloc.restype = i32
     L.lsq_solve_batch.argtypes = [P, ctypes.POINTER(BatchItem), i64, f64, i64, i32, ctypes.POINTER(BatchResult), P]
     L.lsq_solve_batch.restype = i32
+    L.lsq_submit.argtypes = [P, ctypes.POINTER(Problem), ctypes.POINTER(Opts), P, ctypes.POINTER(ctypes.c_int64)]
+    L.lsq_poll.argtypes = [P, i64, ctypes.POINTER(Info)]
+    L.lsq_serve_config.argtypes = [P, ctypes.c_size_t, f64]
+    L.lsq_serve_stats_get.argtypes = [P, ctypes.POINTER(ServeStats)]
     for name in ("lsq_create", "lsq_destroy", "lsq_sketch_indices", "lsq_sketch", "lsq_precond", "lsq_lsqr",
-                 "lsq_check", "lsq_solve"):
+                 "lsq_check", "lsq_solve", "lsq_submit", "lsq_poll", "lsq_serve_config", "lsq_serve_stats_get"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -157,6 +174,7 @@ class Context:
             raise LsqError(st, "lsq_create failed (no usable GPU?)")
         self.h = h
         self.device = device
+        self._live = {}  # ticket -> (A, b, x): buffers the library reads or writes until completion
 
     def close(self):
         if getattr(self, "h", None):
@@ -278,6 +296,66 @@ class Context:
         st = self.lib.lsq_solve(self.h, ctypes.byref(pr), ctypes.byref(op), _ptr(x), ctypes.byref(info), strm)
         self._check(st, allow=(LSQ_OK, LSQ_ERR_NOCONV) if allow_noconv else (LSQ_OK,))
         return x, info.as_dict()
+
+    # -- serving -------------------------------------------------------------
+    def lsq_serve_config(self, arena_bytes=0, cta_bytes=0.0):
+        self._check(self.lib.lsq_serve_config(self.h, arena_bytes, cta_bytes))
+
+    def lsq_submit(self, A, b, d, zeta=8, seed=0, tol=1e-12, maxit=0, flags=0, x=None):
+        """Queue a problem for the persistent request loop; returns a ticket.
+        A, b: CUDA float64 tensors or numpy float64 arrays (host problem).
+        They (and x) are kept referenced here until lsq_poll reports the
+        request complete."""
+        import torch
+        if isinstance(A, np.ndarray):
+            if A.dtype != np.float64 or A.ndim != 2 or A.strides[1] != 8:
+                raise ValueError("host A must be a row-major float64 array")
+            b = np.ascontiguousarray(b, dtype=np.float64)
+            m, n = A.shape
+            lda = A.strides[0] // 8
+            mem = MEM_HOST
+            if x is None:
+                x = np.empty(n, dtype=np.float64)
+        else:
+            _dev_f64(A, "A")
+            _dev_f64(b, "b")
+            m, n, lda = _rowmajor(A)
+            mem = MEM_DEVICE
+            if x is None:
+                x = torch.empty((n,), dtype=torch.float64, device=A.device)
+        pr = Problem(_ptr(A), _ptr(b), m, n, lda, mem, 0)
+        op = Opts(d, zeta, PREC_FP64, seed, tol, maxit, flags, 0)
+        t = ctypes.c_int64()
+        self._check(self.lib.lsq_submit(self.h, ctypes.byref(pr), ctypes.byref(op), _ptr(x), ctypes.byref(t)))
+        self._live[t.value] = (A, b, x)
+        return t.value
+
+    def lsq_poll(self, ticket):
+        """None while the request is pending; else (status, x, info dict)."""
+        info = Info()
+        st = self.lib.lsq_poll(self.h, ticket, ctypes.byref(info))
+        if st == LSQ_PENDING:
+            return None
+        if st == LSQ_ERR_ARG and ticket not in self._live:
+            self._check(st)
+        _, _, x = self._live.pop(ticket, (None, None, None))
+        return st, x, info.as_dict()
+
+    def lsq_wait(self, ticket, timeout=600.0, sleep=50e-6):
+        import time
+        t0 = time.monotonic()
+        while True:
+            r = self.lsq_poll(ticket)
+            if r is not None:
+                return r
+            if time.monotonic() - t0 > timeout:
+                raise TimeoutError(f"ticket {ticket} still pending after {timeout} s")
+            time.sleep(sleep)
+
+    def lsq_serve_stats(self):
+        s = ServeStats()
+        self._check(self.lib.lsq_serve_stats_get(self.h, ctypes.byref(s)))
+        return s.as_dict()
 
 
 def lsq_check_noalloc(A, b, x, M=None, stream=None):

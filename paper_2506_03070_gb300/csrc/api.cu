@@ -8,28 +8,9 @@
 #include <cstring>
 #include <string>
 
-#include "kernels.h"
+#include "ctx.h"
 
 using namespace lsq;
-
-struct lsq_ctx {
-  int device = 0;
-  int sms = 0;
-  size_t budget = 0;
-  std::string err;
-  // grown-on-demand workspace (one allocation, carved per call)
-  char* ws = nullptr;
-  size_t ws_size = 0;
-  // small persistent device words
-  uint32_t* d_status = nullptr;
-  int32_t* d_max_rounds = nullptr;
-  GridBarrier* d_bar = nullptr;
-  double* d_out = nullptr;
-  // pinned host mirror of the small words
-  void* h_small = nullptr;
-  // batched solves: tuned LSQR pass shapes per n-range
-  BatchTuning* tuning = nullptr;
-};
 
 namespace {
 
@@ -258,6 +239,8 @@ lsq_status lsq_create(lsq_ctx** out, int device, size_t hbm_budget_bytes) {
 lsq_status lsq_destroy(lsq_ctx* ctx) {
   if (!ctx) return LSQ_ERR_ARG;
   cudaSetDevice(ctx->device);
+  if (ctx->server) server_destroy(ctx->server);
+  ctx->server = nullptr;
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->h_small) cudaFreeHost(ctx->h_small);
@@ -369,7 +352,9 @@ lsq_status lsq_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t
   if ((s = check_ctx(ctx)) != LSQ_OK) return s;
   if (m < 1 || n < 1 || lda < n) return fail(ctx, LSQ_ERR_ARG, "need m >= 1, n >= 1, lda >= n");
   if (!A || !b || !M || !x0 || !x) return fail(ctx, LSQ_ERR_ARG, "null pointer");
-  if (n > 512) return fail(ctx, LSQ_ERR_UNSUPPORTED, "LSQR kernel built for n <= 512");
+  if (n > kLsqrMaxN) return fail(ctx, LSQ_ERR_UNSUPPORTED, "LSQR kernels built for n <= 4096");
+  if ((flags & LSQ_FLAG_NATIVE_FP64) && !lsqr_native_ok(n))
+    return fail(ctx, LSQ_ERR_UNSUPPORTED, "native FP64 LSQR kernel built for n <= 512");
   cudaStream_t st = (cudaStream_t)stream;
   const int ni = (int)n, npad = (int)((n + 31) / 32 * 32);
   bool native = (flags & LSQ_FLAG_NATIVE_FP64) || !lsqr_df_ok(A, n, lda);
@@ -383,9 +368,9 @@ lsq_status lsq_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t
     probe = Carver{nullptr};
     carve_lsqr(probe, m, ni, npad, grid, false);
   }
-  if (!native && !image && !(vec_ok(A, lda) && n % 2 == 0)) {
+  if (!native && !image && !(vec_ok(A, lda) && n % 2 == 0) && lsqr_native_ok(n)) {
     // without the image every pass streams A through the bulk-copy ring,
-    // which needs even n and lda and an aligned A
+    // which needs even n and lda and an aligned A (wide rows load directly)
     native = true;
     grid = lsqr_grid(ni, vec_ok(A, lda), native, ctx->sms);
     probe = Carver{nullptr};
@@ -414,10 +399,13 @@ lsq_status lsq_check(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_
   if ((s = check_ctx(ctx)) != LSQ_OK) return s;
   if (m < 1 || n < 1 || lda < n) return fail(ctx, LSQ_ERR_ARG, "need m >= 1, n >= 1, lda >= n");
   if (!A || !b || !x) return fail(ctx, LSQ_ERR_ARG, "null pointer");
-  if (n > 512) return fail(ctx, LSQ_ERR_UNSUPPORTED, "check kernel built for n <= 512");
+  if (n > kLsqrMaxN) return fail(ctx, LSQ_ERR_UNSUPPORTED, "check kernels built for n <= 4096");
   cudaStream_t st = (cudaStream_t)stream;
   const int ni = (int)n, npad = (int)((n + 31) / 32 * 32);
-  const int grid = lsqr_grid(ni, vec_ok(A, lda), true, ctx->sms);
+  // FP64 pass for n <= 512; wider rows go through the pair-arithmetic panel pass
+  const bool native = lsqr_native_ok(n);
+  const int grid = lsqr_grid(ni, vec_ok(A, lda), native, ctx->sms);
+  if (grid < 1) return fail(ctx, LSQ_ERR_CUDA, "no launchable check configuration");
   Carver probe{nullptr};
   carve_lsqr(probe, m, ni, npad, grid);
   if ((s = ensure_ws(ctx, probe.off)) != LSQ_OK) return s;
@@ -426,7 +414,7 @@ lsq_status lsq_check(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_
   if ((s = reset_small(ctx, st)) != LSQ_OK) return s;
   if (M) CK(transpose_square(M, ni, w.Mt, st));
   if ((s = run_lsqr(ctx, A, m, ni, lda, b, M, M ? w.Mt : nullptr, const_cast<double*>(x), 0.0, 0, 1, w, grid, npad,
-                    true, st)) != LSQ_OK)
+                    native, st)) != LSQ_OK)
     return s;
   uint32_t bits = 0;
   double out[kOutSlots];
@@ -447,7 +435,9 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
   if (d < n + 1) return fail(ctx, LSQ_ERR_ARG, "need d >= n + 1");
   if (o->prec != LSQ_PREC_FP64 && o->prec != LSQ_PREC_MIXED) return fail(ctx, LSQ_ERR_ARG, "unknown precision");
   if (pr->mem != LSQ_MEM_DEVICE && pr->mem != LSQ_MEM_HOST) return fail(ctx, LSQ_ERR_ARG, "unknown memory kind");
-  if (n > 512) return fail(ctx, LSQ_ERR_UNSUPPORTED, "LSQR kernel built for n <= 512");
+  if (n > kLsqrMaxN) return fail(ctx, LSQ_ERR_UNSUPPORTED, "LSQR kernels built for n <= 4096");
+  if ((o->flags & LSQ_FLAG_NATIVE_FP64) && !lsqr_native_ok(n))
+    return fail(ctx, LSQ_ERR_UNSUPPORTED, "native FP64 LSQR kernel built for n <= 512");
   cudaStream_t st = (cudaStream_t)stream;
   const bool host = pr->mem == LSQ_MEM_HOST;
   const bool timing = (o->flags & LSQ_FLAG_TIMING) != 0;
@@ -495,7 +485,7 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
     carve(probe, &A0, &b0, &x0, &Y0, &pb0, &R0, &M0, &lw0);
     if (image && probe.off > ctx->budget) {
       image = false;  // no room for the float-pair image: split A on the fly
-      if (!(vec && n % 2 == 0)) {
+      if (!(vec && n % 2 == 0) && lsqr_native_ok(n)) {
         // every pass would stream A through the bulk-copy ring: needs even n, lda
         native = true;
         grid = lsqr_grid(ni, vec, native, ctx->sms);
@@ -503,7 +493,7 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
       probe = Carver{nullptr};
       carve(probe, &A0, &b0, &x0, &Y0, &pb0, &R0, &M0, &lw0);
     }
-    if (!native && !image && !(vec && n % 2 == 0)) {
+    if (!native && !image && !(vec && n % 2 == 0) && lsqr_native_ok(n)) {
       native = true;
       grid = lsqr_grid(ni, vec, native, ctx->sms);
       probe = Carver{nullptr};

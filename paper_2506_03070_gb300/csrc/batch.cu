@@ -16,17 +16,10 @@
 #include <numeric>
 #include <vector>
 
-#include "lsqr_device.cuh"
-#include "sketch.cuh"
+#include "problem_device.cuh"
 
 namespace lsq {
 namespace {
-
-constexpr int kBatchShapes = 7;
-// (lanes per row, column pairs per lane) of the double-float pass
-__host__ __device__ constexpr int shape_L(int s) { return s == 0 ? 8 : s == 1 ? 8 : s == 2 ? 16 : s == 3 ? 16 : s == 4 ? 32 : s == 5 ? 32 : 32; }
-__host__ __device__ constexpr int shape_P(int s) { return s == 0 ? 2 : s == 1 ? 4 : s == 2 ? 2 : s == 3 ? 4 : s == 4 ? 2 : s == 5 ? 4 : 8; }
-__host__ __device__ constexpr int shape_maxn(int s) { return 2 * shape_L(s) * shape_P(s); }
 
 struct BatchItem {
   const double* A;
@@ -54,108 +47,6 @@ struct BatchParams {
   uint32_t* status;  // count
   GridBarrier* bar;  // abort flag holder (never waited on)
 };
-
-__device__ int64_t default_maxit_dev(int n, int d, double tol) {
-  const double rate = sqrt((double)n / (double)d);
-  if (!(tol > 0.0) || !(rate < 1.0)) return 1000;
-  return (int64_t)(10.0 * ceil(log(tol) / log(rate)));
-}
-
-// Block-local sketch: warps take 32 rows at a time; lane l draws the column of
-// S for row base+l; the warp then adds +-A_ij/sqrt(zeta) into Y (L2 reductions).
-__device__ void sketch_block(const BatchItem& it, double* Y, int ldy, int32_t* s_idx, uint64_t* s_sgn,
-                             uint32_t* status) {
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  int32_t* my_idx = s_idx + wib * 32 * 8;
-  const int n = it.n, ncol = n + 1;
-  const double scale = 1.0 / sqrt((double)it.zeta);
-  bool bad = false;
-  for (int64_t base = (int64_t)wib * 32; base < it.m; base += (int64_t)kWarps * 32) {
-    const int64_t row = base + lane;
-    if (row < it.m) {
-      int32_t c[8];
-      uint64_t signs;
-      const int r = sketch_column<8>(it.seed, (uint64_t)row, (uint64_t)it.d, it.zeta, c, signs);
-      if (r < 0) atomicOr(status, DS_SKETCH);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) my_idx[lane * 8 + k] = c[k];
-      s_sgn[wib * 32 + lane] = signs;
-    }
-    __syncwarp();
-    const int nrows = (int)min((int64_t)32, it.m - base);
-    for (int rr = 0; rr < nrows; ++rr) {
-      const int64_t i = base + rr;
-      const double* Ai = it.A + i * it.lda;
-      const uint64_t sg = s_sgn[wib * 32 + rr];
-      const int32_t* ci = my_idx + rr * 8;
-      for (int j = lane; j < ncol; j += 32) {
-        const double a = j < n ? __ldcs(Ai + j) : it.b[i];
-        bad |= !isfinite(a);
-        const double sa = a * scale;
-        for (int k = 0; k < it.zeta; ++k) {
-          const double v = __longlong_as_double(__double_as_longlong(sa) ^ ((long long)(((sg >> k) & 1ull) == 0ull) << 63));
-          atomicAdd(Y + (int64_t)ci[k] * ldy + j, v);
-        }
-      }
-    }
-    __syncwarp();
-  }
-  if (bad) atomicOr(status, DS_NONFINITE);
-}
-
-// Block-local Householder QR of the d x ncol column-major W (same reflector
-// convention as the single-problem kernel); rdiag gets R's diagonal, R[k][j]
-// stays in W[j][k].
-__device__ void householder_block(double* W, int d, int n, int ncol, double* rdiag, double* scratch) {
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  for (int k = 0; k < n; ++k) {
-    const double* wk = W + (int64_t)k * d;
-    double part = 0.0;
-    for (int i = k + 1 + threadIdx.x; i < d; i += kThreads) part = fma(__ldcg(wk + i), __ldcg(wk + i), part);
-    const double sigma = block_sum(part, scratch);
-    const double alpha = __ldcg(wk + k);
-    double beta = alpha, tau = 0.0, inv_v0 = 0.0;
-    if (sigma != 0.0) {
-      const double nrm = sqrt(fma(alpha, alpha, sigma));
-      beta = alpha >= 0.0 ? -nrm : nrm;
-      tau = (beta - alpha) / beta;
-      inv_v0 = 1.0 / (alpha - beta);
-    }
-    if (threadIdx.x == 0) rdiag[k] = beta;
-    if (tau != 0.0) {
-      for (int j = k + 1 + wib; j < ncol; j += kWarps) {
-        double* wj = W + (int64_t)j * d;
-        double s0 = 0.0, s1 = 0.0;
-        int i = k + 1 + lane;
-        for (; i + 32 < d; i += 64) {
-          s0 = fma(__ldcg(wk + i), __ldcg(wj + i), s0);
-          s1 = fma(__ldcg(wk + i + 32), __ldcg(wj + i + 32), s1);
-        }
-        if (i < d) s0 = fma(__ldcg(wk + i), __ldcg(wj + i), s0);
-        const double s = warp_allreduce_sum(s0 + s1);
-        const double f = tau * fma(inv_v0, s, __ldcg(wj + k));
-        const double fv = f * inv_v0;
-        if (lane == 0) wj[k] = __ldcg(wj + k) - f;
-        for (int i2 = k + 1 + lane; i2 < d; i2 += 32) wj[i2] = fma(-fv, __ldcg(wk + i2), __ldcg(wj + i2));
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// Doubles of ring per buffer in the batched kernel: chunks of about 4 KB.
-constexpr int kBatchChunk = 512;
-
-template <int S>
-__device__ void lsqr_shape(LsqrParams& p, double* ring, uint64_t* bars, double* s_scal, uint32_t& seq,
-                           float2* s_w) {
-  constexpr int R = 32 / shape_L(S);
-  const int kk = kBatchChunk / (R * (int)p.ldi);
-  p.ring_k = kk > 1 ? kk : 1;
-  DfPass<shape_L(S), shape_P(S), true> pass{ring, bars, s_scal, seq, s_w};
-  lsqr_body(p, pass, s_scal);
-  seq = pass.seq;
-}
 
 __global__ void __launch_bounds__(kThreads, 2) k_batch(BatchParams bp) {
   extern __shared__ __align__(128) double s_ring[];
@@ -191,10 +82,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(BatchParams bp) {
     double* rdiag = reinterpret_cast<double*>(slab + bp.oRd);
     double* vec = reinterpret_cast<double*>(slab + bp.oVec);
 
+    const Group g{0, 1, bp.bar, status};
     // ---- sketch Y = S [A | b]
-    for (int e = threadIdx.x; e < d * ldy; e += kThreads) Y[e] = 0.0;
+    zero_group(Y, (int64_t)d * ldy, g);
     __syncthreads();
-    sketch_block(it, Y, ldy, reinterpret_cast<int32_t*>(s_ring), s_sgn, status);
+    sketch_group(it.A, it.b, it.m, n, it.lda, d, it.zeta, it.seed, Y, ldy, reinterpret_cast<int32_t*>(s_ring), s_sgn,
+                 g);
     __threadfence_block();
     __syncthreads();
     // ---- Householder QR of Y (column-major copy), R, M = R^{-1}, x0 = M z
@@ -202,51 +95,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(BatchParams bp) {
       const int i = e / ncol, j = e % ncol;
       W[(int64_t)j * d + i] = __ldcg(Y + e);
     }
-    __syncthreads();
-    householder_block(W, d, n, ncol, rdiag, scratch);
-    double mx = 0.0;
-    for (int i = threadIdx.x; i < n; i += kThreads) mx = fmax(mx, fabs(rdiag[i]));
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) scratch[wib] = mx;
-    __syncthreads();
-    mx = 0.0;
-    for (int w = 0; w < kWarps; ++w) mx = fmax(mx, scratch[w]);
-    __syncthreads();
-    const double thr = (double)n * 2.220446049250313e-16 * mx;
-    for (int e = threadIdx.x; e < n * n; e += kThreads) {
-      const int i = e / n, j = e % n;
-      R[e] = j < i ? 0.0 : (j == i ? rdiag[i] : __ldcg(W + (int64_t)j * d + i));
-      if (i == j && !(fabs(rdiag[i]) > thr)) atomicOr(status, DS_RANK);
-    }
-    __syncthreads();
-    for (int c = wib; c < n; c += kWarps) {  // column c of M by back substitution, as row c of Mt
-      double* mc = Mt + (int64_t)c * n;
-      for (int i = c + 1 + lane; i < n; i += 32) mc[i] = 0.0;
-      if (lane == 0) mc[c] = 1.0 / R[(int64_t)c * n + c];
-      __syncwarp();
-      for (int i = c - 1; i >= 0; --i) {
-        const double* Ri = R + (int64_t)i * n;
-        double s = 0.0;
-        for (int k = i + 1 + lane; k <= c; k += 32) s = fma(Ri[k], mc[k], s);
-        s = warp_allreduce_sum(s);
-        if (lane == 0) mc[i] = -s / Ri[i];
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < n * n; e += kThreads) {
-      const int i = e / n, k = e % n;
-      M[e] = Mt[(int64_t)k * n + i];
-    }
-    __syncthreads();
-    for (int i = wib; i < n; i += kWarps) {
-      double s = 0.0;
-      for (int k = i + lane; k < n; k += 32) s = fma(M[(int64_t)i * n + k], __ldcg(W + (int64_t)n * d + k), s);
-      s = warp_allreduce_sum(s);
-      if (lane == 0) it.x[i] = s;
-    }
-    __syncthreads();
-    if (*(volatile uint32_t*)status & (DS_RANK | DS_SKETCH | DS_NONFINITE)) continue;
+    householder_group(W, d, n, ncol, rdiag, scratch, g);
+    precond_group(W, d, n, rdiag, R, M, Mt, it.x, scratch, g);
+    const int failed = threadIdx.x == 0 ? ((*(volatile uint32_t*)status & (DS_RANK | DS_SKETCH | DS_NONFINITE)) != 0)
+                                        : 0;
+    if (__syncthreads_or(failed)) continue;
 
     // ---- preconditioned LSQR from x0, block-local
     LsqrParams p;
@@ -316,11 +169,11 @@ BatchTuning* batch_tuning_new() { return new BatchTuning(); }
 void batch_tuning_free(BatchTuning* t) { delete t; }
 
 // Ring doubles per buffer a problem with n columns can need: a chunk of
-// about kBatchChunk doubles, or one step (rows per step x padded row) if larger.
+// about kChunkDoubles doubles, or one step (rows per step x padded row) if larger.
 int batch_ring_elems(int n) {
   const int ldi = (n + 1) / 2 * 2;
   const int step = (n <= 64 ? 4 : n <= 128 ? 2 : 1) * ldi;
-  return step > kBatchChunk ? step : kBatchChunk;
+  return step > kChunkDoubles ? step : kChunkDoubles;
 }
 
 size_t batch_smem_bytes(int ring_elems) {

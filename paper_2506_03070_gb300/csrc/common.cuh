@@ -87,7 +87,7 @@ __device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) 
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ bool grid_sync(GridBarrier* bar, uint32_t* status) {
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, uint32_t* status, unsigned int nblocks) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -98,7 +98,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, uint32_t* status) {
       const unsigned int g = ld_acquire_u32(&bar->gen);
       __threadfence();
       const unsigned int arrived = atomicAdd(&bar->count, 1u);
-      if (arrived == gridDim.x - 1) {
+      if (arrived == nblocks - 1) {
         bar->count = 0;
         __threadfence();
         st_release_u32(&bar->gen, g + 1);
@@ -125,6 +125,10 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, uint32_t* status) {
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, uint32_t* status) {
+  return grid_sync(bar, status, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,34 @@
+// ctx.h -- the library context behind the opaque lsq_ctx handle (internal).
+#pragma once
+#include <string>
+
+#include "kernels.h"
+
+namespace lsq {
+struct Server;
+// Serving side (serve.cu): stop and free a context's server, if any.
+void server_destroy(Server* s);
+}  // namespace lsq
+
+struct lsq_ctx {
+  int device = 0;
+  int sms = 0;
+  size_t budget = 0;
+  std::string err;
+  // grown-on-demand workspace (one allocation, carved per call)
+  char* ws = nullptr;
+  size_t ws_size = 0;
+  // small persistent device words
+  uint32_t* d_status = nullptr;
+  int32_t* d_max_rounds = nullptr;
+  lsq::GridBarrier* d_bar = nullptr;
+  double* d_out = nullptr;
+  // pinned host mirror of the small words
+  void* h_small = nullptr;
+  // batched solves: tuned LSQR pass shapes per n-range
+  lsq::BatchTuning* tuning = nullptr;
+  // serving: persistent request loop, created by the first lsq_submit
+  lsq::Server* server = nullptr;
+  size_t serve_arena = 0;        // 0: the budget minus the synchronous workspace
+  double serve_cta_bytes = 0.0;  // 0: default bytes of A per block of a request's group
+};

@@ -81,9 +81,13 @@ enum {
   OUT_ANORM_EST,
   kOutSlots = 16
 };
-// True when the double-float LSQR kernel applies (n even and <= 512, lda
-// even, A 16-byte aligned); otherwise the native-FP64 kernel runs.
+// Widest problem of the LSQR kernels (the panel kernel shares a row among
+// up to 8 warps of 512 columns each).
+constexpr int kLsqrMaxN = 4096;
+// True when the double-float LSQR kernel applies (1 <= n <= kLsqrMaxN).
 bool lsqr_df_ok(const double* A, int64_t n, int64_t lda);
+// True when the native-FP64 LSQR kernel (one warp per row) applies: n <= 512.
+bool lsqr_native_ok(int64_t n);
 // Rows of gpart the LSQR kernel needs for a grid (per-warp partials).
 int lsqr_gparts(int grid);
 // Grid size the LSQR kernel will use for n (co-resident blocks).

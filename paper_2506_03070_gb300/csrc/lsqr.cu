@@ -47,6 +47,50 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_df(LsqrParams p) {
   lsqr_body(p, pass, s_scal);
 }
 
+// n > 512: PW warps per row (column panels of at most 512); ring of panel
+// slices, then the pass vector as float pairs, in dynamic shared memory.
+template <int PW>
+__global__ void __launch_bounds__(kThreads, 2) k_lsqr_dfp(LsqrParams p) {
+  extern __shared__ __align__(128) double s_ring[];
+  __shared__ __align__(8) uint64_t s_bars[kWarps * kNbuf];
+  __shared__ __align__(16) double s_scal[kWarps * 6];
+  if ((threadIdx.x & 31) == 0) {
+    for (int b = 0; b < kNbuf; ++b) mbar_init(&s_bars[(threadIdx.x >> 5) * kNbuf + b], 1u);
+    fence_proxy_async_smem();
+  }
+  __syncthreads();
+  float2* s_w = reinterpret_cast<float2*>(s_ring + (size_t)kWarps * kNbuf * 512);
+  DfPass<32, 8, false, PW> pass{s_ring, s_bars, s_scal, 0u, s_w};
+  p.gidx = blockIdx.x;
+  p.gcount = gridDim.x;
+  lsqr_body(p, pass, s_scal);
+}
+
+size_t dfp_smem(int n) { return (size_t)kWarps * kNbuf * 512 * sizeof(double) + (size_t)((n + 1) / 2 * 2) * 8; }
+
+template <int PW>
+int grid_dfp(int n, int sms) {
+  const size_t smem = dfp_smem(n);
+  if (cudaFuncSetAttribute(k_lsqr_dfp<PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lsqr_dfp<PW>, kThreads, smem) != cudaSuccess ||
+      per_sm < 1)
+    return 0;
+  if (per_sm > 2) per_sm = 2;
+  return per_sm * sms;
+}
+
+template <int PW>
+cudaError_t launch_dfp(const LsqrParams& p, int grid, cudaStream_t st) {
+  LsqrParams q = p;
+  void* args[] = {&q};
+  const size_t smem = dfp_smem(p.n);
+  cudaError_t e = cudaFuncSetAttribute(k_lsqr_dfp<PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaLaunchCooperativeKernel((const void*)k_lsqr_dfp<PW>, grid, kThreads, args, smem, st);
+}
+
 size_t df_smem(int T, int n) {
   const size_t ring = (size_t)kWarps * kNbuf * (size_t)((n + 1) / 2 * 2) * sizeof(double);  // one row per step
   const size_t red = (size_t)kWarps * 64 * T * sizeof(double);
@@ -93,11 +137,20 @@ cudaError_t launch_df(const LsqrParams& p, int grid, cudaStream_t st) {
   return cudaLaunchCooperativeKernel((const void*)k_lsqr_df<T>, grid, kThreads, args, smem, st);
 }
 
+// column pairs per lane of the one-warp-per-row kernels (n <= 512)
 int chunks_for(int n) {
   if (n <= 64) return 1;
   if (n <= 128) return 2;
   if (n <= 256) return 4;
   if (n <= 512) return 8;
+  return 0;
+}
+// warps per row of the panel kernel (512 < n <= 4096)
+int panels_for(int n) {
+  if (n <= 512) return 0;
+  if (n <= 1024) return 2;
+  if (n <= 2048) return 4;
+  if (n <= 4096) return 8;
   return 0;
 }
 
@@ -108,10 +161,20 @@ int lsqr_gparts(int grid) { return grid * kWarps; }
 bool lsqr_df_ok(const double* A, int64_t n, int64_t lda) {
   (void)A;
   (void)lda;
-  return chunks_for((int)n) > 0;
+  return n >= 1 && n <= kLsqrMaxN;
 }
 
+bool lsqr_native_ok(int64_t n) { return n >= 1 && n <= 512; }
+
 int lsqr_grid(int n, bool vec, bool native, int sms) {
+  if (!native && n > 512) {
+    switch (panels_for(n)) {
+      case 2: return grid_dfp<2>(n, sms);
+      case 4: return grid_dfp<4>(n, sms);
+      case 8: return grid_dfp<8>(n, sms);
+      default: return 0;
+    }
+  }
   if (!native) {
     switch (chunks_for(n)) {
       case 1: return grid_df<1>(n, sms);
@@ -131,6 +194,14 @@ int lsqr_grid(int n, bool vec, bool native, int sms) {
 }
 
 cudaError_t lsqr_run(const LsqrParams& p, bool vec, bool native, int grid, cudaStream_t st) {
+  if (!native && p.n > 512) {
+    switch (panels_for(p.n)) {
+      case 2: return launch_dfp<2>(p, grid, st);
+      case 4: return launch_dfp<4>(p, grid, st);
+      case 8: return launch_dfp<8>(p, grid, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   if (!native) {
     switch (chunks_for(p.n)) {
       case 1: return launch_df<1>(p, grid, st);

@@ -21,7 +21,7 @@ __device__ __forceinline__ bool group_sync(const LsqrParams& p) {
     __syncthreads();
     return true;
   }
-  return grid_sync(p.bar, p.status);
+  return grid_sync(p.bar, p.status, (unsigned int)p.gcount);
 }
 
 // --------------------------------------------------------------------------
@@ -235,9 +235,10 @@ __device__ void m_apply_update(const LsqrParams& p, double ainv, double cx, doub
 // each, as FP64); later passes stream the image: identical values, and the
 // per-entry integer split leaves the hot loop.
 // --------------------------------------------------------------------------
-template <int L, int PPL, bool CHUNKED = false>
+template <int L, int PPL, bool CHUNKED = false, int PW = 1>
 struct DfPass {
   static constexpr int R = 32 / L;
+  static_assert(PW == 1 || (L == 32 && PPL == 8 && !CHUNKED), "panel pass: one row per step, 512 columns a warp");
   double* ring;     // dynamic shared memory [kWarps][kNbuf][p.ring_k * R * ldi]
   uint64_t* bars;   // [kWarps][kNbuf]
   double* s_scal;
@@ -477,7 +478,212 @@ struct DfPass {
     __syncthreads();
   }
 
+  // ------------------------------------------------------------------------
+  // Wide rows (n > 512): PW warps share each row.  The block's warps form
+  // kWarps/PW row groups; warp pw of a group owns the column panel
+  // [c0, c0 + pwid), c0 = pw * pwid, pwid = ceil(n/PW) rounded up to 16, and
+  // keeps its own bulk-copy ring of panel slices.  Per row: every warp forms
+  // its panel's partial dot, writes it to shared memory, the group meets at a
+  // named barrier, and every warp sums the PW partials in panel order (the
+  // same value in all of them), forms y and adds y * A_i into its own panel's
+  // column accumulators.  Only panel 0 stores y and sums y^2 and u_i^2.  A
+  // warp whose copy wait gives up keeps meeting its group's barriers (on
+  // stale data, with DS_TIMEOUT raised) so the group never waits on it.
+  // ------------------------------------------------------------------------
+  __device__ __forceinline__ void group_bar(int rg) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + rg), "r"(32 * PW) : "memory");
+  }
+
+  template <bool FROM_IMAGE>
+  __device__ void issue_panel(const LsqrParams& p, int64_t row, int c0, int cols, uint32_t jc, double* myring,
+                              uint64_t* mybars) {
+    const uint32_t b = (seq + jc) % kNbuf;
+    double* dst = myring + (size_t)b * 512;
+    const uint32_t bytes = (uint32_t)cols * 8u;
+    mbar_arrive_expect_tx(mybars + b, bytes);
+    if (FROM_IMAGE)
+      bulk_g2s(dst, p.asplit + row * p.ldi + c0, bytes, mybars + b);
+    else
+      bulk_g2s(dst, p.A + row * p.lda + c0, bytes, mybars + b);
+  }
+
+  template <bool UIN_B, bool UIN2, bool STORE, bool FROM_IMAGE, bool WRITE_IMAGE, bool FRO>
+  __device__ void run_panel(const LsqrParams& p, const double* __restrict__ wvec, double wsign, double gamma) {
+    constexpr int NRG = kWarps / PW;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int rg = wib / PW, pw = wib % PW;
+    const int G = p.gcount, blk = p.gidx, n = p.n;
+    const int pwid = ((n + PW - 1) / PW + 15) / 16 * 16;
+    const int c0 = pw * pwid;
+    const int cend = min(c0 + pwid, n);
+    // bulk-copied slice: the panel's columns, padded to the image's even row
+    const int cols = FROM_IMAGE ? (int)min((int64_t)pwid, p.ldi - c0) : cend - c0;
+    const int64_t r0 = (p.m * blk) / G, r1 = (p.m * (blk + 1)) / G;
+    const int64_t nrows = r1 - r0;
+    const uint32_t count = nrows > rg ? (uint32_t)((nrows - rg + NRG - 1) / NRG) : 0u;
+    const bool use_ring = FROM_IMAGE || p.a_ring;
+    double* myring = ring + (size_t)wib * kNbuf * 512;
+    uint64_t* mybars = bars + wib * kNbuf;
+    float2* ubuf = reinterpret_cast<float2*>(p.u);
+    double* gw = p.gpart + ((int64_t)blk * NRG + rg) * p.npad;
+    // s_scal holds kWarps * 6 doubles here: 4 per warp, then [row group][2 parities][PW] pairs
+    df* pdot = reinterpret_cast<df*>(s_scal + kWarps * 4) + rg * 2 * PW;
+
+    for (int c = threadIdx.x; c < p.ldi; c += kThreads) {
+      const double v = c < n ? wsign * wvec[c] : 0.0;
+      const float v1 = __double2float_rn(v);
+      s_w[c] = make_float2(v1, __double2float_rn(v - (double)v1));
+    }
+    __syncthreads();
+    df Gc[2 * PPL];
+#pragma unroll
+    for (int q = 0; q < 2 * PPL; ++q) Gc[q] = df{0.f, 0.f};
+    const float g1 = __double2float_rn(gamma);
+    const df gdf{g1, __double2float_rn(gamma - (double)g1)};
+    df ss{0.f, 0.f}, bb{0.f, 0.f}, fro{0.f, 0.f};
+    bool first_flush = true;
+
+    if (lane == 0 && use_ring) {
+      fence_proxy_async_smem();
+      for (uint32_t jc = 0; jc < count && jc < (uint32_t)kNbuf; ++jc)
+        issue_panel<FROM_IMAGE>(p, r0 + rg + (int64_t)NRG * jc, c0, cols, jc, myring, mybars);
+    }
+    bool ok = true;
+    uint32_t failed_at = count;
+    for (uint32_t jc = 0; jc < count; ++jc) {
+      if (use_ring && ok && !wait(jc, mybars)) {
+        ok = false;
+        failed_at = jc;
+        if (lane == 0) {
+          atomicOr(p.status, DS_TIMEOUT);
+          atomicExch(&p.bar->abort, 1u);
+        }
+      }
+      const int64_t row = r0 + rg + (int64_t)NRG * jc;
+      const double* buf = myring + (size_t)((seq + jc) % kNbuf) * 512;
+      double bi = 0.0;
+      float2 uu = make_float2(0.f, 0.f);
+      if (UIN_B)
+        bi = p.b[row];
+      else
+        uu = ubuf[row];
+      float h[2 * PPL], mm[2 * PPL];
+#pragma unroll
+      for (int t = 0; t < PPL; ++t) {
+        const int c = c0 + 2 * lane + 64 * t;
+        const bool in = c < cend;
+        if (FROM_IMAGE) {
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (in) v = *reinterpret_cast<const float4*>(buf + (c - c0));
+          h[2 * t] = v.x;
+          mm[2 * t] = v.y;
+          h[2 * t + 1] = v.z;
+          mm[2 * t + 1] = v.w;
+        } else {
+          double2 v = make_double2(0.0, 0.0);
+          if (p.a_ring) {
+            if (in) v = *reinterpret_cast<const double2*>(buf + (c - c0));
+          } else if (in) {
+            const double* Ar = p.A + row * p.lda;
+            v.x = __ldcs(Ar + c);
+            if (c + 1 < n) v.y = __ldcs(Ar + c + 1);
+          }
+          split2(v.x, h[2 * t], mm[2 * t]);
+          split2(v.y, h[2 * t + 1], mm[2 * t + 1]);
+          if (WRITE_IMAGE && in)
+            *reinterpret_cast<float4*>(p.asplit + row * p.ldi + c) =
+                make_float4(h[2 * t], mm[2 * t], h[2 * t + 1], mm[2 * t + 1]);
+        }
+      }
+      df av[2] = {df{0.f, 0.f}, df{0.f, 0.f}};
+#pragma unroll
+      for (int t = 0; t < PPL; ++t) {
+        const int c = c0 + 2 * lane + 64 * t;
+        float4 ww = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c < cend) ww = *reinterpret_cast<const float4*>(s_w + c);
+        df_fma_acc(av[0], h[2 * t], mm[2 * t], ww.x, ww.y);
+        df_fma_acc(av[1], h[2 * t + 1], mm[2 * t + 1], ww.z, ww.w);
+      }
+      df dot = df_add(av[0], av[1]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) dot = df_add_unnorm(dot, shfl_xor_df(dot, o));
+      dot = df_renorm(dot);
+      df* slot = pdot + (jc & 1u) * PW;
+      if (lane == 0) slot[pw] = dot;
+      group_bar(rg);
+      dot = slot[0];
+#pragma unroll
+      for (int q = 1; q < PW; ++q) dot = df_add(dot, slot[q]);
+      const df ui = UIN_B ? df_from_double(bi) : df{uu.x, uu.y};
+      const df y = df_add(dot, df_neg(df_mul(gdf, ui)));
+      if (pw == 0) {
+        if (STORE && lane == 0) ubuf[row] = make_float2(y.hi, y.lo);
+        ss = df_add(ss, df_mul(y, y));
+        if (UIN2) bb = df_add(bb, df_mul(ui, ui));
+      }
+#pragma unroll
+      for (int q = 0; q < 2 * PPL; ++q) {
+        df_fma_acc(Gc[q], h[q], mm[q], y.hi, y.lo);
+        if (jc & 1u) Gc[q] = df_renorm(Gc[q]);
+        if (FRO) df_fma_acc(fro, h[q], mm[q], h[q], mm[q]);
+      }
+      if (FRO) fro = df_renorm(fro);
+      if ((jc & 31u) == 31u) flush_panel(Gc, gw, c0, cend, first_flush);
+      __syncwarp();
+      if (lane == 0 && use_ring && ok && jc + kNbuf < count) {
+        fence_proxy_async_smem();
+        issue_panel<FROM_IMAGE>(p, r0 + rg + (int64_t)NRG * (jc + kNbuf), c0, cols, jc + kNbuf, myring, mybars);
+      }
+    }
+    if (!ok) {
+      // let the copies already issued land before the ring is reused
+      for (uint32_t k = failed_at; k < count && k < failed_at + kNbuf; ++k) wait(k, mybars);
+    }
+    if (use_ring) seq += count;
+    flush_panel(Gc, gw, c0, cend, first_flush);
+    double frow = 0.0;
+    if (FRO) frow = warp_allreduce_sum(df_to_double(fro));
+    if (lane == 0) {
+      s_scal[wib * 4 + 0] = df_to_double(ss);
+      s_scal[wib * 4 + 1] = df_to_double(bb);
+      s_scal[wib * 4 + 2] = frow;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      double sum = 0.0;
+      for (int w = 0; w < kWarps; ++w) sum += s_scal[w * 4 + threadIdx.x];
+      p.part[(int64_t)blk * 4 + threadIdx.x] = sum;
+    }
+    __syncthreads();
+  }
+
+  __device__ void flush_panel(df (&Gc)[2 * PPL], double* gw, int c0, int cend, bool& first) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int t = 0; t < PPL; ++t) {
+      const int c = c0 + 2 * lane + 64 * t;
+      if (c < cend) {
+        double2 g = first ? make_double2(0.0, 0.0) : *reinterpret_cast<const double2*>(gw + c);
+        g.x += df_to_double(Gc[2 * t]);
+        g.y += df_to_double(Gc[2 * t + 1]);
+        *reinterpret_cast<double2*>(gw + c) = g;
+      }
+      Gc[2 * t] = Gc[2 * t + 1] = df{0.f, 0.f};
+    }
+    first = false;
+  }
+
   __device__ void init(LsqrParams& p) {
+    if (PW > 1) {
+      p.gparts = p.gcount * (kWarps / PW);
+      if (p.asplit) {
+        run_panel<true, true, true, false, true, false>(p, p.x, -1.0, -1.0);
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+      } else {
+        run_panel<true, true, true, false, false, false>(p, p.x, -1.0, -1.0);
+      }
+      return;
+    }
     p.gparts = p.gcount * kWarps;
     if (p.asplit) {
       run<true, true, true, false, true, false>(p, p.x, -1.0, -1.0);
@@ -489,6 +695,14 @@ struct DfPass {
     }
   }
   __device__ void iter(LsqrParams& p, double gamma) {
+    if (PW > 1) {
+      p.gparts = p.gcount * (kWarps / PW);
+      if (p.asplit)
+        run_panel<false, false, true, true, false, false>(p, p.wv, 1.0, gamma);
+      else
+        run_panel<false, false, true, false, false, false>(p, p.wv, 1.0, gamma);
+      return;
+    }
     p.gparts = p.gcount * kWarps;
     if (p.asplit)
       run<false, false, true, true, false, false>(p, p.wv, 1.0, gamma);
@@ -498,6 +712,16 @@ struct DfPass {
   // Accuracy pass: native FP64 on the original A (single-problem kernel), or
   // in pair arithmetic on the image (batched problems, p.check_df).
   __device__ void check(LsqrParams& p) {
+    if (PW > 1) {
+      // wide rows: the accuracy pass runs in pair arithmetic as well, on the
+      // image when there is one, else on A split on the fly
+      p.gparts = p.gcount * (kWarps / PW);
+      if (p.asplit)
+        run_panel<true, true, false, true, false, true>(p, p.x, -1.0, -1.0);
+      else
+        run_panel<true, true, false, false, false, true>(p, p.x, -1.0, -1.0);
+      return;
+    }
     if (CHUNKED && p.check_df && p.asplit) {
       p.gparts = p.gcount * kWarps;
       run<true, true, false, true, false, true>(p, p.x, -1.0, -1.0);

@@ -268,9 +268,9 @@ def test_solve_edge_shapes(ctx, orc):
     x, info = ctx.lsq_solve(_dev(A), _dev(b), 4, zeta=3, seed=1, tol=1e-12)
     assert orc.backward_error_kw(A, b, x.cpu().numpy()) <= 1e-10
     # n beyond the built kernels
-    A2 = torch.zeros((2000, 513), dtype=torch.float64, device="cuda")
+    A2 = torch.zeros((600, 4097), dtype=torch.float64, device="cuda")
     with pytest.raises(P.LsqError) as e:
-        ctx.lsq_solve(A2, torch.zeros(2000, dtype=torch.float64, device="cuda"), 2100)
+        ctx.lsq_solve(A2, torch.zeros(600, dtype=torch.float64, device="cuda"), 4200)
     assert e.value.status == -10
     # d < n + 1
     with pytest.raises(P.LsqError) as e:
@@ -333,3 +333,65 @@ def test_solve_double_float_repeatable(ctx):
     x2, i2 = ctx.lsq_solve(_dev(A), _dev(b), 400, seed=9, tol=1e-12)
     assert abs(i1["iters"] - i2["iters"]) <= 1
     assert np.linalg.norm(A @ (x1.cpu().numpy() - x2.cpu().numpy())) <= 1e-11 * np.linalg.norm(b)
+
+
+# ------------------------------------------------ wide rows (n > 512) ---
+@pytest.mark.parametrize("m,n,d,lda_pad", [(6000, 513, 1100, 0), (8000, 1000, 2400, 0), (5000, 1100, 2300, 3),
+                                           (9000, 2100, 4300, 0)])
+def test_lsqr_wide_rows_match_oracle(ctx, orc, m, n, d, lda_pad):
+    """Rows shared by 2, 4 or 8 warps (column panels).  M comes from LAPACK's
+    QR of the oracle's sketch (any upper triangular M is a valid input); the
+    iterates must follow the oracle's LSQR."""
+    A, b, xt = _problem(m, n, 1e6, m + n)
+    Yo = orc.sketch_apply(A, b, d, 8, 3)
+    Ro = np.linalg.qr(Yo, mode="r")
+    Mo = orc.tri_inverse(Ro[:n, :n])
+    x0 = Mo @ Ro[:n, n]
+    maxit = orc.default_maxit(n, d, 1e-12)
+    ref = orc.lsqr(A, b, Mo, x0, 1e-12, maxit)
+    if lda_pad:
+        Ap = np.zeros((m, n + lda_pad))
+        Ap[:, :n] = A
+        Ad = _dev(Ap)[:, :n]
+    else:
+        Ad = _dev(A)
+    x, info = ctx.lsq_lsqr(Ad, _dev(b), _dev(Mo), _dev(x0), 1e-12, maxit)
+    x_ni, info_ni = ctx.lsq_lsqr(Ad, _dev(b), _dev(Mo), _dev(x0), 1e-12, maxit, flags=NO_IMAGE)
+    bn = np.linalg.norm(b)
+    if n % 2 == 0 and not lda_pad % 2:
+        assert np.array_equal(x.cpu().numpy(), x_ni.cpu().numpy())
+    for xx, inf in ((x, info), (x_ni, info_ni)):
+        xx = xx.cpu().numpy()
+        assert inf["status"] == 0
+        assert abs(inf["iters"] - ref["iters"]) <= 2, (inf["iters"], ref["iters"])
+        assert np.linalg.norm(A @ (xx - ref["x"])) <= 1e-10 * bn
+        assert orc.backward_error_kw(A, b, xx) <= 1e-10
+    # the FP64-pipe kernel is built for n <= 512 only
+    import paper_2506_03070_gb300 as P
+    with pytest.raises(P.LsqError) as e:
+        ctx.lsq_lsqr(Ad, _dev(b), _dev(Mo), _dev(x0), 1e-12, maxit, flags=NATIVE)
+    assert e.value.status == -10
+
+
+def test_check_wide_rows_matches_oracle(ctx, orc):
+    """Accuracy pass in pair arithmetic for n > 512.  It evaluates r for
+    A + E with |E_ij| <= 2^-47 |A_ij| (split truncation): ||E x|| ~ 1e-13
+    here against ||r|| ~ 5e-7, so rnorm may move by ~2e-7 relative and
+    ||A^T r|| (~3e-7) by a similar relative amount; ||A||_F by <= 2^-47."""
+    A, b, xt = _problem(7001, 700, 1e5, 8)
+    x = xt + 1e-7 * np.random.default_rng(0).standard_normal(700)
+    info = ctx.lsq_check(_dev(A), _dev(b), _dev(x))
+    eta, parts = orc.backward_error(A, b, x, parts=True)
+    assert abs(info["backward_error_ne"] - eta) <= 1e-4 * eta
+    assert abs(info["rnorm"] - parts["rnorm"]) <= 1e-6 * parts["rnorm"]
+    assert abs(info["anorm_fro"] - parts["fro"]) <= 1e-13 * parts["fro"]
+
+
+def test_solve_wide_rows(ctx, orc):
+    """Whole solve (sketch, QR, inverse, LSQR, check) at n = 1000, d = 4n."""
+    A, b, xt = _problem(20000, 1000, 1e8, 31)
+    x, info = ctx.lsq_solve(_dev(A), _dev(b), 4000, zeta=8, seed=11, tol=1e-12)
+    x = x.cpu().numpy()
+    assert info["status"] == 0 and info["stop"] in (1, 2)
+    assert orc.backward_error_kw(A, b, x) <= 1e-10
+    assert np.linalg.norm(A @ (x - xt)) <= 1e-10 * np.linalg.norm(b)
