@@ -345,11 +345,18 @@ def run_serve(args):
     dev = f"cuda:{local}"
     bank = make_bank(args.bank_count, int(args.bank_gb * 1e9), dev)
     ctx = P.Context(local)
-    ctx.lsq_serve_config(arena_bytes=int(args.arena_gb * 1e9))
-    # the autotuner picks the small-problem pass shapes (untimed)
-    small = [dict(A=bk["A"], b=bk["b"], d=bk["d"], seed=1) for bk in bank if bk["n"] <= 256][:64]
-    if small:
-        ctx.lsq_solve_batch(small, tol=1e-12, flags=P.FLAG_AUTOTUNE)
+    ctx.lsq_serve_config(arena_bytes=int(args.arena_gb * 1e9), cta_bytes=args.cta_mb * 2.0 ** 20,
+                         max_group=args.max_group)
+    # the autotuner picks the small-problem (n <= 256) pass shapes, once per
+    # n-range, on small synthetic problems (untimed)
+    from paper_2506_03070_gb300 import synth
+    small = []
+    for j, n in enumerate((24, 48, 100, 200)):
+        for rep in range(4):
+            p = synth.batched_problem(20000, n, 1e4, seed=900 + 10 * j + rep, device=dev)
+            small.append(dict(A=p["A"], b=p["b"], d=4 * n, seed=1))
+    ctx.lsq_solve_batch(small, tol=1e-12, flags=P.FLAG_AUTOTUNE)
+    del small
     rng = np.random.default_rng(args.serve_seed)
 
     def stream_run(nreq, rate, tag):
@@ -390,12 +397,20 @@ def run_serve(args):
             if 8 * bk["m"] * bk["n"] <= 2e9:  # the check itself needs a copy of A
                 worst = max(worst, oracle.backward_error_kw(bk["A"], bk["b"], out[i][1]))
         groups = [o[2]["group_blocks"] for o in out]
+        # block-time per phase (group size x device duration) as a share of
+        # all resident blocks over the run's span
+        grid = ctx.lsq_serve_stats()["grid_blocks"]
+        share = {}
+        for key in ("t_group_wait_ms", "t_sketch_ms", "t_precond_ms", "t_lsqr_ms"):
+            share[key.replace("t_", "").replace("_ms", "")] = sum(o[2]["group_blocks"] * o[2][key] for o in out) \
+                / 1e3 / (grid * span)
         return {"tag": tag, "requests": nreq, "rate_per_s": rate, "solves_per_s": nreq / span, "span_s": span,
                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                "mean": float(lat.mean()), "max": float(lat.max())},
                 "hbm_gbs_A_stream": abytes / span / 1e9, "statuses": statuses,
                 "backward_error_kw_max_sampled": worst,
                 "group_blocks": {"min": min(groups), "median": float(np.median(groups)), "max": max(groups)},
+                "block_time_share": share,
                 "lsqr_iters_mean": float(np.mean([o[2]["iters"] for o in out])), "body": body}
 
     # warm-up: a few requests through the server
@@ -609,6 +624,8 @@ def main():
     ap.add_argument("--arena-gb", type=float, default=150.0, help="serving: HBM budget for admitted requests")
     ap.add_argument("--seq-sample", type=int, default=100, help="serving: requests timed as sequential solves")
     ap.add_argument("--serve-seed", type=int, default=7)
+    ap.add_argument("--cta-mb", type=float, default=0.0, help="serving: MiB of A per block of a group (0: default)")
+    ap.add_argument("--max-group", type=int, default=0, help="serving: most blocks per request (0: default)")
     ap.add_argument("--batch", type=int, default=4096, help="problems in the batched config")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--native", action="store_true", help="LSQR matvecs on the native FP64 pipe")

@@ -108,10 +108,13 @@ typedef struct {
   float t_sketch_ms, t_precond_ms, t_lsqr_ms, t_check_ms, t_h2d_ms, t_d2h_ms;
   /* lsq_submit / lsq_poll only: host monotonic clock (CLOCK_MONOTONIC) in
    * seconds when the request was submitted, handed to the device, and seen
-   * complete; and the number of blocks that solved it together. */
+   * complete; the number of blocks that solved it together and how long its
+   * first block waited for the rest of the group (device clock).  For served
+   * requests t_sketch_ms, t_precond_ms and t_lsqr_ms (LSQR + accuracy pass)
+   * are device-clock durations of the phases. */
   double t_submit_s, t_start_s, t_done_s;
   int32_t group_blocks;
-  int32_t reserved;
+  float t_group_wait_ms;
 } lsq_info;
 
 /* Context on `device` with a workspace budget of hbm_budget_bytes (0 = 90% of
@@ -267,14 +270,21 @@ lsq_status lsq_solve_batch(lsq_ctx* ctx, const lsq_batch_item* items, int64_t co
  * fit the arena.  Several host threads may submit and poll concurrently. */
 typedef int64_t lsq_ticket;
 
-lsq_status lsq_submit(lsq_ctx* ctx, const lsq_problem* problem, const lsq_opts* opts, double* x, lsq_ticket* out);
+/* stream: the request starts only after the work enqueued on `stream` before
+ * this call has completed (so inputs still being produced, and buffers that
+ * pending work reads or writes, e.g. memory a caching allocator recycles, are
+ * safe); NULL is the legacy default stream, as everywhere in this header. */
+lsq_status lsq_submit(lsq_ctx* ctx, const lsq_problem* problem, const lsq_opts* opts, double* x, lsq_ticket* out,
+                      void* stream);
 lsq_status lsq_poll(lsq_ctx* ctx, lsq_ticket ticket, lsq_info* info);
 
 /* Serving configuration; takes effect only before the first lsq_submit.
  * arena_bytes: device memory for admitted requests (0 = the context's budget
  * minus the synchronous workspace it holds); cta_bytes: bytes of A per block
- * when sizing a request's group (0 = 4 MiB). */
-lsq_status lsq_serve_config(lsq_ctx* ctx, size_t arena_bytes, double cta_bytes);
+ * when sizing a request's group (0 = 64 MiB); max_group: most blocks one
+ * request may take (0 = an eighth of the resident blocks).  A request's group
+ * is max(A bytes / cta_bytes, QR flops / 2.5e8), clamped to [1, max_group]. */
+lsq_status lsq_serve_config(lsq_ctx* ctx, size_t arena_bytes, double cta_bytes, int32_t max_group);
 
 typedef struct {
   int64_t submitted, completed, pending, in_flight;

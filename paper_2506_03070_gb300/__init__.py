@@ -62,7 +62,7 @@ class Info(ctypes.Structure):
                 ("t_sketch_ms", ctypes.c_float), ("t_precond_ms", ctypes.c_float), ("t_lsqr_ms", ctypes.c_float),
                 ("t_check_ms", ctypes.c_float), ("t_h2d_ms", ctypes.c_float), ("t_d2h_ms", ctypes.c_float),
                 ("t_submit_s", ctypes.c_double), ("t_start_s", ctypes.c_double), ("t_done_s", ctypes.c_double),
-                ("group_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("group_blocks", ctypes.c_int32), ("t_group_wait_ms", ctypes.c_float)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -124,9 +124,9 @@ def load(path: str = LIB_PATH):
     L.lsq_check_noalloc.restype = i32
     L.lsq_solve_batch.argtypes = [P, ctypes.POINTER(BatchItem), i64, f64, i64, i32, ctypes.POINTER(BatchResult), P]
     L.lsq_solve_batch.restype = i32
-    L.lsq_submit.argtypes = [P, ctypes.POINTER(Problem), ctypes.POINTER(Opts), P, ctypes.POINTER(ctypes.c_int64)]
+    L.lsq_submit.argtypes = [P, ctypes.POINTER(Problem), ctypes.POINTER(Opts), P, ctypes.POINTER(ctypes.c_int64), P]
     L.lsq_poll.argtypes = [P, i64, ctypes.POINTER(Info)]
-    L.lsq_serve_config.argtypes = [P, ctypes.c_size_t, f64]
+    L.lsq_serve_config.argtypes = [P, ctypes.c_size_t, f64, i32]
     L.lsq_serve_stats_get.argtypes = [P, ctypes.POINTER(ServeStats)]
     for name in ("lsq_create", "lsq_destroy", "lsq_sketch_indices", "lsq_sketch", "lsq_precond", "lsq_lsqr",
                  "lsq_check", "lsq_solve", "lsq_submit", "lsq_poll", "lsq_serve_config", "lsq_serve_stats_get"):
@@ -298,14 +298,16 @@ class Context:
         return x, info.as_dict()
 
     # -- serving -------------------------------------------------------------
-    def lsq_serve_config(self, arena_bytes=0, cta_bytes=0.0):
-        self._check(self.lib.lsq_serve_config(self.h, arena_bytes, cta_bytes))
+    def lsq_serve_config(self, arena_bytes=0, cta_bytes=0.0, max_group=0):
+        self._check(self.lib.lsq_serve_config(self.h, arena_bytes, cta_bytes, max_group))
 
-    def lsq_submit(self, A, b, d, zeta=8, seed=0, tol=1e-12, maxit=0, flags=0, x=None):
+    def lsq_submit(self, A, b, d, zeta=8, seed=0, tol=1e-12, maxit=0, flags=0, x=None, stream=None):
         """Queue a problem for the persistent request loop; returns a ticket.
         A, b: CUDA float64 tensors or numpy float64 arrays (host problem).
         They (and x) are kept referenced here until lsq_poll reports the
-        request complete."""
+        request complete.  The request starts after the work already queued
+        on `stream` (default: torch's current stream), so tensors that pending
+        kernels still use are safe to hand over."""
         import torch
         if isinstance(A, np.ndarray):
             if A.dtype != np.float64 or A.ndim != 2 or A.strides[1] != 8:
@@ -326,7 +328,8 @@ class Context:
         pr = Problem(_ptr(A), _ptr(b), m, n, lda, mem, 0)
         op = Opts(d, zeta, PREC_FP64, seed, tol, maxit, flags, 0)
         t = ctypes.c_int64()
-        self._check(self.lib.lsq_submit(self.h, ctypes.byref(pr), ctypes.byref(op), _ptr(x), ctypes.byref(t)))
+        self._check(self.lib.lsq_submit(self.h, ctypes.byref(pr), ctypes.byref(op), _ptr(x), ctypes.byref(t),
+                                        _stream(stream)))
         self._live[t.value] = (A, b, x)
         return t.value
 

@@ -31,4 +31,5 @@ struct lsq_ctx {
   lsq::Server* server = nullptr;
   size_t serve_arena = 0;        // 0: the budget minus the synchronous workspace
   double serve_cta_bytes = 0.0;  // 0: default bytes of A per block of a request's group
+  int serve_max_group = 0;       // 0: default cap on a request's group
 };

@@ -79,7 +79,14 @@ enum {
   OUT_ETA_PRE,
   OUT_MARNORM,
   OUT_ANORM_EST,
-  kOutSlots = 16
+  // serving only: %globaltimer (ns) when the group's first block joined, when
+  // the group was complete, and after the sketch, the preconditioner and LSQR
+  OUT_T_JOIN = 12,
+  OUT_T_START,
+  OUT_T_SKETCH,
+  OUT_T_PRECOND,
+  OUT_T_END,
+  kOutSlots = 24
 };
 // Widest problem of the LSQR kernels (the panel kernel shares a row among
 // up to 8 warps of 512 columns each).

@@ -1,8 +1,12 @@
 // serve.cu -- lsq_submit / lsq_poll: a persistent request loop.
 //
 // Device side: k_serve is one cooperative launch with every block resident
-// (2 per SM).  Requests sit in a ring in mapped host memory (the host writes
-// an entry, then advances `tail` with release ordering).  A block claims the
+// (2 per SM).  Requests sit in a ring in device memory.  The host publishes
+// an entry with two copy-engine copies on one stream -- the entry, then the
+// new `tail` -- so an entry has always landed before `tail` covers it, with
+// no reliance on the host CPU's memory ordering towards the GPU; each entry
+// also carries its sequence number, which a block checks before trusting
+// it.  A block claims the
 // request at the queue head with a compare-and-swap on a device word
 // (head << 16 | joined): a request of group size G stays at the head until G
 // blocks have joined, each getting its index in the group.  Requests are
@@ -21,13 +25,16 @@
 // copies only (no kernel may need SMs while the server holds them),
 // publishes staged requests, watches completion flags, copies host results
 // back, and frees slots.  It launches the server when work is published and
-// none is running, and closes it (a flag the idle blocks read) once nothing
-// is queued or in flight.
+// none is running, and closes it (a flag the idle blocks read) 2 ms after the
+// last published request completed -- also while requests are still staged,
+// since their callers' earlier GPU work (which they are ordered after) cannot
+// run while the server holds every SM.
 //
 // Every device wait is bounded: group barriers and bulk-copy waits by
-// kBarrierTimeoutNs, an idle block by kServeIdleNs.  A block whose request hit
-// a timeout leaves the loop (its copy ring may be out of phase); the host
-// relaunches the server once the rest has drained.
+// kBarrierTimeoutNs, an idle block by kServeIdleNs, after which it retires the
+// whole launch (kRetired) so that no group can form on a half-exited server.
+// A block whose request hit a timeout leaves the loop (its copy ring may be
+// out of phase); the host relaunches the server once the rest has drained.
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -51,6 +58,11 @@ constexpr int kServeMaxN = 1024;
 constexpr int kServeRingDoubles = kWarps * kNbuf * 512;  // per-warp rings of 3 x 4 KB
 constexpr unsigned long long kServeIdleNs = 10ull * 1000ull * 1000ull * 1000ull;
 constexpr uint32_t kServeCap = 4096;  // queue entries
+// Bit of the queue word that retires the running launch: set (by a block
+// that waited kServeIdleNs with no work) only by compare-and-swap on the
+// same word that claims carry, so no group is joined once it is set; every
+// block leaves on seeing it, and the last block out clears it.
+constexpr unsigned long long kRetired = 1ull << 63;
 
 // Pass variants: 0..5 chunked shapes (n <= 256), 6: one warp per row with
 // 8 column pairs per lane (n <= 512), 7: two warps per row (n <= 1024).
@@ -69,6 +81,7 @@ struct ServeItem {  // written by the host into mapped memory; 8-byte words only
   char* slot;
   uint64_t oCtl, oY, oW, oR, oM, oMt, oRd, oU, oVec, oGpart, oPart, oImg;
   int64_t npad;
+  uint64_t seq;  // queue index + 1
 };
 constexpr int kItemWords = sizeof(ServeItem) / 8;
 static_assert(sizeof(ServeItem) % 8 == 0, "item is copied as 8-byte words");
@@ -82,34 +95,25 @@ struct ServeCtl {  // per request, in its slot; zeroed by the host before publis
 };
 
 struct ServeDone {  // per queue entry, mapped host memory
-  uint32_t done;
+  unsigned long long done;  // the entry's sequence number once its request is complete
   uint32_t status;
-  uint32_t pad[2];
+  uint32_t pad;
   double out[kOutSlots];
 };
 
-struct ServeHdr {  // mapped host memory
-  unsigned long long tail;
-  unsigned int closed;
-  unsigned int pad;
-};
-
 struct ServeArgs {
-  ServeHdr* hdr;
+  const unsigned long long* tail;  // device: entries published
+  const unsigned int* closed;      // device: 1 = idle blocks leave
   const ServeItem* ring;
   ServeDone* done;
-  unsigned long long* qstate;  // device: head << 16 | joined
+  unsigned long long* qstate;  // device: head << 16 | joined, plus kRetired
   uint32_t* srv_status;        // device: DS_TIMEOUT when a block left early
+  unsigned int* exits;         // device: blocks of this launch that have left
   uint32_t cap;
 };
 
-__device__ __forceinline__ unsigned long long ld_acquire_sys_u64(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_sys_u32(uint32_t* p, uint32_t v) {
-  asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void st_release_sys_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 // Thread 0: claim the next request (or learn that the server is to stop).
@@ -119,16 +123,25 @@ __device__ int claim(const ServeArgs& a, unsigned long long& idx, int& gidx, uns
   unsigned int ns = 128;
   for (;;) {
     const unsigned long long st = atomicAdd(a.qstate, 0ull);
+    if (st & kRetired) return 1;
     const unsigned long long head = st >> 16;
     const unsigned int joined = (unsigned int)(st & 0xFFFFull);
-    const unsigned long long tail = ld_acquire_sys_u64(&a.hdr->tail);
-    if (head >= tail) {
-      if (*(volatile unsigned int*)&a.hdr->closed) return 1;
+    const unsigned long long tail = *(volatile const unsigned long long*)a.tail;
+    const ServeItem* e = a.ring + (head % a.cap);
+    // an entry counts once its own sequence number has landed (always true
+    // after `tail` covers it; checked rather than assumed)
+    const bool ready = head < tail && *(volatile const unsigned long long*)&e->seq == head + 1;
+    if (!ready) {
+      if (head >= tail && *(volatile const unsigned int*)a.closed) return 1;
       const unsigned long long now = globaltimer_ns();
       if (idle0 == 0) {
         idle0 = now;
       } else if (now - idle0 > kServeIdleNs) {
-        return 1;  // the host stopped closing the server: leave
+        // the host stopped closing the server: retire the whole launch,
+        // unless a claim changed the queue word meanwhile
+        if (atomicCAS(a.qstate, st, st | kRetired) == st) return 1;
+        idle0 = 0;
+        continue;
       }
       __nanosleep(ns);
       if (ns < 4096) ns <<= 1;
@@ -136,7 +149,6 @@ __device__ int claim(const ServeArgs& a, unsigned long long& idx, int& gidx, uns
     }
     idle0 = 0;
     ns = 128;
-    const ServeItem* e = a.ring + (head % a.cap);
     const unsigned int G = (unsigned int)*(volatile const int32_t*)&e->G;
     const unsigned long long next = (joined + 1 >= G) ? ((head + 1) << 16) : (st + 1);
     if (atomicCAS(a.qstate, st, next) == st) {
@@ -173,12 +185,16 @@ __device__ void serve_solve(const ServeItem& it, int gidx, double* s_ring, uint6
   double* vec = reinterpret_cast<double*>(slot + it.oVec);
   const int npad = (int)it.npad;
 
+  const bool stamp = gidx == 0 && threadIdx.x == 0;
+  if (stamp) ctl->out[OUT_T_JOIN] = (double)globaltimer_ns();
   // ---- Y = S [A | b]
   zero_group(Y, (int64_t)d * ldy, g);
   if (!gsync(g)) return;
+  if (stamp) ctl->out[OUT_T_START] = (double)globaltimer_ns();
   sketch_group(it.A, it.b, it.m, n, it.lda, d, it.zeta, it.seed, Y, ldy, reinterpret_cast<int32_t*>(s_ring), s_sgn, g);
   __threadfence();
   if (!gsync(g)) return;
+  if (stamp) ctl->out[OUT_T_SKETCH] = (double)globaltimer_ns();
   // ---- QR of Y, R, M = R^{-1}, x0 = M z
   {
     const int64_t tid = (int64_t)gidx * kThreads + threadIdx.x, ts = (int64_t)it.G * kThreads;
@@ -189,6 +205,7 @@ __device__ void serve_solve(const ServeItem& it, int gidx, double* s_ring, uint6
   }
   if (!householder_group(W, d, n, ncol, rdiag, scratch, g)) return;
   if (!precond_group(W, d, n, rdiag, R, M, Mt, it.x, scratch, g)) return;
+  if (stamp) ctl->out[OUT_T_PRECOND] = (double)globaltimer_ns();
   // one reader, so the whole block takes the same branch
   const int failed = threadIdx.x == 0 ? ((*(volatile uint32_t*)&ctl->status &
                                           (DS_RANK | DS_SKETCH | DS_NONFINITE | DS_TIMEOUT)) != 0)
@@ -238,6 +255,7 @@ __device__ void serve_solve(const ServeItem& it, int gidx, double* s_ring, uint6
     case kVarWarpRow: lsqr_wide<1>(p, s_ring, s_bars, s_scal, seq, s_w); break;
     default: lsqr_wide<2>(p, s_ring, s_bars, s_scal, seq, s_w); break;
   }
+  if (stamp) ctl->out[OUT_T_END] = (double)globaltimer_ns();
 }
 
 __global__ void __launch_bounds__(kThreads, 2) k_serve(ServeArgs a) {
@@ -282,7 +300,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_serve(ServeArgs a) {
         for (int k = 0; k < kOutSlots; ++k) dn->out[k] = __ldcg(&ctl->out[k]);
         dn->status = *(volatile uint32_t*)&ctl->status;
         __threadfence_system();
-        st_release_sys_u32(&dn->done, 1u);
+        st_release_sys_u64(&dn->done, s_idx + 1ull);
       }
       if (leave) atomicOr(a.srv_status, DS_TIMEOUT);
       s_leave = leave ? 1 : 0;
@@ -291,6 +309,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_serve(ServeArgs a) {
     // s_cmd is rewritten only after the next request's first barrier, s_leave
     // only after its second: every thread has read both by then
     if (s_leave != 0) break;
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(a.exits, 1u) == gridDim.x - 1u) {  // last block out: reset for the next launch
+      atomicExch(a.exits, 0u);
+      atomicAnd(a.qstate, ~kRetired);
+      __threadfence();
+    }
   }
 }
 
@@ -335,6 +361,7 @@ struct ServeRequest {
   size_t oA = 0, oB = 0, oX = 0;  // host problems: device copies in the slot
   uint64_t qidx = 0;
   cudaEvent_t ev = nullptr;
+  cudaEvent_t ready = nullptr;  // recorded on the caller's stream at submission, or null
   enum { kPending, kStaging, kPublished, kDraining, kDone } state = kPending;
   lsq_status status = LSQ_PENDING;
   double out[kOutSlots] = {0};
@@ -348,22 +375,32 @@ struct Server {
   char* arena = nullptr;
   size_t arena_bytes = 0, arena_used = 0, arena_peak = 0;
   std::map<size_t, size_t> free_blocks;  // offset -> size
+  // device memory: queue words and the ring of entries
+  char* d_q = nullptr;
+  unsigned long long* d_tail = nullptr;
+  unsigned int* d_closed = nullptr;
+  unsigned int* d_exits = nullptr;
   unsigned long long* d_qstate = nullptr;
   uint32_t* d_srv_status = nullptr;
-  // mapped host memory: header, ring, completion records; pinned zeros
-  char* hmem = nullptr;
-  ServeHdr* hdr = nullptr;
-  ServeItem* ring = nullptr;
-  ServeDone* done = nullptr;
-  ServeHdr* d_hdr = nullptr;
   ServeItem* d_ring = nullptr;
-  ServeDone* d_done = nullptr;
+  // pinned host memory: staged entries and tail values (sources of the
+  // publishing copies), constant words, a zero page
+  char* h_pin = nullptr;
+  ServeItem* h_items = nullptr;
+  unsigned long long* h_tails = nullptr;
+  unsigned int* h_words = nullptr;  // {0, 1}
   void* h_zero = nullptr;
+  // mapped host memory: completion records written by the device
+  char* hmem = nullptr;
+  ServeDone* done = nullptr;
+  ServeDone* d_done = nullptr;
+  cudaEvent_t ev_pub = nullptr;
   cudaStream_t s_srv = nullptr, s_copy = nullptr;
   cudaEvent_t ev_srv = nullptr;
   std::vector<cudaEvent_t> ev_pool;
   int grid = 0;
-  double cta_bytes = 4.0 * 1024 * 1024;
+  int max_group = 0;
+  double cta_bytes = 64.0 * 1024 * 1024;
   bool running = false, closing = false;
   double idle_since = 0;
   uint64_t tail = 0;
@@ -441,7 +478,7 @@ struct Server {
     for (auto it = published.begin(); it != published.end();) {
       ServeRequest* r = it->second;
       ServeDone* dn = done + (r->qidx % kServeCap);
-      if (*(volatile uint32_t*)&dn->done) {
+      if (*(volatile unsigned long long*)&dn->done == r->qidx + 1) {
         std::atomic_thread_fence(std::memory_order_acquire);
         const uint32_t bits = *(volatile uint32_t*)&dn->status;
         for (int k = 0; k < kOutSlots; ++k) r->out[k] = ((volatile double*)dn->out)[k];
@@ -487,6 +524,7 @@ struct Server {
       pending.pop_front();
       r->off = off;
       char* slot = arena + off;
+      if (r->ready) cudaStreamWaitEvent(s_copy, r->ready, 0);  // the caller's earlier work first
       r->item.slot = slot;
       if (r->pr.mem == LSQ_MEM_HOST) {
         double* Ad = reinterpret_cast<double*>(slot + r->oA);
@@ -515,14 +553,16 @@ struct Server {
         staging.pop_front();
         put_event(r->ev);
         r->ev = nullptr;
+        put_event(r->ready);
+        r->ready = nullptr;
         r->qidx = tail;
-        ServeDone* dn = done + (tail % kServeCap);
-        *(volatile uint32_t*)&dn->done = 0u;
-        ring[tail % kServeCap] = r->item;
-        std::atomic_thread_fence(std::memory_order_release);
+        const uint32_t q = (uint32_t)(tail % kServeCap);
+        h_items[q] = r->item;
+        h_items[q].seq = tail + 1;
+        h_tails[q] = tail + 1;
+        cudaMemcpyAsync(d_ring + q, h_items + q, sizeof(ServeItem), cudaMemcpyHostToDevice, s_copy);
+        cudaMemcpyAsync(d_tail, h_tails + q, sizeof(unsigned long long), cudaMemcpyHostToDevice, s_copy);
         ++tail;
-        *(volatile unsigned long long*)&hdr->tail = tail;
-        std::atomic_thread_fence(std::memory_order_seq_cst);
         r->state = ServeRequest::kPublished;
         r->t_start = now_s();
         published[r->qidx] = r;
@@ -533,14 +573,18 @@ struct Server {
     // (5) launch or close the server
     const bool work = !published.empty();
     if (work && !running) {
-      *(volatile unsigned int*)&hdr->closed = 0u;
-      std::atomic_thread_fence(std::memory_order_seq_cst);
+      // the open flag and every entry published so far land before the launch
+      cudaMemcpyAsync(d_closed, h_words + 0, sizeof(unsigned int), cudaMemcpyHostToDevice, s_copy);
+      cudaEventRecord(ev_pub, s_copy);
+      cudaStreamWaitEvent(s_srv, ev_pub, 0);
       ServeArgs a;
-      a.hdr = d_hdr;
+      a.tail = d_tail;
+      a.closed = d_closed;
       a.ring = d_ring;
       a.done = d_done;
       a.qstate = d_qstate;
       a.srv_status = d_srv_status;
+      a.exits = d_exits;
       a.cap = kServeCap;
       void* args[] = {&a};
       cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_serve, grid, kThreads, args, serve_smem(), s_srv);
@@ -561,12 +605,14 @@ struct Server {
       }
       moved = true;
     }
-    const bool idle = published.empty() && staging.empty() && pending.empty();
+    // close as soon as nothing is published: staged requests may be waiting
+    // for other work on the GPU (their callers' streams), which cannot run
+    // while the server holds every SM
+    const bool idle = published.empty();
     if (running && !closing && idle) {
       if (idle_since == 0) idle_since = now_s();
       if (now_s() - idle_since > 0.002) {  // linger 2 ms, then let the blocks leave
-        *(volatile unsigned int*)&hdr->closed = 1u;
-        std::atomic_thread_fence(std::memory_order_seq_cst);
+        cudaMemcpyAsync(d_closed, h_words + 1, sizeof(unsigned int), cudaMemcpyHostToDevice, s_copy);
         closing = true;
         moved = true;
       }
@@ -592,8 +638,7 @@ struct Server {
       }
     }
     // shut down: close the server and let it drain (published work completes)
-    *(volatile unsigned int*)&hdr->closed = 1u;
-    std::atomic_thread_fence(std::memory_order_seq_cst);
+    cudaMemcpyAsync(d_closed, h_words + 1, sizeof(unsigned int), cudaMemcpyHostToDevice, s_copy);
   }
 };
 
@@ -606,20 +651,22 @@ void server_destroy(Server* s) {
   s->cv.notify_all();
   if (s->th.joinable()) s->th.join();
   cudaSetDevice(s->device);
-  if (s->s_srv) cudaStreamSynchronize(s->s_srv);  // bounded: idle blocks leave once closed
   if (s->s_copy) cudaStreamSynchronize(s->s_copy);
+  if (s->s_srv) cudaStreamSynchronize(s->s_srv);  // bounded: idle blocks leave once closed
   for (auto& kv : s->tickets) {
     if (kv.second->ev) cudaEventDestroy(kv.second->ev);
+    if (kv.second->ready) cudaEventDestroy(kv.second->ready);
     delete kv.second;
   }
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
   if (s->ev_srv) cudaEventDestroy(s->ev_srv);
+  if (s->ev_pub) cudaEventDestroy(s->ev_pub);
   if (s->s_srv) cudaStreamDestroy(s->s_srv);
   if (s->s_copy) cudaStreamDestroy(s->s_copy);
   if (s->arena) cudaFree(s->arena);
-  if (s->d_qstate) cudaFree(s->d_qstate);
+  if (s->d_q) cudaFree(s->d_q);
   if (s->hmem) cudaFreeHost(s->hmem);
-  if (s->h_zero) cudaFreeHost(s->h_zero);
+  if (s->h_pin) cudaFreeHost(s->h_pin);
   delete s;
 }
 
@@ -630,6 +677,7 @@ lsq_status server_create(lsq_ctx* ctx, Server** out) {
   s->ctx = ctx;
   s->device = ctx->device;
   if (ctx->serve_cta_bytes > 0) s->cta_bytes = ctx->serve_cta_bytes;
+  s->max_group = ctx->serve_max_group;
   size_t want = ctx->serve_arena ? ctx->serve_arena : (ctx->budget > ctx->ws_size ? ctx->budget - ctx->ws_size : 0);
   want = want / 256 * 256;
   auto bail = [&](lsq_status st, const std::string& m) {
@@ -646,35 +694,45 @@ lsq_status server_create(lsq_ctx* ctx, Server** out) {
     return bail(LSQ_ERR_CUDA, "server kernel does not fit an SM");
   if (per_sm > 2) per_sm = 2;
   s->grid = per_sm * ctx->sms;
+  if (s->max_group <= 0 || s->max_group > s->grid) s->max_group = s->max_group > 0 ? s->grid : s->grid / 8;
+  if (s->max_group < 1) s->max_group = 1;
   if (cudaMalloc(&s->arena, want) != cudaSuccess) {
     cudaGetLastError();
     return bail(LSQ_ERR_OOM, "serving arena allocation failed");
   }
   s->arena_bytes = want;
   s->free_blocks[0] = want;
-  char* small = nullptr;
-  if (cudaMalloc(&small, 256) != cudaSuccess) return bail(LSQ_ERR_OOM, "server words");
-  cudaMemset(small, 0, 256);
-  s->d_qstate = reinterpret_cast<unsigned long long*>(small);
-  s->d_srv_status = reinterpret_cast<uint32_t*>(small + 64);
-  const size_t hbytes = 256 + sizeof(ServeItem) * kServeCap + sizeof(ServeDone) * kServeCap;
+  const size_t qbytes = 256 + sizeof(ServeItem) * kServeCap;
+  if (cudaMalloc(&s->d_q, qbytes) != cudaSuccess) return bail(LSQ_ERR_OOM, "server queue");
+  cudaMemset(s->d_q, 0, qbytes);
+  s->d_tail = reinterpret_cast<unsigned long long*>(s->d_q);
+  s->d_closed = reinterpret_cast<unsigned int*>(s->d_q + 8);
+  s->d_qstate = reinterpret_cast<unsigned long long*>(s->d_q + 64);
+  s->d_srv_status = reinterpret_cast<uint32_t*>(s->d_q + 128);
+  s->d_exits = reinterpret_cast<unsigned int*>(s->d_q + 192);
+  s->d_ring = reinterpret_cast<ServeItem*>(s->d_q + 256);
+  const size_t pbytes = sizeof(ServeItem) * kServeCap + sizeof(unsigned long long) * kServeCap + 256 + 4096;
+  if (cudaHostAlloc(&s->h_pin, pbytes, cudaHostAllocDefault) != cudaSuccess) return bail(LSQ_ERR_OOM, "pinned queue");
+  std::memset(s->h_pin, 0, pbytes);
+  s->h_items = reinterpret_cast<ServeItem*>(s->h_pin);
+  s->h_tails = reinterpret_cast<unsigned long long*>(s->h_pin + sizeof(ServeItem) * kServeCap);
+  s->h_words = reinterpret_cast<unsigned int*>(s->h_pin + sizeof(ServeItem) * kServeCap +
+                                               sizeof(unsigned long long) * kServeCap);
+  s->h_words[0] = 0u;
+  s->h_words[1] = 1u;
+  s->h_zero = s->h_pin + sizeof(ServeItem) * kServeCap + sizeof(unsigned long long) * kServeCap + 256;
+  const size_t hbytes = sizeof(ServeDone) * kServeCap;
   if (cudaHostAlloc(&s->hmem, hbytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess)
-    return bail(LSQ_ERR_OOM, "mapped queue memory");
+    return bail(LSQ_ERR_OOM, "mapped completion records");
   std::memset(s->hmem, 0, hbytes);
-  s->hdr = reinterpret_cast<ServeHdr*>(s->hmem);
-  s->ring = reinterpret_cast<ServeItem*>(s->hmem + 256);
-  s->done = reinterpret_cast<ServeDone*>(s->hmem + 256 + sizeof(ServeItem) * kServeCap);
+  s->done = reinterpret_cast<ServeDone*>(s->hmem);
   void* dp = nullptr;
-  if (cudaHostGetDevicePointer(&dp, s->hmem, 0) != cudaSuccess) return bail(LSQ_ERR_CUDA, "mapped queue pointer");
-  char* dbase = static_cast<char*>(dp);
-  s->d_hdr = reinterpret_cast<ServeHdr*>(dbase);
-  s->d_ring = reinterpret_cast<ServeItem*>(dbase + 256);
-  s->d_done = reinterpret_cast<ServeDone*>(dbase + 256 + sizeof(ServeItem) * kServeCap);
-  if (cudaHostAlloc(&s->h_zero, 4096, cudaHostAllocDefault) != cudaSuccess) return bail(LSQ_ERR_OOM, "zero page");
-  std::memset(s->h_zero, 0, 4096);
+  if (cudaHostGetDevicePointer(&dp, s->hmem, 0) != cudaSuccess) return bail(LSQ_ERR_CUDA, "mapped record pointer");
+  s->d_done = reinterpret_cast<ServeDone*>(dp);
   if (cudaStreamCreateWithFlags(&s->s_srv, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->s_copy, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&s->ev_srv, cudaEventDisableTiming) != cudaSuccess)
+      cudaEventCreateWithFlags(&s->ev_srv, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_pub, cudaEventDisableTiming) != cudaSuccess)
     return bail(LSQ_ERR_CUDA, "server streams");
   if (cudaDeviceSynchronize() != cudaSuccess) return bail(LSQ_ERR_CUDA, "server setup");
   s->th = std::thread([s] { s->loop(); });
@@ -683,7 +741,7 @@ lsq_status server_create(lsq_ctx* ctx, Server** out) {
 }
 
 // Slot layout and group size of a request; false if it cannot be served.
-void plan_request(ServeRequest* r, int grid, double cta_bytes, const BatchTuning* tune) {
+void plan_request(ServeRequest* r, int max_group, double cta_bytes, const BatchTuning* tune) {
   const int64_t m = r->pr.m, n = r->pr.n, d = r->o.d;
   const int64_t npad = (n + 31) / 32 * 32, ldi = (n + 1) / 2 * 2, ncol = n + 1;
   const double abytes = 8.0 * (double)m * (double)n;
@@ -694,7 +752,7 @@ void plan_request(ServeRequest* r, int grid, double cta_bytes, const BatchTuning
   const int64_t rows_cap = (m + 31) / 32;  // at least one 32-row sketch block per block
   if (G > rows_cap) G = rows_cap;
   if (G < 1) G = 1;
-  if (G > grid) G = grid;
+  if (G > max_group) G = max_group;
   ServeItem& it = r->item;
   it.A = r->pr.A;
   it.b = r->pr.b;
@@ -744,22 +802,24 @@ using namespace lsq;
 
 extern "C" {
 
-lsq_status lsq_serve_config(lsq_ctx* ctx, size_t arena_bytes, double cta_bytes) {
+lsq_status lsq_serve_config(lsq_ctx* ctx, size_t arena_bytes, double cta_bytes, int32_t max_group) {
   if (!ctx) return LSQ_ERR_ARG;
   if (ctx->server) {
     ctx->err = "serving is already running on this context";
     return LSQ_ERR_ARG;
   }
-  if (cta_bytes < 0) {
-    ctx->err = "cta_bytes must be >= 0";
+  if (cta_bytes < 0 || max_group < 0) {
+    ctx->err = "cta_bytes and max_group must be >= 0";
     return LSQ_ERR_ARG;
   }
   ctx->serve_arena = arena_bytes;
   ctx->serve_cta_bytes = cta_bytes;
+  ctx->serve_max_group = max_group;
   return LSQ_OK;
 }
 
-lsq_status lsq_submit(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts* o, double* x, lsq_ticket* out) {
+lsq_status lsq_submit(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts* o, double* x, lsq_ticket* out,
+                      void* stream) {
   if (!ctx) return LSQ_ERR_ARG;
   if (!pr || !o || !x || !out) {
     ctx->err = "null problem, options, x or ticket";
@@ -803,7 +863,7 @@ lsq_status lsq_submit(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts* o, do
   r->pr = *pr;
   r->o = *o;
   r->x_user = x;
-  plan_request(r, srv->grid, srv->cta_bytes, ctx->tuning);
+  plan_request(r, srv->max_group, srv->cta_bytes, ctx->tuning);
   if (r->bytes > srv->arena_bytes) {
     ctx->err = "request needs " + std::to_string(r->bytes) + " bytes; the serving arena holds " +
                std::to_string(srv->arena_bytes);
@@ -812,6 +872,16 @@ lsq_status lsq_submit(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts* o, do
   }
   {
     std::lock_guard<std::mutex> lk(srv->mu);
+    {
+      r->ready = srv->get_event();
+      if (!r->ready || cudaEventRecord(r->ready, (cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        if (r->ready) srv->put_event(r->ready);
+        delete r;
+        ctx->err = "could not record the ordering event on the caller's stream";
+        return LSQ_ERR_CUDA;
+      }
+    }
     r->ticket = srv->next_ticket++;
     r->t_submit = now_s();
     srv->tickets[r->ticket] = r;
@@ -859,6 +929,11 @@ lsq_status lsq_poll(lsq_ctx* ctx, lsq_ticket ticket, lsq_info* info) {
     info->t_start_s = r->t_start;
     info->t_done_s = r->t_done;
     info->group_blocks = r->item.G;
+    const double* t = r->out;
+    if (t[OUT_T_START] > 0) info->t_group_wait_ms = (float)((t[OUT_T_START] - t[OUT_T_JOIN]) * 1e-6);
+    if (t[OUT_T_SKETCH] > 0) info->t_sketch_ms = (float)((t[OUT_T_SKETCH] - t[OUT_T_START]) * 1e-6);
+    if (t[OUT_T_PRECOND] > 0) info->t_precond_ms = (float)((t[OUT_T_PRECOND] - t[OUT_T_SKETCH]) * 1e-6);
+    if (t[OUT_T_END] > 0) info->t_lsqr_ms = (float)((t[OUT_T_END] - t[OUT_T_PRECOND]) * 1e-6);
   }
   const lsq_status s = r->status;
   delete r;
