@@ -24,6 +24,8 @@ solution and ||b - A x_true|| = resid_norm (up to rounding of the construction).
 ``batched_problem`` is the cheap construction used for many small problems:
   A = (G / sqrt(m)) diag(s) H1 H2 with H1, H2 random Householder reflectors,
   b = A x_true + 1e-6 g/||g||.
+``large_problem`` builds the same construction in place, in row chunks, for
+matrices too large to hold twice (the 5e6 x 2000, 80 GB case).
 """
 from __future__ import annotations
 
@@ -110,3 +112,27 @@ def batched_problem(m, n, cond, *, seed, device="cpu", dtype=torch.float64):
     g = torch.randn(m, generator=gen, device=dev, dtype=dtype)
     b = A @ x_true + 1e-6 * g / torch.linalg.vector_norm(g)
     return {"A": A.contiguous(), "b": b, "x_true": x_true, "cond": cond}
+
+
+def large_problem(m, n, cond, *, seed, device="cuda", chunk_rows=1 << 18, dtype=torch.float64):
+    """Cheap construction of ``batched_problem`` built in place: A (m x n) is the
+    only full-size allocation; G, diag(s) and the two reflectors are applied
+    chunk by chunk of rows.  cond(A) is within (1+sqrt(n/m))/(1-sqrt(n/m)) of
+    ``cond``."""
+    dev = torch.device(device)
+    gen = _gen(dev, seed)
+    A = torch.empty((m, n), device=dev, dtype=dtype)
+    s = torch.logspace(0.0, -math.log10(cond), n, device=dev, dtype=dtype) / math.sqrt(m)
+    vs = [_householder(n, _gen(dev, seed + 1 + k), dev, dtype) for k in range(2)]
+    for r0 in range(0, m, chunk_rows):
+        blk = A[r0:r0 + chunk_rows]
+        blk.normal_(generator=gen)
+        blk.mul_(s)
+        for v in vs:
+            blk.addr_(blk @ v, v, alpha=-2.0)
+    x_true = torch.randn(n, generator=_gen(dev, seed + 3), device=dev, dtype=dtype)
+    g = torch.randn(m, generator=_gen(dev, seed + 4), device=dev, dtype=dtype)
+    b = A @ x_true
+    b.add_(g, alpha=1e-6 / float(torch.linalg.vector_norm(g)))
+    del g
+    return {"A": A, "b": b, "x_true": x_true, "cond": cond}
