@@ -156,6 +156,17 @@ lsq_status lsq_sketch(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64
 lsq_status lsq_precond(lsq_ctx* ctx, const void* Y, int64_t d, int64_t n, int64_t ldy, int32_t has_b, int32_t prec,
                        double* R, double* M, double* x0, void* stream);
 
+/* Which Householder QR lsq_precond and lsq_solve use.  AUTO (the default):
+ * the blocked factorisation (compact WY: panels factored by a cooperative
+ * kernel, trailing updates as tensor-core GEMMs -- DGEMM for FP64, FP32
+ * emulated with three BF16 terms for the mixed form) once the d x (n+1)
+ * working copy reaches 32 MiB and n >= 128, the unblocked one (one grid
+ * barrier per column) below.  Both compute the same reflectors. */
+#define LSQ_QR_AUTO 0
+#define LSQ_QR_UNBLOCKED 1
+#define LSQ_QR_BLOCKED 2
+lsq_status lsq_set_qr_mode(lsq_ctx* ctx, int32_t mode);
+
 /* Preconditioned LSQR (Algorithm 2) from x0 with preconditioner M (device,
  * n x n row-major upper triangular), in the one-synchronisation order of
  * App. D.5.1.  A, b, x0, x device.  x receives the final iterate.  Stops when

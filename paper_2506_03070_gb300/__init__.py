@@ -33,7 +33,8 @@ FLAG_TIMING, FLAG_NO_CHECK, FLAG_NATIVE_FP64, FLAG_NO_IMAGE, FLAG_NO_FALLBACK = 
 EXPORTS = ("lsq_create", "lsq_destroy", "lsq_last_error", "lsq_status_string", "lsq_workspace_bytes",
            "lsq_sketch_indices", "lsq_sketch", "lsq_precond", "lsq_lsqr", "lsq_check", "lsq_solve",
            "lsq_check_noalloc", "lsq_solve_batch", "lsq_submit", "lsq_poll", "lsq_serve_config",
-           "lsq_serve_stats_get")
+           "lsq_serve_stats_get", "lsq_set_qr_mode")
+QR_AUTO, QR_UNBLOCKED, QR_BLOCKED = 0, 1, 2
 
 
 class LsqError(RuntimeError):
@@ -127,6 +128,8 @@ def load(path: str = LIB_PATH):
     L.lsq_submit.argtypes = [P, ctypes.POINTER(Problem), ctypes.POINTER(Opts), P, ctypes.POINTER(ctypes.c_int64), P]
     L.lsq_poll.argtypes = [P, i64, ctypes.POINTER(Info)]
     L.lsq_serve_config.argtypes = [P, ctypes.c_size_t, f64, i32]
+    L.lsq_set_qr_mode.argtypes = [P, i32]
+    L.lsq_set_qr_mode.restype = i32
     L.lsq_serve_stats_get.argtypes = [P, ctypes.POINTER(ServeStats)]
     for name in ("lsq_create", "lsq_destroy", "lsq_sketch_indices", "lsq_sketch", "lsq_precond", "lsq_lsqr",
                  "lsq_check", "lsq_solve", "lsq_submit", "lsq_poll", "lsq_serve_config", "lsq_serve_stats_get"):
@@ -191,6 +194,9 @@ class Context:
         if st not in allow:
             raise LsqError(st, self.lib.lsq_last_error(self.h).decode())
         return st
+
+    def lsq_set_qr_mode(self, mode):
+        self._check(self.lib.lsq_set_qr_mode(self.h, mode))
 
     @property
     def workspace_bytes(self):

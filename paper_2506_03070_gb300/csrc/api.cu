@@ -8,6 +8,8 @@
 #include <cstring>
 #include <string>
 
+#include <cublas_v2.h>
+
 #include "ctx.h"
 
 using namespace lsq;
@@ -105,6 +107,19 @@ lsq_status read_small(lsq_ctx* ctx, cudaStream_t st, uint32_t* bits, int32_t* ro
   if (rounds) std::memcpy(rounds, h + off_rounds, sizeof(int32_t));
   if (out) std::memcpy(out, h + off_out, sizeof(double) * kOutSlots);
   return LSQ_OK;
+}
+
+// cuBLAS handle of the context (null if it cannot be created: the QR then
+// runs unblocked).
+void* blas_handle(lsq_ctx* ctx) {
+  if (!ctx->blas && !ctx->blas_failed) {
+    cublasHandle_t h = nullptr;
+    if (cublasCreate(&h) == CUBLAS_STATUS_SUCCESS)
+      ctx->blas = h;
+    else
+      ctx->blas_failed = true;
+  }
+  return ctx->blas;
 }
 
 bool vec_ok(const double* A, int64_t lda) { return ((uintptr_t)A % 16 == 0) && (lda % 2 == 0); }
@@ -241,6 +256,7 @@ lsq_status lsq_destroy(lsq_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->server) server_destroy(ctx->server);
   ctx->server = nullptr;
+  if (ctx->blas) cublasDestroy(static_cast<cublasHandle_t>(ctx->blas));
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->h_small) cudaFreeHost(ctx->h_small);
@@ -270,6 +286,14 @@ const char* lsq_status_string(lsq_status s) {
 }
 
 size_t lsq_workspace_bytes(const lsq_ctx* ctx) { return ctx ? ctx->ws_size + kSmallBytes : 0; }
+
+lsq_status lsq_set_qr_mode(lsq_ctx* ctx, int32_t mode) {
+  if (!ctx) return LSQ_ERR_ARG;
+  if (mode != LSQ_QR_AUTO && mode != LSQ_QR_UNBLOCKED && mode != LSQ_QR_BLOCKED)
+    return fail(ctx, LSQ_ERR_ARG, "unknown QR mode");
+  ctx->qr_mode = mode;
+  return LSQ_OK;
+}
 
 lsq_status lsq_sketch_indices(lsq_ctx* ctx, uint64_t seed, int64_t row0, int64_t rows, int64_t d, int32_t zeta,
                               int32_t* idx, int8_t* sign, int32_t* rounds, void* stream) {
@@ -326,6 +350,7 @@ lsq_status lsq_precond(lsq_ctx* ctx, const void* Y, int64_t d, int64_t n, int64_
   probe.take<double>(n);
   probe.take<double>((size_t)n * n);
   probe.take<double>((size_t)n * n);
+  probe.take<char>(precond_blocked_bytes(d, n));
   if ((s = ensure_ws(ctx, probe.off)) != LSQ_OK) return s;
   Carver cv{ctx->ws};
   PrecondBuffers buf;
@@ -333,6 +358,9 @@ lsq_status lsq_precond(lsq_ctx* ctx, const void* Y, int64_t d, int64_t n, int64_
   buf.rdiag = cv.take<double>(n);
   buf.R = cv.take<double>((size_t)n * n);
   buf.Mt = cv.take<double>((size_t)n * n);
+  buf.blk = cv.take<char>(precond_blocked_bytes(d, n));
+  buf.blas = blas_handle(ctx);
+  buf.mode = ctx->qr_mode;
   buf.bar = ctx->d_bar;
   buf.status = ctx->d_status;
   if ((s = reset_small(ctx, st)) != LSQ_OK) return s;
@@ -468,6 +496,7 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
     *Y = cv.take<char>((size_t)d * ldy * yes);
     pb->W = cv.take<double>((size_t)ncol * d);
     pb->rdiag = cv.take<double>(npad);
+    pb->blk = cv.take<char>(precond_blocked_bytes(d, n));
     pb->R = nullptr;
     pb->Mt = nullptr;
     *R = cv.take<double>((size_t)n * n);
@@ -510,6 +539,8 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
   carve(cv, &A, &b, &xd, &Y, &pb, &R, &M, &lw);
   pb.bar = ctx->d_bar;
   pb.status = ctx->d_status;
+  pb.blas = blas_handle(ctx);
+  pb.mode = ctx->qr_mode;
 
   cudaEvent_t ev[6] = {};
   if (timing)

@@ -27,6 +27,10 @@ struct lsq_ctx {
   void* h_small = nullptr;
   // batched solves: tuned LSQR pass shapes per n-range
   lsq::BatchTuning* tuning = nullptr;
+  // cublasHandle_t of the blocked QR's trailing updates (created on first use)
+  void* blas = nullptr;
+  bool blas_failed = false;
+  int qr_mode = 0;  // LSQ_QR_AUTO / LSQ_QR_UNBLOCKED / LSQ_QR_BLOCKED
   // serving: persistent request loop, created by the first lsq_submit
   lsq::Server* server = nullptr;
   size_t serve_arena = 0;        // 0: the budget minus the synchronous workspace

@@ -25,7 +25,12 @@ struct PrecondBuffers {
   double* Mt;      // n * n, row-major transpose of M (working buffer)
   GridBarrier* bar;
   uint32_t* status;
+  void* blk;       // precond_blocked_bytes(d, n) of scratch for the blocked QR, or null (unblocked)
+  void* blas;      // cublasHandle_t for the blocked QR's trailing updates
+  int mode;        // 0: choose by size, 1: unblocked, 2: blocked (LSQ_QR_*)
 };
+// Scratch the blocked Householder QR needs for a d x (n+1) sketch.
+size_t precond_blocked_bytes(int64_t d, int64_t n);
 // dst = src^T for a row-major n x n matrix.
 cudaError_t transpose_square(const double* src, int n, double* dst, cudaStream_t st);
 template <typename TY>

@@ -2,12 +2,25 @@
 // "Factor Q, R = QR(Y)"), explicit M = R^{-1} (Sec. 3.2) and the
 // sketch-and-solve start x0 = M z, z = (Q^T S b)[:n] (Algorithm 1).
 //
-// The QR runs as one cooperative kernel over a column-major FP64 copy of Y.
-// Step k: every block recomputes ||Y[k+1:,k]|| (same order, same result in
-// all blocks), builds the reflector scalars, and the grid's warps update the
-// trailing columns j > k, one warp per column.  Column k itself is never
-// written, so one grid barrier per column suffices; R's diagonal goes to a
-// separate array and R[k][j] is left in W[j][k].
+// Two factorisations of the column-major copy W of Y, same reflectors and
+// same storage (R's diagonal in a separate array, R[k][j] left in W[j][k]):
+//
+// Unblocked (small sketches, see kBlockedMinBytes): one cooperative kernel.  Step k: every block
+// recomputes ||Y[k+1:,k]|| (same order, same result in all blocks), builds the
+// reflector scalars, and the grid's warps update the trailing columns j > k,
+// one warp per column.  Column k itself is never written, so one grid barrier
+// per column suffices.
+//
+// Blocked (compact WY, as LAPACK's geqrf/larft/larfb): panels of nb columns.
+// A panel kernel factors the panel with the reflectors of the unblocked
+// kernel, touching only the panel's columns (two barriers per column over its
+// G blocks, ~256 panel rows each); T of
+// Q = H_0 ... H_{b-1} = I - U T U^T comes from the Gram U^T U; the trailing
+// columns (and the sketched b column) then take Q^T in three GEMMs,
+// C <- C - U (T^T (U^T C)), on the tensor cores through cuBLAS (DGEMM in the
+// plain form, FP32 emulated with three BF16 terms in the mixed form).
+#include <cublas_v2.h>
+
 #include <algorithm>
 
 #include "kernels.h"
@@ -97,6 +110,231 @@ __global__ void __launch_bounds__(256) k_householder(TW* __restrict__ W, int64_t
   grid_sync(bar, status);
 }
 
+// ---------------------------------------------------------------------------
+// Blocked Householder QR.
+// ---------------------------------------------------------------------------
+constexpr int kPanelMax = 64;
+
+template <typename TW>
+__device__ __forceinline__ TW warp_sum_t(TW v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Factor the panel P = W[k0:d, k0:k0+b] (L = d - k0 rows, ld = d): for each
+// column j, the reflector of the unblocked kernel, applied to the panel's later
+// columns only.  Block g of G owns panel rows [L g / G, L (g+1) / G).  Per
+// column: (a) partial ||x_{j+1:}||^2 of my rows -> part, the owner of row j
+// publishes row j of the panel -> rowv; barrier; (b) every block sums the
+// partials in block order (same scalars everywhere), writes column j of U
+// (unit lower trapezoid: 0 above row j, 1 at j, x_i / (alpha - beta) below);
+// (c) partial dots of x with the later columns -> part; barrier; (d) every
+// block updates its rows of the later columns.  part and rowv alternate by
+// column parity, so a block one step ahead never overwrites what a slower
+// block still reads.
+template <typename TW>
+__global__ void __launch_bounds__(256) k_panel(TW* __restrict__ W, int64_t ld, int64_t k0, int64_t L, int b,
+                                               TW* __restrict__ U, double* __restrict__ rdiag, TW* __restrict__ tau,
+                                               TW* __restrict__ part, TW* __restrict__ rowv, GridBarrier* bar,
+                                               uint32_t* status) {
+  __shared__ TW scratch[32];
+  const int G = gridDim.x, g = blockIdx.x;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int64_t r0 = L * g / G, r1 = L * (g + 1) / G;
+  TW* P = W + k0 * ld + k0;
+  const int PS = kPanelMax + 2;
+  auto sync = [&]() -> bool {
+    if (G == 1) {
+      __syncthreads();
+      return true;
+    }
+    return grid_sync(bar, status, (unsigned int)G);
+  };
+  for (int j = 0; j < b; ++j) {
+    // the previous step's updates of this block's rows (other warps) come first
+    __syncthreads();
+    const int par = j & 1;
+    const TW* pj = P + (int64_t)j * ld;
+    TW* prt = part + (int64_t)par * G * PS;
+    TW* rv = rowv + par * kPanelMax;
+    const int64_t i0 = r0 > j + 1 ? r0 : (int64_t)j + 1;
+    TW s = 0;
+    for (int64_t i = i0 + threadIdx.x; i < r1; i += blockDim.x) {
+      const TW x = __ldcg(pj + i);
+      s = fma(x, x, s);
+    }
+    s = block_sum_t<TW>(s, scratch);
+    if (threadIdx.x == 0) prt[(int64_t)g * PS] = s;
+    if (j >= r0 && j < r1)
+      for (int jj = j + threadIdx.x; jj < b; jj += blockDim.x) rv[jj] = __ldcg(P + (int64_t)jj * ld + j);
+    if (!sync()) return;
+    TW sigma = 0;
+    for (int q = 0; q < G; ++q) sigma += __ldcg(prt + (int64_t)q * PS);
+    const TW alpha = __ldcg(rv + j);
+    TW beta = alpha, t = 0, inv_v0 = 0;
+    if (sigma != (TW)0) {
+      const TW nrm = sqrt(fma(alpha, alpha, sigma));
+      beta = alpha >= (TW)0 ? -nrm : nrm;
+      t = (beta - alpha) / beta;
+      inv_v0 = (TW)1 / (alpha - beta);
+    }
+    if (g == 0 && threadIdx.x == 0) {
+      rdiag[k0 + j] = (double)beta;
+      tau[j] = t;
+    }
+    TW* uj = U + (int64_t)j * ld;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x)
+      uj[i] = i < j ? (TW)0 : (i == j ? (TW)1 : __ldcg(pj + i) * inv_v0);
+    if (t == (TW)0) continue;  // same in every block: same barrier count
+    for (int jj = j + 1 + wib; jj < b; jj += nwarps) {
+      const TW* pjj = P + (int64_t)jj * ld;
+      TW acc = 0;
+      for (int64_t i = i0 + lane; i < r1; i += 32) acc = fma(__ldcg(pj + i), __ldcg(pjj + i), acc);
+      acc = warp_sum_t<TW>(acc);
+      if (lane == 0) prt[(int64_t)g * PS + 1 + jj] = acc;
+    }
+    if (!sync()) return;
+    for (int jj = j + 1 + wib; jj < b; jj += nwarps) {
+      TW S = 0;
+      for (int q = 0; q < G; ++q) S += __ldcg(prt + (int64_t)q * PS + 1 + jj);
+      const TW wj = __ldcg(rv + jj);
+      const TW f = t * fma(inv_v0, S, wj);
+      const TW fv = f * inv_v0;
+      TW* pjj = P + (int64_t)jj * ld;
+      for (int64_t i = i0 + lane; i < r1; i += 32) pjj[i] = fma(-fv, __ldcg(pj + i), __ldcg(pjj + i));
+      if (lane == 0 && j >= r0 && j < r1) pjj[j] = wj - f;
+    }
+  }
+}
+
+// T (b x b, column-major, upper) of Q = I - U T U^T from the Gram U^T U and
+// tau (LAPACK larft, forward, columnwise): T[j][j] = tau_j,
+// T[0:j, j] = -tau_j T[0:j, 0:j] (U[:, 0:j]^T u_j).  One block.
+template <typename TW>
+__global__ void __launch_bounds__(256) k_tform(const TW* __restrict__ gram, const TW* __restrict__ tau, int b,
+                                               TW* __restrict__ T) {
+  __shared__ TW sT[kPanelMax * kPanelMax];
+  __shared__ TW w[kPanelMax];
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) sT[e] = 0;
+  __syncthreads();
+  for (int j = 0; j < b; ++j) {
+    const TW tj = tau[j];
+    if (threadIdx.x < j) w[threadIdx.x] = gram[threadIdx.x + (int64_t)j * b];
+    __syncthreads();
+    if (threadIdx.x < j) {
+      TW s = 0;
+      for (int l = threadIdx.x; l < j; ++l) s = fma(sT[threadIdx.x + l * b], w[l], s);
+      sT[threadIdx.x + j * b] = -tj * s;
+    }
+    if (threadIdx.x == 0) sT[j + j * b] = tj;
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) T[e] = sT[e];
+}
+
+cublasStatus_t gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, double alpha,
+                    const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc) {
+  return cublasDgemm(h, ta, tb, m, n, k, &alpha, A, lda, B, ldb, &beta, C, ldc);
+}
+cublasStatus_t gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, float alpha,
+                    const float* A, int lda, const float* B, int ldb, float beta, float* C, int ldc) {
+  return cublasGemmEx(h, ta, tb, m, n, k, &alpha, A, CUDA_R_32F, lda, B, CUDA_R_32F, ldb, &beta, C, CUDA_R_32F, ldc,
+                      CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUBLAS_GEMM_DEFAULT);
+}
+
+template <typename TW>
+constexpr int panel_width() {
+  return sizeof(TW) == 4 ? 64 : 32;
+}
+
+struct BlockedScratch {
+  size_t oU, oGram, oT, oZ, oZ2, oTau, oPart, oRow, bytes;
+};
+constexpr int kPanelBlocksMax = 64;
+BlockedScratch blocked_layout(int64_t d, int64_t n) {
+  auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+  BlockedScratch s;
+  size_t o = 0;
+  const size_t ncol = (size_t)n + 1;
+  s.oU = o; o += al((size_t)d * kPanelMax * 8);
+  s.oGram = o; o += al((size_t)kPanelMax * kPanelMax * 8);
+  s.oT = o; o += al((size_t)kPanelMax * kPanelMax * 8);
+  s.oZ = o; o += al((size_t)kPanelMax * ncol * 8);
+  s.oZ2 = o; o += al((size_t)kPanelMax * ncol * 8);
+  s.oTau = o; o += al((size_t)kPanelMax * 8);
+  s.oPart = o; o += al((size_t)2 * kPanelBlocksMax * (kPanelMax + 2) * 8);
+  s.oRow = o; o += al((size_t)2 * kPanelMax * 8);
+  s.bytes = o;
+  return s;
+}
+
+// The blocked factorisation of the d x ncol column-major W (first kmax = n
+// columns reflected, the rest -- the sketched b column -- transformed).
+template <typename TW>
+cudaError_t householder_blocked(TW* W, int64_t d, int n, int ncol, double* rdiag, const PrecondBuffers& buf, int sms,
+                                cudaStream_t st) {
+  const BlockedScratch L0 = blocked_layout(d, n);
+  char* s = static_cast<char*>(buf.blk);
+  TW* U = reinterpret_cast<TW*>(s + L0.oU);
+  TW* gram = reinterpret_cast<TW*>(s + L0.oGram);
+  TW* T = reinterpret_cast<TW*>(s + L0.oT);
+  TW* Z = reinterpret_cast<TW*>(s + L0.oZ);
+  TW* Z2 = reinterpret_cast<TW*>(s + L0.oZ2);
+  TW* tau = reinterpret_cast<TW*>(s + L0.oTau);
+  TW* part = reinterpret_cast<TW*>(s + L0.oPart);
+  TW* rowv = reinterpret_cast<TW*>(s + L0.oRow);
+  cublasHandle_t h = static_cast<cublasHandle_t>(buf.blas);
+  if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+  constexpr int nb = panel_width<TW>();
+  const int kmax = n < d ? n : (int)d;
+  const int ld = (int)d;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_panel<TW>, 256, 0);
+  if (e != cudaSuccess) return e;
+  for (int k0 = 0; k0 < kmax; k0 += nb) {
+    const int b = kmax - k0 < nb ? kmax - k0 : nb;
+    const int64_t L = d - k0;
+    // the panel's rows spread over blocks (~256 rows each): one block would
+    // stream the whole panel from L2 for every column
+    int G = (int)std::min<int64_t>((L + 255) / 256, kPanelBlocksMax);
+    G = std::min(G, std::max(1, per_sm * sms));
+    if (G < 1) G = 1;
+    TW* Wp = W;
+    int64_t ld64 = d, k064 = k0, L64 = L;
+    int bb = b;
+    double* rd = rdiag;
+    GridBarrier* bar = buf.bar;
+    uint32_t* status = buf.status;
+    void* args[] = {&Wp, &ld64, &k064, &L64, &bb, &U, &rd, &tau, &part, &rowv, &bar, &status};
+    if (G == 1)
+      e = cudaLaunchKernel((const void*)k_panel<TW>, 1, 256, args, 0, st);
+    else
+      e = cudaLaunchCooperativeKernel((const void*)k_panel<TW>, G, 256, args, 0, st);
+    if (e != cudaSuccess) return e;
+    const int c = ncol - k0 - b;
+    if (c <= 0) continue;
+    TW* C = W + (int64_t)(k0 + b) * d + k0;
+    const int Li = (int)L;
+    if (gemm(h, CUBLAS_OP_T, CUBLAS_OP_N, b, b, Li, (TW)1, U, ld, U, ld, (TW)0, gram, b) != CUBLAS_STATUS_SUCCESS)
+      return cudaErrorUnknown;
+    k_tform<TW><<<1, 256, 0, st>>>(gram, tau, b, T);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (gemm(h, CUBLAS_OP_T, CUBLAS_OP_N, b, c, Li, (TW)1, U, ld, C, ld, (TW)0, Z, b) != CUBLAS_STATUS_SUCCESS ||
+        gemm(h, CUBLAS_OP_T, CUBLAS_OP_N, b, c, b, (TW)1, T, b, Z, b, (TW)0, Z2, b) != CUBLAS_STATUS_SUCCESS ||
+        gemm(h, CUBLAS_OP_N, CUBLAS_OP_N, Li, c, b, (TW)-1, U, ld, Z2, b, (TW)1, C, ld) != CUBLAS_STATUS_SUCCESS)
+      return cudaErrorUnknown;
+  }
+  return cudaSuccess;
+}
+
+// Automatic choice: the blocked path once the working copy W no longer sits
+// comfortably in L2 (the unblocked kernel then streams the trailing matrix
+// from HBM for every column); below that the unblocked kernel's single
+// barrier per column is cheaper than the panel's two plus the GEMM launches.
+constexpr int kBlockedMinN = 128;
+constexpr size_t kBlockedMinBytes = (size_t)32 << 20;
+
 // R (row-major n x n, upper), z = W[n][0:n] (x0 slot), and the rank test
 // |R_kk| <= n * eps * max_i |R_ii|.
 template <typename TW>
@@ -181,6 +419,8 @@ __global__ void k_matvec_upper(const double* __restrict__ M, int n, const TZ* __
 
 }  // namespace
 
+size_t precond_blocked_bytes(int64_t d, int64_t n) { return blocked_layout(d, n).bytes; }
+
 cudaError_t transpose_square(const double* src, int n, double* dst, cudaStream_t st) {
   dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32)), block(32, 8);
   k_transpose<<<grid, block, 0, st>>>(src, n, dst);
@@ -200,7 +440,11 @@ cudaError_t precond(const TY* Y, int64_t d, int64_t n64, int64_t ldy, int has_b,
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if ((e = cudaMemsetAsync(buf.bar, 0, sizeof(GridBarrier), st)) != cudaSuccess) return e;
-  {
+  const bool big = n >= kBlockedMinN && (size_t)d * ncol * sizeof(TY) >= kBlockedMinBytes;
+  const bool blocked = buf.mode == 2 || (buf.mode == 0 && big);
+  if (buf.blk && buf.blas && blocked && (size_t)kPanelMax * ncol <= ((size_t)1 << 31)) {
+    if ((e = householder_blocked<TY>(W, d, n, ncol, buf.rdiag, buf, sms, st)) != cudaSuccess) return e;
+  } else {
     int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_householder<TY>, 256, 0)) != cudaSuccess)
       return e;

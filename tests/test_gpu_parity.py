@@ -94,6 +94,42 @@ def test_precond_fp32_from_fp32_sketch(ctx, orc):
     assert np.linalg.norm(A @ (x0.cpu().numpy() - Mo @ Ro[:64, 64])) <= 1e-5 * np.linalg.norm(b)
 
 
+@pytest.mark.parametrize("m,n,d", [(20000, 300, 1200), (8000, 130, 300)])
+def test_precond_fp32_blocked(ctx, orc, m, n, d):
+    """Mixed form, blocked FP32 QR (one-block panels of 64, trailing updates as
+    FP32-accurate tensor-core GEMMs): cond(AM) stays at the FP64 value."""
+    A, b, _ = _problem(m, n, 1e5, n + 7)
+    Y32 = ctx.lsq_sketch(_dev(A), _dev(b), d, 8, 5, prec=1)
+    ctx.lsq_set_qr_mode(2)
+    try:
+        R, M, x0 = ctx.lsq_precond(Y32, n, has_b=True)
+    finally:
+        ctx.lsq_set_qr_mode(0)
+    M = M.cpu().numpy()
+    sv = np.linalg.svd(A @ M, compute_uv=False)
+    Yo = orc.sketch_apply(A, b, d, 8, 5)
+    Ro, _, _ = orc.householder_qr(Yo)
+    Mo = orc.tri_inverse(Ro[:n, :n])
+    svo = np.linalg.svd(A @ Mo, compute_uv=False)
+    assert sv[0] / sv[-1] <= 1.05 * svo[0] / svo[-1]
+    assert np.linalg.norm(A @ (x0.cpu().numpy() - Mo @ Ro[:n, n])) <= 1e-4 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_solve_mixed_matches_plain_wide(ctx, orc, mode):
+    A, b, xt = _problem(40000, 600, 1e6, 45)
+    ctx.lsq_set_qr_mode(mode)
+    try:
+        xp, ip = ctx.lsq_solve(_dev(A), _dev(b), 2400, seed=3, tol=1e-12, prec=0)
+        xm, im = ctx.lsq_solve(_dev(A), _dev(b), 2400, seed=3, tol=1e-12, prec=1)
+    finally:
+        ctx.lsq_set_qr_mode(0)
+    assert ip["status"] == 0 and im["status"] == 0 and im["precond_fallback"] == 0
+    bn = np.linalg.norm(b)
+    assert np.linalg.norm(A @ (xm.cpu().numpy() - xp.cpu().numpy())) <= 1e-10 * bn
+    assert orc.backward_error_kw(A, b, xp.cpu().numpy()) <= 1e-10
+
+
 def test_solve_mixed_falls_back_when_fp32_sketch_is_too_coarse(ctx, orc):
     """cond 1e12: the FP32 sketch cannot precondition; the mixed solve stalls,
     re-solves in FP64 and still meets the accuracy bar."""
@@ -149,12 +185,20 @@ def test_sketch_detects_nonfinite(ctx):
 
 
 # ---------------------------------------------------------- precondition ---
-@pytest.mark.parametrize("m,n,d,cond", [(20000, 200, 800, 1e8), (3000, 31, 124, 1e4), (500, 1, 8, 1.0),
-                                        (4000, 64, 65, 1e6)])
-def test_precond_matches_oracle(ctx, orc, m, n, d, cond):
+# mode 2 forces the blocked QR (panels of 32 in FP64, rows spread over blocks;
+# 700 = 21 panels + a remainder of 28; 129 = 4 panels + 1), mode 1 the unblocked
+@pytest.mark.parametrize("m,n,d,cond,mode", [(20000, 200, 800, 1e8, 1), (3000, 31, 124, 1e4, 0),
+                                             (500, 1, 8, 1.0, 0), (4000, 64, 65, 1e6, 0),
+                                             (20000, 200, 800, 1e8, 2), (12000, 700, 1400, 1e6, 2),
+                                             (6000, 129, 600, 1e8, 2)])
+def test_precond_matches_oracle(ctx, orc, m, n, d, cond, mode):
     A, b, _ = _problem(m, n, cond, n)
     Yo = orc.sketch_apply(A, b, d, 8, 11)
-    R, M, x0 = ctx.lsq_precond(_dev(Yo), n, has_b=True)
+    ctx.lsq_set_qr_mode(mode)
+    try:
+        R, M, x0 = ctx.lsq_precond(_dev(Yo), n, has_b=True)
+    finally:
+        ctx.lsq_set_qr_mode(0)
     R, M, x0 = R.cpu().numpy(), M.cpu().numpy(), x0.cpu().numpy()
     Ro, _, _ = orc.householder_qr(Yo)
     Ro = Ro[:n, :n]
