@@ -50,9 +50,11 @@ def test_sketch_indices_bit_exact(ctx, orc, d, zeta, row0, rows):
     assert np.array_equal(rnd.cpu().numpy(), orr)
 
 
+# larger m: many row blocks, ragged last warp block (70001), wide d, zeta < 8, no b
 @pytest.mark.parametrize("m,n,d,zeta,has_b", [(20000, 200, 800, 8, True), (3001, 37, 120, 8, True),
                                               (513, 1, 16, 3, False), (1000, 129, 400, 16, True),
-                                              (257, 64, 300, 64, True)])
+                                              (257, 64, 300, 64, True), (80000, 50, 300, 8, True),
+                                              (70001, 33, 2560, 5, True), (66000, 16, 64, 8, False)])
 def test_sketch_apply_fp64(ctx, orc, m, n, d, zeta, has_b):
     rng = np.random.default_rng(m + n)
     A = rng.standard_normal((m, n))
@@ -320,6 +322,18 @@ def test_solve_edge_shapes(ctx, orc):
     with pytest.raises(P.LsqError) as e:
         ctx.lsq_solve(_dev(A), _dev(b), 1)
     assert e.value.status == -1
+
+
+def test_solve_tall_matches_oracle(ctx, orc):
+    """A taller solve (100000 x 64, d = 256) against the oracle end to end."""
+    A, b, xt = _problem(100000, 64, 1e8, 17)
+    x, info = ctx.lsq_solve(_dev(A), _dev(b), 256, seed=4, tol=1e-12)
+    x = x.cpu().numpy()
+    ref = orc.solve(A, b, 256, 8, 4, 1e-12, orc.default_maxit(64, 256, 1e-12))
+    assert info["status"] == 0
+    assert abs(info["iters"] - ref["iters"]) <= 2
+    assert np.linalg.norm(A @ (x - ref["x"])) <= 1e-10 * np.linalg.norm(b)
+    assert orc.backward_error_kw(A, b, x) <= 1e-10
 
 
 def test_solve_consistent_system(ctx, orc):
