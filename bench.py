@@ -116,6 +116,12 @@ def _workload(p, prec):
             if 8 * m * n > L2_BYTES else "inputs fit in L2 (small config)"}
 
 
+# DRAM traffic / algorithmic bytes of the double-float LSQR kernel, from the ncu
+# capture summarised in profiles/lsqr_df_1000000x500.md (1e6 x 500, 5 passes:
+# 25.33 GB measured for 24.08 GB algorithmic); traffic grows with passes x rows.
+LSQR_DF_TRAFFIC_RATIO = 25.33 / 24.08
+
+
 def lsqr_algorithmic_bytes(m, n, iters):
     """Bytes the LSQR kernel must move per launch: per LSQR iteration one read
     of A (8mn), u read+write (16m) and M, M^T (16n^2); plus the initial
@@ -650,7 +656,9 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": dict(_workload(p, args.prec), parallelism="replicas" if world > 1 else "single"),
         "roofline": {"bound": "hbm", "kernel": "k_lsqr_native" if args.native else "k_lsqr_df", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None if (args.native or n > 512 or args.prec != "fp64")
+                     else LSQR_DF_TRAFFIC_RATIO * alg_bytes,
                      "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
                      else "fallback 6.8 TB/s"},
         "gpu_launches": 8 * args.steps,

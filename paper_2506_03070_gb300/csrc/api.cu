@@ -547,8 +547,11 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
     for (auto& e : ev) CK(cudaEventCreate(&e));
   if (timing) CK(cudaEventRecord(ev[0], st));
   if (host) {
-    CK(cudaMemcpy2DAsync((void*)A, sizeof(double) * n, pr->A, sizeof(double) * lda, sizeof(double) * n, m,
-                         cudaMemcpyHostToDevice, st));
+    if (lda == n)  // packed rows: one flat copy
+      CK(cudaMemcpyAsync((void*)A, pr->A, sizeof(double) * (size_t)m * n, cudaMemcpyHostToDevice, st));
+    else
+      CK(cudaMemcpy2DAsync((void*)A, sizeof(double) * n, pr->A, sizeof(double) * lda, sizeof(double) * n, m,
+                           cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync((void*)b, pr->b, sizeof(double) * m, cudaMemcpyHostToDevice, st));
   }
   if (timing) CK(cudaEventRecord(ev[1], st));

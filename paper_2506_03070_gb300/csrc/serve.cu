@@ -533,8 +533,11 @@ struct Server {
         r->item.b = bd;
         r->item.x = reinterpret_cast<double*>(slot + r->oX);
         r->item.lda = r->pr.n;
-        cudaMemcpy2DAsync(Ad, sizeof(double) * r->pr.n, r->pr.A, sizeof(double) * r->pr.lda,
-                          sizeof(double) * r->pr.n, r->pr.m, cudaMemcpyHostToDevice, s_copy);
+        if (r->pr.lda == r->pr.n)
+          cudaMemcpyAsync(Ad, r->pr.A, sizeof(double) * (size_t)r->pr.m * r->pr.n, cudaMemcpyHostToDevice, s_copy);
+        else
+          cudaMemcpy2DAsync(Ad, sizeof(double) * r->pr.n, r->pr.A, sizeof(double) * r->pr.lda,
+                            sizeof(double) * r->pr.n, r->pr.m, cudaMemcpyHostToDevice, s_copy);
         cudaMemcpyAsync(bd, r->pr.b, sizeof(double) * r->pr.m, cudaMemcpyHostToDevice, s_copy);
       }
       cudaMemcpyAsync(slot + r->item.oCtl, h_zero, sizeof(ServeCtl), cudaMemcpyHostToDevice, s_copy);
