@@ -133,18 +133,31 @@ __device__ bool householder_group(double* W, int d, int n, int ncol, double* rdi
     if (tau == 0.0) continue;
     for (int j = k + 1 + gw; j < ncol; j += nw) {
       double* wj = W + (int64_t)j * d;
-      double s0 = 0.0, s1 = 0.0;
+      // 8 loads in flight per lane and 8 partial sums (load-latency bound)
+      double s8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
       int i = k + 1 + lane;
-      for (; i + 32 < d; i += 64) {
-        s0 = fma(__ldcg(wk + i), __ldcg(wj + i), s0);
-        s1 = fma(__ldcg(wk + i + 32), __ldcg(wj + i + 32), s1);
+      for (; i + 7 * 32 < d; i += 8 * 32) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s8[u] = fma(__ldcg(wk + i + 32 * u), __ldcg(wj + i + 32 * u), s8[u]);
       }
-      if (i < d) s0 = fma(__ldcg(wk + i), __ldcg(wj + i), s0);
-      const double s = warp_allreduce_sum(s0 + s1);
+      for (; i < d; i += 32) s8[0] = fma(__ldcg(wk + i), __ldcg(wj + i), s8[0]);
+      const double s =
+          warp_allreduce_sum(((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7])));
       const double f = tau * fma(inv_v0, s, __ldcg(wj + k));
       const double fv = f * inv_v0;
       if (lane == 0) wj[k] = __ldcg(wj + k) - f;
-      for (int i2 = k + 1 + lane; i2 < d; i2 += 32) wj[i2] = fma(-fv, __ldcg(wk + i2), __ldcg(wj + i2));
+      int i2 = k + 1 + lane;
+      for (; i2 + 7 * 32 < d; i2 += 8 * 32) {
+        double a[8], w[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          a[u] = __ldcg(wk + i2 + 32 * u);
+          w[u] = __ldcg(wj + i2 + 32 * u);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) wj[i2 + 32 * u] = fma(-fv, a[u], w[u]);
+      }
+      for (; i2 < d; i2 += 32) wj[i2] = fma(-fv, __ldcg(wk + i2), __ldcg(wj + i2));
     }
   }
   return gsync(g);

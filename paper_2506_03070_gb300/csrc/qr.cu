@@ -90,21 +90,33 @@ __global__ void __launch_bounds__(256) k_householder(TW* __restrict__ W, int64_t
     if (tau == (TW)0) continue;
     for (int j = k + 1 + gw; j < ncol; j += nw) {
       TW* wj = W + (int64_t)j * d;
-      // two partial sums shorten the dependent chain
-      TW s0 = 0, s1 = 0;
+      // 8 loads in flight per lane and 8 partial sums: the column is streamed
+      // from L2, so the loop is bound by load latency, not arithmetic
+      TW s8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
       int64_t i = k + 1 + lane;
-      for (; i + 32 < d; i += 64) {
-        s0 = fma(wk[i], wj[i], s0);
-        s1 = fma(wk[i + 32], wj[i + 32], s1);
+      for (; i + 7 * 32 < d; i += 8 * 32) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s8[u] = fma(wk[i + 32 * u], wj[i + 32 * u], s8[u]);
       }
-      if (i < d) s0 = fma(wk[i], wj[i], s0);
-      TW s = s0 + s1;
+      for (; i < d; i += 32) s8[0] = fma(wk[i], wj[i], s8[0]);
+      TW s = ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       const TW f = tau * fma(inv_v0, s, wj[k]);
       const TW fv = f * inv_v0;
       if (lane == 0) wj[k] -= f;
-      for (int64_t i2 = k + 1 + lane; i2 < d; i2 += 32) wj[i2] = fma(-fv, wk[i2], wj[i2]);
+      int64_t i2 = k + 1 + lane;
+      for (; i2 + 7 * 32 < d; i2 += 8 * 32) {
+        TW a[8], w[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          a[u] = wk[i2 + 32 * u];
+          w[u] = wj[i2 + 32 * u];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) wj[i2 + 32 * u] = fma(-fv, a[u], w[u]);
+      }
+      for (; i2 < d; i2 += 32) wj[i2] = fma(-fv, wk[i2], wj[i2]);
     }
   }
   grid_sync(bar, status);
