@@ -65,18 +65,25 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 }
 
 // ---------------------------------------------------------------------------
-// Grid barrier for cooperative (co-resident) launches.  State: {count, gen,
-// abort}, zeroed by the host before the launch.  Every wait is bounded by
-// kBarrierTimeoutNs; on timeout the block raises DS_TIMEOUT and the abort flag,
-// and every block leaves at its next barrier.  Returns false when the caller
-// must exit.
+// Grid barrier for cooperative (co-resident) launches: a ticket barrier on
+// one counter.  Thread 0 of each block arrives with one release atomic
+// (count += 1) and polls the same word with acquire loads until the round's
+// nblocks arrivals are in: target = (arrival / nblocks + 1) * nblocks.  The
+// counter is zeroed by the host before a launch and advances by nblocks per
+// barrier, so it stays a multiple of nblocks between barriers (a launch with a
+// different block count needs it zeroed again).  Abort is the top bit of the
+// same word, seen by every arrival and poll without an extra load.  Every wait
+// is bounded by kBarrierTimeoutNs; on timeout the block raises DS_TIMEOUT and
+// the abort bit, and every block leaves at its next barrier.  Returns false
+// when the caller must exit.
 // ---------------------------------------------------------------------------
 struct GridBarrier {
-  unsigned int count;
-  unsigned int gen;
-  unsigned int abort;
+  unsigned int count;  // arrivals (low 31 bits) | kBarrierAbort
+  unsigned int gen;    // unused
+  unsigned int abort;  // unused (kept for layout)
   unsigned int pad;
 };
+constexpr unsigned int kBarrierAbort = 0x80000000u;
 
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
   unsigned int v;
@@ -86,40 +93,42 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
 __device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ unsigned int atom_add_release_u32(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+// Raise the abort bit: every block of the barrier leaves at its next barrier.
+__device__ __forceinline__ void barrier_abort(GridBarrier* bar) { atomicOr(&bar->count, kBarrierAbort); }
 
 __device__ __forceinline__ bool grid_sync(GridBarrier* bar, uint32_t* status, unsigned int nblocks) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    if (ld_acquire_u32(&bar->abort)) {
+    const unsigned int a = atom_add_release_u32(&bar->count, 1u);
+    if (a & kBarrierAbort) {
       ok = 0;
     } else {
-      const unsigned int g = ld_acquire_u32(&bar->gen);
-      __threadfence();
-      const unsigned int arrived = atomicAdd(&bar->count, 1u);
-      if (arrived == nblocks - 1) {
-        bar->count = 0;
-        __threadfence();
-        st_release_u32(&bar->gen, g + 1);
-      } else {
+      const unsigned int target = (a / nblocks + 1u) * nblocks;
+      unsigned int v = ld_acquire_u32(&bar->count);
+      if (!(v & kBarrierAbort) && (int)(v - target) < 0) {
         const unsigned long long t0 = globaltimer_ns();
         unsigned int spins = 0;
-        while (ld_acquire_u32(&bar->gen) == g) {
-          if (ld_acquire_u32(&bar->abort)) {
-            ok = 0;
-            break;
-          }
+        for (;;) {
+          __nanosleep(20);
+          v = ld_acquire_u32(&bar->count);
+          if ((v & kBarrierAbort) || (int)(v - target) >= 0) break;
           if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > kBarrierTimeoutNs) {
             atomicOr(status, DS_TIMEOUT);
-            atomicExch(&bar->abort, 1u);
-            ok = 0;
+            barrier_abort(bar);
+            v = kBarrierAbort;
             break;
           }
-          __nanosleep(32);
         }
-        __threadfence();
       }
+      if (v & kBarrierAbort) ok = 0;
     }
     s_ok = ok;
   }

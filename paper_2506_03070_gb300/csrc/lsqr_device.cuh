@@ -450,7 +450,7 @@ struct DfPass {
       // give up: flag, then let the copies already issued land before leaving
       if (lane == 0) {
         atomicOr(p.status, DS_TIMEOUT);
-        atomicExch(&p.bar->abort, 1u);
+        barrier_abort(p.bar);
       }
       for (uint32_t k = jc; k < count && k < jc + kNbuf; ++k) wait(k, mybars);
     }
@@ -556,7 +556,7 @@ struct DfPass {
         failed_at = jc;
         if (lane == 0) {
           atomicOr(p.status, DS_TIMEOUT);
-          atomicExch(&p.bar->abort, 1u);
+          barrier_abort(p.bar);
         }
       }
       const int64_t row = r0 + rg + (int64_t)NRG * jc;

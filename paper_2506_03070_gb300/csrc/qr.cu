@@ -64,13 +64,14 @@ __device__ __forceinline__ T block_sum_t(T v, T* scratch) {
 }
 
 // TW = double (plain form) or float (mixed form: FP32 factorisation).
+// One block per trailing column (columns j = k+1+blockIdx.x, step gridDim.x):
+// its 256 threads share the column's dot product (fixed-order block sum) and
+// its update, so every SM's FP64 pipe works on the step -- on GB300 the FP64
+// rate, not memory, bounds a column step on few SMs.
 template <typename TW>
 __global__ void __launch_bounds__(256) k_householder(TW* __restrict__ W, int64_t d, int n, int ncol,
                                                      double* __restrict__ rdiag, GridBarrier* bar, uint32_t* status) {
   __shared__ TW scratch[32];
-  const int lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int nw = gridDim.x * (blockDim.x >> 5);
   const int kmax = n < d ? n : (int)d;
   for (int k = 0; k < kmax; ++k) {
     if (!grid_sync(bar, status)) return;
@@ -88,35 +89,16 @@ __global__ void __launch_bounds__(256) k_householder(TW* __restrict__ W, int64_t
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) rdiag[k] = (double)beta;
     if (tau == (TW)0) continue;
-    for (int j = k + 1 + gw; j < ncol; j += nw) {
+    for (int j = k + 1 + blockIdx.x; j < ncol; j += gridDim.x) {
       TW* wj = W + (int64_t)j * d;
-      // 8 loads in flight per lane and 8 partial sums: the column is streamed
-      // from L2, so the loop is bound by load latency, not arithmetic
-      TW s8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      int64_t i = k + 1 + lane;
-      for (; i + 7 * 32 < d; i += 8 * 32) {
-#pragma unroll
-        for (int u = 0; u < 8; ++u) s8[u] = fma(wk[i + 32 * u], wj[i + 32 * u], s8[u]);
-      }
-      for (; i < d; i += 32) s8[0] = fma(wk[i], wj[i], s8[0]);
-      TW s = ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      const TW f = tau * fma(inv_v0, s, wj[k]);
+      const TW wjk = wj[k];  // every thread reads it before thread 0 rewrites it (after the block sum)
+      TW s = 0;
+      for (int64_t i = k + 1 + threadIdx.x; i < d; i += blockDim.x) s = fma(wk[i], wj[i], s);
+      s = block_sum_t<TW>(s, scratch);
+      const TW f = tau * fma(inv_v0, s, wjk);
       const TW fv = f * inv_v0;
-      if (lane == 0) wj[k] -= f;
-      int64_t i2 = k + 1 + lane;
-      for (; i2 + 7 * 32 < d; i2 += 8 * 32) {
-        TW a[8], w[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          a[u] = wk[i2 + 32 * u];
-          w[u] = wj[i2 + 32 * u];
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) wj[i2 + 32 * u] = fma(-fv, a[u], w[u]);
-      }
-      for (; i2 < d; i2 += 32) wj[i2] = fma(-fv, wk[i2], wj[i2]);
+      if (threadIdx.x == 0) wj[k] = wjk - f;
+      for (int64_t i = k + 1 + threadIdx.x; i < d; i += blockDim.x) wj[i] = fma(-fv, wk[i], wj[i]);
     }
   }
   grid_sync(bar, status);
@@ -319,6 +301,8 @@ cudaError_t householder_blocked(TW* W, int64_t d, int n, int ncol, double* rdiag
     GridBarrier* bar = buf.bar;
     uint32_t* status = buf.status;
     void* args[] = {&Wp, &ld64, &k064, &L64, &bb, &U, &rd, &tau, &part, &rowv, &bar, &status};
+    // the ticket barrier's counter restarts for each launch (G changes with L)
+    if (G > 1 && (e = cudaMemsetAsync(buf.bar, 0, sizeof(GridBarrier), st)) != cudaSuccess) return e;
     if (G == 1)
       e = cudaLaunchKernel((const void*)k_panel<TW>, 1, 256, args, 0, st);
     else
@@ -460,9 +444,10 @@ cudaError_t precond(const TY* Y, int64_t d, int64_t n64, int64_t ldy, int has_b,
     int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_householder<TY>, 256, 0)) != cudaSuccess)
       return e;
-    int blocks = (ncol + 7) / 8;
-    blocks = blocks < sms ? blocks : sms;
-    if (blocks > per_sm * sms) blocks = per_sm * sms;
+    // one block per trailing column, at most 2 per SM
+    int blocks = ncol - 1;
+    const int cap = (per_sm < 2 ? per_sm : 2) * sms;
+    if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     int64_t dd = d;
     int nn = n, nc = ncol;
