@@ -86,6 +86,17 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x, device):
+    """x from every rank -> the largest (barrier first); x itself on one rank."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -607,12 +618,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     total_ms = ev0.elapsed_time(ev1)
-    t_tensor = torch.tensor([total_ms], dtype=torch.float64, device=f"cuda:{local}")
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-        dist.all_reduce(t_tensor, op=dist.ReduceOp.MAX)
-    t_max = float(t_tensor.item())
+    t_max = max_over_ranks(total_ms, f"cuda:{local}")
     value = world * args.steps / (t_max / 1e3)
 
     # accuracy of the last solution (outside the timed region)
