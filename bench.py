@@ -679,6 +679,26 @@ def run_gpu(args):
         "clocks": clocks,
         "e2e": e2e,
     }
+    if rank == 0 and world == 1 and not args.no_auto_d:
+        # the same A and b with the embedding dimension chosen by lsq_choose_d
+        # (Sec. 4.3 balance with this GPU's measured constants); the headline
+        # value above keeps the configuration's d
+        d_auto = ctx.lsq_choose_d(m, n, tol)
+        for _ in range(2):
+            xa, ia = ctx.lsq_solve(A, b, 0, zeta=zeta, seed=seed, tol=tol, prec=prec, flags=flags, stream=stream)
+        ms_a = []
+        for _ in range(max(1, min(args.steps, 3))):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            xa, ia = ctx.lsq_solve(A, b, 0, zeta=zeta, seed=seed, tol=tol, prec=prec, flags=flags, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms_a.append(e0.elapsed_time(e1))
+        line["auto_d"] = {"d": ia["d_used"], "chosen": d_auto, "solves_per_s": 1e3 / statistics.mean(ms_a),
+                          "ms_per_solve": statistics.mean(ms_a), "lsqr_iters": ia["iters"],
+                          "phases_ms": {"sketch": ia["t_sketch_ms"], "precond": ia["t_precond_ms"],
+                                        "lsqr_and_check": ia["t_lsqr_ms"]},
+                          "backward_error_kw": oracle.backward_error_kw(A, b, xa)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle as orc
         orc.build()
@@ -725,6 +745,7 @@ def main():
     ap.add_argument("--maxit", type=int, default=0, help="cap LSQR iterations (profiling runs)")
     ap.add_argument("--no-check", action="store_true", help="skip the accuracy pass (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-auto-d", action="store_true", help="skip the extra solve with the chosen embedding dimension")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -76,7 +76,7 @@ typedef struct {
 
 /* Solver options (Algorithm 1 parameters d, zeta; Algorithm 2 tolerance). */
 typedef struct {
-  int64_t d;      /* embedding dimension, n+1 <= d <= 2^31-1 */
+  int64_t d;      /* embedding dimension, n+1 <= d <= 2^31-1; 0 = chosen by lsq_choose_d (lsq_solve) */
   int32_t zeta;   /* nonzeros per sketch column, 1 <= zeta <= min(d, 64) */
   int32_t prec;   /* lsq_prec */
   uint64_t seed;  /* sketch seed (Philox key) */
@@ -115,6 +115,7 @@ typedef struct {
   double t_submit_s, t_start_s, t_done_s;
   int32_t group_blocks;
   float t_group_wait_ms;
+  int64_t d_used; /* lsq_solve: the embedding dimension used (the chosen one when opts->d == 0) */
 } lsq_info;
 
 /* Context on `device` with a workspace budget of hbm_budget_bytes (0 = 90% of
@@ -162,6 +163,25 @@ lsq_status lsq_precond(lsq_ctx* ctx, const void* Y, int64_t d, int64_t n, int64_
  * emulated with three BF16 terms for the mixed form) once the d x (n+1)
  * working copy reaches 32 MiB and n >= 128, the unblocked one (one grid
  * barrier per column) below.  Both compute the same reflectors. */
+/* ---- Embedding dimension (Sec. 4.3 "Selecting the embedding dimension") ----
+ * The solve time is modelled as T(d) = T_qr(d) + (t(d) + 2) T_iter(m): the
+ * preconditioner grows linearly in d, and the Sec. 4.3 rate estimate
+ * (n/d)^{t/2} <= tol gives t(d) = 2 |ln tol| / ln(d/n) LSQR iterations, each
+ * linear in m.  Its minimum has a closed form through the Lambert W function
+ * (the paper balances the two costs the same way with unit constants):
+ * d = n exp(2 W0(sqrt(C)/2)), C = 2 |ln tol| t_iter_per_row m / (t_qr_per_d n).
+ * lsq_choose_d measures t_iter_per_row (one LSQR iteration per row of A) and
+ * t_qr_per_d (preconditioner time per extra sketch row) on this GPU with
+ * synthetic data of width n, once per n and context (tens of ms; not while
+ * requests are being served), then clamps d to [max(n+1, 1.25 n), min(m,
+ * what fits in an eighth of the budget)].  lsq_solve with opts->d == 0 uses it
+ * and reports the choice in info->d_used. */
+lsq_status lsq_choose_d(lsq_ctx* ctx, int64_t m, int64_t n, double tol, int64_t* d);
+/* The model's minimiser for given constants (no clamping; 0 on bad input). */
+int64_t lsq_d_from_model(int64_t m, int64_t n, double tol, double t_iter_per_row, double t_qr_per_d);
+/* Principal branch W0 of the Lambert W function on [-1/e, inf) (NaN outside). */
+double lsq_lambert_w0(double x);
+
 #define LSQ_QR_AUTO 0
 #define LSQ_QR_UNBLOCKED 1
 #define LSQ_QR_BLOCKED 2

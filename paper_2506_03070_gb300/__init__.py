@@ -33,7 +33,7 @@ FLAG_TIMING, FLAG_NO_CHECK, FLAG_NATIVE_FP64, FLAG_NO_IMAGE, FLAG_NO_FALLBACK = 
 EXPORTS = ("lsq_create", "lsq_destroy", "lsq_last_error", "lsq_status_string", "lsq_workspace_bytes",
            "lsq_sketch_indices", "lsq_sketch", "lsq_precond", "lsq_lsqr", "lsq_check", "lsq_solve",
            "lsq_check_noalloc", "lsq_solve_batch", "lsq_submit", "lsq_poll", "lsq_serve_config",
-           "lsq_serve_stats_get", "lsq_set_qr_mode")
+           "lsq_serve_stats_get", "lsq_set_qr_mode", "lsq_choose_d", "lsq_d_from_model", "lsq_lambert_w0")
 QR_AUTO, QR_UNBLOCKED, QR_BLOCKED = 0, 1, 2
 
 
@@ -63,7 +63,7 @@ class Info(ctypes.Structure):
                 ("t_sketch_ms", ctypes.c_float), ("t_precond_ms", ctypes.c_float), ("t_lsqr_ms", ctypes.c_float),
                 ("t_check_ms", ctypes.c_float), ("t_h2d_ms", ctypes.c_float), ("t_d2h_ms", ctypes.c_float),
                 ("t_submit_s", ctypes.c_double), ("t_start_s", ctypes.c_double), ("t_done_s", ctypes.c_double),
-                ("group_blocks", ctypes.c_int32), ("t_group_wait_ms", ctypes.c_float)]
+                ("group_blocks", ctypes.c_int32), ("t_group_wait_ms", ctypes.c_float), ("d_used", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -130,6 +130,12 @@ def load(path: str = LIB_PATH):
     L.lsq_serve_config.argtypes = [P, ctypes.c_size_t, f64, i32]
     L.lsq_set_qr_mode.argtypes = [P, i32]
     L.lsq_set_qr_mode.restype = i32
+    L.lsq_choose_d.argtypes = [P, i64, i64, f64, ctypes.POINTER(ctypes.c_int64)]
+    L.lsq_choose_d.restype = i32
+    L.lsq_d_from_model.argtypes = [i64, i64, f64, f64, f64]
+    L.lsq_d_from_model.restype = i64
+    L.lsq_lambert_w0.argtypes = [f64]
+    L.lsq_lambert_w0.restype = f64
     L.lsq_serve_stats_get.argtypes = [P, ctypes.POINTER(ServeStats)]
     for name in ("lsq_create", "lsq_destroy", "lsq_sketch_indices", "lsq_sketch", "lsq_precond", "lsq_lsqr",
                  "lsq_check", "lsq_solve", "lsq_submit", "lsq_poll", "lsq_serve_config", "lsq_serve_stats_get"):
@@ -194,6 +200,12 @@ class Context:
         if st not in allow:
             raise LsqError(st, self.lib.lsq_last_error(self.h).decode())
         return st
+
+    def lsq_choose_d(self, m, n, tol=1e-12):
+        """Embedding dimension minimising the modelled solve time on this GPU."""
+        d = ctypes.c_int64()
+        self._check(self.lib.lsq_choose_d(self.h, m, n, tol, ctypes.byref(d)))
+        return d.value
 
     def lsq_set_qr_mode(self, mode):
         self._check(self.lib.lsq_set_qr_mode(self.h, mode))
@@ -365,6 +377,16 @@ class Context:
         s = ServeStats()
         self._check(self.lib.lsq_serve_stats_get(self.h, ctypes.byref(s)))
         return s.as_dict()
+
+
+def lsq_lambert_w0(x):
+    """Principal branch of the Lambert W function (host code of the library)."""
+    return load().lsq_lambert_w0(float(x))
+
+
+def lsq_d_from_model(m, n, tol, t_iter_per_row, t_qr_per_d):
+    """The solve-time model's minimising embedding dimension (no clamping)."""
+    return load().lsq_d_from_model(m, n, tol, t_iter_per_row, t_qr_per_d)
 
 
 def lsq_check_noalloc(A, b, x, M=None, stream=None):

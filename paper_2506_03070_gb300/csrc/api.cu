@@ -206,6 +206,107 @@ lsq_status run_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int n, int64_t lda
   return LSQ_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Embedding dimension (Sec. 4.3 "Selecting the embedding dimension").  The
+// solve time is modelled as T(d) = T_qr(d) + (t(d) + 2) T_iter(m) with the
+// Sec. 4.3 rate estimate (n/d)^{t/2} <= tol, i.e. t(d) = 2 |ln tol| / ln(d/n)
+// iterations, a preconditioner cost linear in d (t_qr_per_d per sketch row)
+// and an iteration cost linear in m (t_iter_per_row).  The constants are this
+// GPU's, measured by calibrate_d on synthetic data of the problem's width.
+// ---------------------------------------------------------------------------
+lsq_status calibrate_d(lsq_ctx* ctx, int64_t n64, lsq_ctx::DCalib* out) {
+  auto it = ctx->dcalib.find(n64);
+  if (it != ctx->dcalib.end()) {
+    *out = it->second;
+    return LSQ_OK;
+  }
+  const int n = (int)n64, npad = (int)((n64 + 31) / 32 * 32), ncol = n + 1;
+  int64_t mc = (int64_t)1 << 18;
+  const int64_t mmax = ((int64_t)1 << 30) / (8 * n64);
+  if (mc > mmax) mc = mmax;
+  if (mc < 8192) mc = 8192;
+  const int64_t d1 = std::max<int64_t>(n64 + 1, 2 * n64), d2 = std::max<int64_t>(8 * n64, d1 + n64);
+  const bool native = !lsqr_df_ok(nullptr, n64, n64);
+  const int grid = lsqr_grid(n, n % 2 == 0, native, ctx->sms);
+  if (grid < 1) return fail(ctx, LSQ_ERR_CUDA, "no launchable LSQR configuration");
+  auto carve = [&](Carver& cv, double** A, double** b, double** x, double** M, LsqrWork* lw, double** Y,
+                   PrecondBuffers* pb, double** R2, double** M2, double** x0) {
+    *A = cv.take<double>((size_t)mc * n);
+    *b = cv.take<double>((size_t)mc);
+    *x = cv.take<double>(npad);
+    *M = cv.take<double>((size_t)n * n);
+    *lw = carve_lsqr(cv, mc, n, npad, grid, !native);
+    *Y = cv.take<double>((size_t)d2 * ncol);
+    pb->W = cv.take<double>((size_t)d2 * ncol);
+    pb->rdiag = cv.take<double>(npad);
+    pb->R = cv.take<double>((size_t)n * n);
+    pb->Mt = cv.take<double>((size_t)n * n);
+    pb->blk = cv.take<char>(precond_blocked_bytes(d2, n));
+    *R2 = cv.take<double>((size_t)n * n);
+    *M2 = cv.take<double>((size_t)n * n);
+    *x0 = cv.take<double>(npad);
+  };
+  double *A, *b, *x, *M, *Y, *R2, *M2, *x0;
+  LsqrWork lw;
+  PrecondBuffers pb;
+  {
+    Carver probe{nullptr};
+    carve(probe, &A, &b, &x, &M, &lw, &Y, &pb, &R2, &M2, &x0);
+    lsq_status s = ensure_ws(ctx, probe.off);
+    if (s != LSQ_OK) return s;
+  }
+  Carver cv{ctx->ws};
+  carve(cv, &A, &b, &x, &M, &lw, &Y, &pb, &R2, &M2, &x0);
+  pb.bar = ctx->d_bar;
+  pb.status = ctx->d_status;
+  pb.blas = blas_handle(ctx);
+  pb.mode = ctx->qr_mode;
+  cudaStream_t st = nullptr;
+  CK(fill_hash(A, mc, n, n, 11, ctx->sms, st));
+  CK(fill_hash(b, mc, 1, 1, 12, ctx->sms, st));
+  CK(fill_identity(M, n, ctx->sms, st));
+  CK(transpose_square(M, n, lw.Mt, st));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto timed = [&](auto&& fn) -> float {
+    float ms = -1.f;
+    if (cudaEventRecord(e0, st) != cudaSuccess) return ms;
+    if (fn() != LSQ_OK) return ms;
+    if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return ms;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
+  auto lsqr_k = [&](int64_t k) {
+    lsq_status s = reset_small(ctx, st);
+    if (s != LSQ_OK) return s;
+    if (cudaMemsetAsync(x, 0, sizeof(double) * npad, st) != cudaSuccess) return LSQ_ERR_CUDA;
+    return run_lsqr(ctx, A, mc, n, n, b, M, lw.Mt, x, 0.0, k, 2, lw, grid, npad, native, st);
+  };
+  auto qr_d = [&](int64_t d) {
+    if (fill_hash(Y, d, ncol, ncol, 13, ctx->sms, st) != cudaSuccess) return LSQ_ERR_CUDA;
+    if (reset_small(ctx, st) != LSQ_OK) return LSQ_ERR_CUDA;
+    return precond<double>(Y, d, n, ncol, 1, R2, M2, x0, pb, ctx->sms, st) == cudaSuccess ? LSQ_OK
+                                                                                          : LSQ_ERR_CUDA;
+  };
+  timed([&] { return lsqr_k(1); });  // warm-up (module load, image)
+  const float t2 = timed([&] { return lsqr_k(2); });
+  const float t6 = timed([&] { return lsqr_k(6); });
+  timed([&] { return qr_d(d1); });
+  const float q1 = timed([&] { return qr_d(d1); });
+  const float q2 = timed([&] { return qr_d(d2); });
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (t2 < 0 || t6 < 0 || q1 < 0 || q2 < 0) return fail(ctx, LSQ_ERR_CUDA, "embedding-dimension calibration failed");
+  lsq_ctx::DCalib cal;
+  cal.t_iter_per_row = std::max(1e-15, (double)(t6 - t2) * 1e-3 / 4.0 / (double)mc);
+  // the QR's cost per extra sketch row, floored at its FP64 flop time (2 n^2 at ~1 TFLOP/s)
+  cal.t_qr_per_d = std::max(2.0 * (double)n * n * 1e-12, (double)(q2 - q1) * 1e-3 / (double)(d2 - d1));
+  ctx->dcalib[n64] = cal;
+  *out = cal;
+  return reset_small(ctx, st);
+}
+
 }  // namespace
 
 extern "C" {
@@ -286,6 +387,62 @@ const char* lsq_status_string(lsq_status s) {
 }
 
 size_t lsq_workspace_bytes(const lsq_ctx* ctx) { return ctx ? ctx->ws_size + kSmallBytes : 0; }
+
+double lsq_lambert_w0(double x) {
+  // principal branch on [-1/e, inf): Halley's iteration on f(w) = w e^w - x
+  const double em1 = 0.36787944117144233;  // 1/e
+  if (!(x >= -em1) || std::isinf(x)) return std::isinf(x) && x > 0 ? x : NAN;
+  if (x == 0.0) return 0.0;
+  double w;
+  if (x < -0.32) {
+    const double p = std::sqrt(2.0 * (1.0 + x / em1));  // series about the branch point
+    w = -1.0 + p - p * p / 3.0;
+  } else if (x < 3.0) {
+    w = std::log1p(x) * 0.75;
+  } else {
+    const double l = std::log(x);
+    w = l - std::log(l);
+  }
+  for (int k = 0; k < 64; ++k) {
+    const double ew = std::exp(w);
+    const double f = w * ew - x;
+    const double wp1 = w + 1.0;
+    if (wp1 == 0.0) break;
+    const double dw = f / (ew * wp1 - (w + 2.0) * f / (2.0 * wp1));
+    w -= dw;
+    if (std::fabs(dw) <= 4e-16 * (1.0 + std::fabs(w))) break;
+  }
+  return w;
+}
+
+int64_t lsq_d_from_model(int64_t m, int64_t n, double tol, double t_iter_per_row, double t_qr_per_d) {
+  // minimise T(d) = t_qr_per_d d + (2 |ln tol| / ln(d/n) + 2) t_iter_per_row m over d > n:
+  // with d = n e^u, dT/du = 0 gives u^2 e^u = C, C = 2 |ln tol| t_iter_per_row m / (t_qr_per_d n),
+  // so u/2 = W0(sqrt(C) / 2)
+  if (m < 1 || n < 1 || !(tol > 0.0 && tol < 1.0) || !(t_iter_per_row > 0.0) || !(t_qr_per_d > 0.0)) return 0;
+  const double C = 2.0 * std::fabs(std::log(tol)) * t_iter_per_row * (double)m / (t_qr_per_d * (double)n);
+  const double u = 2.0 * lsq_lambert_w0(std::sqrt(C) / 2.0);
+  const double d = (double)n * std::exp(u);
+  if (!(d < 2147483647.0)) return 2147483647LL;
+  return (int64_t)std::ceil(d);
+}
+
+lsq_status lsq_choose_d(lsq_ctx* ctx, int64_t m, int64_t n, double tol, int64_t* d) {
+  lsq_status s;
+  if ((s = check_ctx(ctx)) != LSQ_OK) return s;
+  if (!d || m < 1 || n < 1 || n > kLsqrMaxN || !(tol > 0.0 && tol < 1.0))
+    return fail(ctx, LSQ_ERR_ARG, "need d, m >= 1, 1 <= n <= 4096, 0 < tol < 1");
+  lsq_ctx::DCalib cal;
+  if ((s = calibrate_d(ctx, n, &cal)) != LSQ_OK) return s;
+  int64_t v = lsq_d_from_model(m, n, tol, cal.t_iter_per_row, cal.t_qr_per_d);
+  // keep the rate below 0.9 and the sketch within m rows and an eighth of the budget
+  const int64_t lo = std::max<int64_t>(n + 1, (n * 5 + 3) / 4);
+  int64_t hi = std::min<int64_t>(m, 2147483647LL);
+  hi = std::min<int64_t>(hi, (int64_t)(ctx->budget / 8 / (16 * (size_t)(n + 1))));
+  if (hi < lo) hi = lo;
+  *d = std::min(std::max(v, lo), hi);
+  return LSQ_OK;
+}
 
 lsq_status lsq_set_qr_mode(lsq_ctx* ctx, int32_t mode) {
   if (!ctx) return LSQ_ERR_ARG;
@@ -613,8 +770,26 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
 // cond(A) * u_fp32 * sqrt(m zeta / d) stays well below 1.  The mixed solve is
 // therefore capped at twice the iteration count the Sec. 4.3 rate estimate
 // predicts; if the cap is hit, the plain FP64 form solves the problem again.
-lsq_status lsq_solve(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts* o, double* x, lsq_info* info,
+static lsq_status lsq_solve_d(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts* o, double* x, lsq_info* info,
+                              void* stream);
+
+lsq_status lsq_solve(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts* o_in, double* x, lsq_info* info,
                      void* stream) {
+  lsq_opts oa;
+  const lsq_opts* o = o_in;
+  if (o_in && pr && o_in->d == 0) {  // automatic embedding dimension
+    oa = *o_in;
+    lsq_status s = lsq_choose_d(ctx, pr->m, pr->n, o_in->tol, &oa.d);
+    if (s != LSQ_OK) return s;
+    o = &oa;
+  }
+  lsq_status s0 = lsq_solve_d(ctx, pr, o, x, info, stream);
+  if (info && o) info->d_used = o->d;
+  return s0;
+}
+
+static lsq_status lsq_solve_d(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts* o, double* x, lsq_info* info,
+                              void* stream) {
   if (!o || o->prec != LSQ_PREC_MIXED || (o->flags & LSQ_FLAG_NO_FALLBACK) || !pr)
     return solve_once(ctx, pr, o, x, info, stream);
   lsq_opts om = *o;

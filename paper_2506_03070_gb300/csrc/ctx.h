@@ -1,5 +1,6 @@
 // ctx.h -- the library context behind the opaque lsq_ctx handle (internal).
 #pragma once
+#include <map>
 #include <string>
 
 #include "kernels.h"
@@ -31,6 +32,12 @@ struct lsq_ctx {
   void* blas = nullptr;
   bool blas_failed = false;
   int qr_mode = 0;  // LSQ_QR_AUTO / LSQ_QR_UNBLOCKED / LSQ_QR_BLOCKED
+  // embedding-dimension calibration per width n: seconds per row of one LSQR
+  // iteration, seconds per extra sketch row of the preconditioner
+  struct DCalib {
+    double t_iter_per_row = 0, t_qr_per_d = 0;
+  };
+  std::map<int64_t, DCalib> dcalib;
   // serving: persistent request loop, created by the first lsq_submit
   lsq::Server* server = nullptr;
   size_t serve_arena = 0;        // 0: the budget minus the synchronous workspace

@@ -106,6 +106,10 @@ int lsqr_gparts(int grid);
 int lsqr_grid(int n, bool vec, bool native, int sms);
 cudaError_t lsqr_run(const LsqrParams& p, bool vec, bool native, int grid, cudaStream_t st);
 
+// Calibration fills (calib.cu): hash values in [-1, 1) into rows x cols (ld), M = I.
+cudaError_t fill_hash(double* p, int64_t rows, int64_t cols, int64_t ld, uint64_t seed, int sms, cudaStream_t st);
+cudaError_t fill_identity(double* M, int n, int sms, cudaStream_t st);
+
 // Batched solves (batch.cu).
 struct BatchTuning;
 BatchTuning* batch_tuning_new();

@@ -336,6 +336,17 @@ def test_solve_tall_matches_oracle(ctx, orc):
     assert orc.backward_error_kw(A, b, x) <= 1e-10
 
 
+def test_solve_automatic_embedding_dimension(ctx, orc):
+    """d = 0: lsq_choose_d calibrates on this GPU and picks d from the model."""
+    A, b, xt = _problem(60000, 100, 1e8, 51)
+    d = ctx.lsq_choose_d(60000, 100, 1e-12)
+    assert 125 <= d <= 60000
+    x, info = ctx.lsq_solve(_dev(A), _dev(b), 0, seed=3, tol=1e-12)
+    assert info["status"] == 0 and info["d_used"] == d
+    assert orc.backward_error_kw(A, b, x.cpu().numpy()) <= 1e-10
+    assert np.linalg.norm(A @ (x.cpu().numpy() - xt)) <= 1e-10 * np.linalg.norm(b)
+
+
 def test_solve_consistent_system(ctx, orc):
     rng = np.random.default_rng(3)
     A = rng.standard_normal((4000, 30))
