@@ -16,6 +16,9 @@ slow, single-threaded FP64 C written from the paper (arXiv 2506.03070):
 * ``backward_error_kw``  -- Karlson-Waldén estimate of the optimal normwise
                            backward error (the acceptance metric).
 * ``solve``              -- Algorithm 1 end to end.
+* ``hbm``, ``hbm_params``  -- Algorithm 6 (gradient descent with heavy-ball
+                           momentum) with the step/momentum rule of App. C.2,
+                           plain numpy.
 
 Pins: every function is checked in ``tests/test_oracle_*.py`` against facts
 fixed by the paper or by mathematics (numpy's Philox, closed-form redraw
@@ -241,3 +244,56 @@ def default_maxit(n, d, tol):
 
 if __name__ == "__main__":  # pragma: no cover
     print(build(force="--force" in sys.argv))
+
+
+def hbm_params(eta_hat):
+    """App. C.2 ("Gradient methods"): step alpha = (1 - eta^2)^2 and momentum
+    beta = eta^2, rate sqrt(beta).  These are the optimal heavy-ball
+    parameters 4/(sqrt(L)+sqrt(mu))^2 and ((sqrt(L)-sqrt(mu))/(sqrt(L)+sqrt(mu)))^2
+    for singular values of AM in [1/(1+eta), 1/(1-eta)] -- what a sketch with
+    distortion eta leaves (||S A x|| within (1 +- eta) ||A x||, M from QR(SA)),
+    and a condition number (1 + eta)/(1 - eta)."""
+    eta2 = float(eta_hat) ** 2
+    return (1.0 - eta2) ** 2, eta2
+
+
+def hbm(A, b, M, x0, alpha, beta, tol, maxit, trace=False):
+    """Algorithm 6, gradient descent with heavy-ball momentum, in FP64:
+
+        x_{-1} = x_0
+        for t = 1, 2, ...:
+            g_t = M M^T A^T (b - A x_{t-1})      (= v - M M^T A^T A x_{t-1})
+            x_t = x_{t-1} + alpha g_t + beta (x_{t-1} - x_{t-2})
+
+    The algorithm leaves the convergence test open; here, before each update,
+    with r = b - A x_{t-1}: stop (1) when ||M^T A^T r|| <= tol ||r|| (the
+    normal-equation test for the preconditioned problem, ||AM|| ~ 1), (2) when
+    ||r|| <= tol ||b||, (3) after maxit updates."""
+    A, b, M, x = _f64(A), _f64(b), _f64(M), _f64(x0).copy()
+    x_prev = x.copy()
+    bn = float(np.linalg.norm(b))
+    iters, stop, rel = 0, 3, 0.0
+    tr = []
+    while True:
+        r = b - A @ x
+        q = M.T @ (A.T @ r)
+        rn, qn = float(np.linalg.norm(r)), float(np.linalg.norm(q))
+        rel = qn / rn if rn > 0 else 0.0
+        if qn <= tol * rn:
+            stop = 1
+            break
+        if rn <= tol * bn:
+            stop = 2
+            break
+        if iters >= maxit:
+            stop = 3
+            break
+        x_new = x + alpha * (M @ q) + beta * (x - x_prev)
+        x_prev, x = x, x_new
+        iters += 1
+        if trace:
+            tr.append(x.copy())
+    out = {"x": x, "iters": iters, "stop": stop, "normal_rel": rel}
+    if trace:
+        out["trace"] = np.array(tr).reshape(len(tr), -1)
+    return out
