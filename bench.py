@@ -699,6 +699,23 @@ def run_gpu(args):
                           "phases_ms": {"sketch": ia["t_sketch_ms"], "precond": ia["t_precond_ms"],
                                         "lsqr_and_check": ia["t_lsqr_ms"]},
                           "backward_error_kw": oracle.backward_error_kw(A, b, xa)}
+    if rank == 0 and world == 1 and not args.no_auto_d:
+        # the same problem solved with heavy-ball momentum (Algorithm 6) instead of LSQR
+        for _ in range(2):
+            xh, ih = ctx.lsq_solve(A, b, d, zeta=zeta, seed=seed, tol=tol, prec=prec, flags=flags | P.FLAG_HBM,
+                                   stream=stream, allow_noconv=True)
+        ms_h = []
+        for _ in range(max(1, min(args.steps, 3))):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            xh, ih = ctx.lsq_solve(A, b, d, zeta=zeta, seed=seed, tol=tol, prec=prec, flags=flags | P.FLAG_HBM,
+                                   stream=stream, allow_noconv=True)
+            e1.record(stream)
+            e1.synchronize()
+            ms_h.append(e0.elapsed_time(e1))
+        line["hbm"] = {"solves_per_s": 1e3 / statistics.mean(ms_h), "ms_per_solve": statistics.mean(ms_h),
+                       "iters": ih["iters"], "status": ih["status"], "stop": ih["stop"],
+                       "lsqr_phase_ms": ih["t_lsqr_ms"], "backward_error_kw": oracle.backward_error_kw(A, b, xh)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle as orc
         orc.build()

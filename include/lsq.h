@@ -93,6 +93,8 @@ typedef struct {
                                   m*n*8 bytes of workspace; each pass splits A itself) */
 #define LSQ_FLAG_NO_FALLBACK 16 /* mixed form: report LSQ_ERR_NOCONV instead of re-solving
                                    in FP64 when the FP32 preconditioner stalls LSQR */
+#define LSQ_FLAG_HBM 64         /* lsq_solve: heavy-ball momentum (Algorithm 6) instead of
+                                   LSQR, with eta_hat = sqrt(n/d) (see lsq_hbm) */
 
 typedef struct {
   int32_t status;          /* status of the solve (same as the return value) */
@@ -198,6 +200,22 @@ lsq_status lsq_set_qr_mode(lsq_ctx* ctx, int32_t mode);
 lsq_status lsq_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
                     const double* M, const double* x0, double tol, int64_t maxit, int32_t flags, double* x,
                     lsq_info* info, void* stream);
+
+/* Gradient descent with heavy-ball momentum (Algorithm 6, App. C.2) from x0
+ * with preconditioner M: x_t = x_{t-1} + alpha M M^T A^T (b - A x_{t-1})
+ * + beta (x_{t-1} - x_{t-2}), alpha = (1 - eta_hat^2)^2, beta = eta_hat^2 --
+ * the optimal parameters when the singular values of A M lie in
+ * [1/(1+eta_hat), 1/(1-eta_hat)], as a sketch with distortion eta_hat leaves
+ * them (0 <= eta_hat < 1; sqrt(n/d) estimates it).  One pass over A per
+ * iteration (r, A^T r and ||r|| fused, double-float arithmetic as in lsq_lsqr).
+ * Stops before an update when ||M^T A^T r|| <= tol ||b|| (which bounds
+ * ||A (x - x_*)|| by tol ||b|| / sigma_min(AM), the accuracy target of the
+ * paper's Sec. 4.3 experiments), ||r|| <= tol ||b||, or after maxit updates
+ * (LSQ_ERR_NOCONV).  Same limits and flags as lsq_lsqr; with a poor eta_hat it
+ * converges slowly or diverges, where LSQR needs no parameter. */
+lsq_status lsq_hbm(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
+                   const double* M, const double* x0, double tol, int64_t maxit, double eta_hat, int32_t flags,
+                   double* x, lsq_info* info, void* stream);
 
 /* Accuracy of a candidate solution: one pass over A computing r = b - A x,
  * A^T r, ||A||_F and the two backward-error bounds of lsq_info (M may be NULL;

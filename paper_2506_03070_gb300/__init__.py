@@ -29,11 +29,13 @@ LSQ_ERR_ARG, LSQ_ERR_NOCONV = -1, -7
 PREC_FP64, PREC_MIXED = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
 FLAG_TIMING, FLAG_NO_CHECK, FLAG_NATIVE_FP64, FLAG_NO_IMAGE, FLAG_NO_FALLBACK = 1, 2, 4, 8, 16
+FLAG_HBM = 64
 
 EXPORTS = ("lsq_create", "lsq_destroy", "lsq_last_error", "lsq_status_string", "lsq_workspace_bytes",
            "lsq_sketch_indices", "lsq_sketch", "lsq_precond", "lsq_lsqr", "lsq_check", "lsq_solve",
            "lsq_check_noalloc", "lsq_solve_batch", "lsq_submit", "lsq_poll", "lsq_serve_config",
-           "lsq_serve_stats_get", "lsq_set_qr_mode", "lsq_choose_d", "lsq_d_from_model", "lsq_lambert_w0")
+           "lsq_serve_stats_get", "lsq_set_qr_mode", "lsq_choose_d", "lsq_d_from_model", "lsq_lambert_w0",
+           "lsq_hbm")
 QR_AUTO, QR_UNBLOCKED, QR_BLOCKED = 0, 1, 2
 
 
@@ -119,6 +121,8 @@ def load(path: str = LIB_PATH):
     L.lsq_sketch.argtypes = [P, P, i64, i64, i64, P, i64, i32, u64, i32, P, i64, P]
     L.lsq_precond.argtypes = [P, P, i64, i64, i64, i32, i32, P, P, P, P]
     L.lsq_lsqr.argtypes = [P, P, i64, i64, i64, P, P, P, f64, i64, i32, P, P, P]
+    L.lsq_hbm.argtypes = [P, P, i64, i64, i64, P, P, P, f64, i64, f64, i32, P, P, P]
+    L.lsq_hbm.restype = i32
     L.lsq_check.argtypes = [P, P, i64, i64, i64, P, P, P, P, P]
     L.lsq_solve.argtypes = [P, ctypes.POINTER(Problem), ctypes.POINTER(Opts), P, ctypes.POINTER(Info), P]
     L.lsq_check_noalloc.argtypes = [P, i64, i64, i64, P, P, P, ctypes.POINTER(Info), P]
@@ -262,6 +266,18 @@ class Context:
         info = Info()
         st = self.lib.lsq_lsqr(self.h, _ptr(A), m, n, lda, _ptr(b), _ptr(M), _ptr(x0), tol, maxit, flags, _ptr(x),
                                ctypes.byref(info), _stream(stream))
+        self._check(st, allow=(LSQ_OK, LSQ_ERR_NOCONV))
+        return x, info.as_dict()
+
+    def lsq_hbm(self, A, b, M, x0, tol, maxit, eta_hat, flags=0, stream=None):
+        """Heavy-ball momentum (Algorithm 6) from x0; returns (x, info)."""
+        import torch
+        _dev_f64(A, "A")
+        m, n, lda = _rowmajor(A)
+        x = torch.empty((n,), dtype=torch.float64, device=A.device)
+        info = Info()
+        st = self.lib.lsq_hbm(self.h, _ptr(A), m, n, lda, _ptr(b), _ptr(M), _ptr(x0), tol, maxit, eta_hat, flags,
+                              _ptr(x), ctypes.byref(info), _stream(stream))
         self._check(st, allow=(LSQ_OK, LSQ_ERR_NOCONV))
         return x, info.as_dict()
 

@@ -170,7 +170,7 @@ void fill_info(lsq_info* info, const double* out, lsq_status st, int32_t rounds)
 // Launch the LSQR / check kernel (native: FP64-pipe pass; else double-float pass).
 lsq_status run_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int n, int64_t lda, const double* b, const double* M,
                     const double* Mt, double* x, double tol, int64_t maxit, int mode, const LsqrWork& w, int grid,
-                    int npad, bool native, cudaStream_t st) {
+                    int npad, bool native, cudaStream_t st, double hbm_alpha = 0.0, double hbm_beta = 0.0) {
   LsqrParams p;
   p.A = A;
   p.m = m;
@@ -198,6 +198,8 @@ lsq_status run_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int n, int64_t lda
   p.tol = tol;
   p.maxit = maxit;
   p.mode = mode;
+  p.hbm_alpha = hbm_alpha;
+  p.hbm_beta = hbm_beta;
   p.bar = ctx->d_bar;
   p.status = ctx->d_status;
   p.out = ctx->d_out;
@@ -578,6 +580,59 @@ lsq_status lsq_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t
   return s;
 }
 
+lsq_status lsq_hbm(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
+                   const double* M, const double* x0, double tol, int64_t maxit, double eta_hat, int32_t flags,
+                   double* x, lsq_info* info, void* stream) {
+  lsq_status s;
+  if ((s = check_ctx(ctx)) != LSQ_OK) return s;
+  if (m < 1 || n < 1 || lda < n) return fail(ctx, LSQ_ERR_ARG, "need m >= 1, n >= 1, lda >= n");
+  if (!A || !b || !M || !x0 || !x) return fail(ctx, LSQ_ERR_ARG, "null pointer");
+  if (!(eta_hat >= 0.0 && eta_hat < 1.0)) return fail(ctx, LSQ_ERR_ARG, "need 0 <= eta_hat < 1");
+  if (n > kLsqrMaxN) return fail(ctx, LSQ_ERR_UNSUPPORTED, "LSQR kernels built for n <= 4096");
+  if ((flags & LSQ_FLAG_NATIVE_FP64) && !lsqr_native_ok(n))
+    return fail(ctx, LSQ_ERR_UNSUPPORTED, "native FP64 LSQR kernel built for n <= 512");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int ni = (int)n, npad = (int)((n + 31) / 32 * 32);
+  bool native = (flags & LSQ_FLAG_NATIVE_FP64) || !lsqr_df_ok(A, n, lda);
+  int grid = lsqr_grid(ni, vec_ok(A, lda), native, ctx->sms);
+  if (grid < 1) return fail(ctx, LSQ_ERR_CUDA, "no launchable LSQR configuration");
+  bool image = !native && !(flags & LSQ_FLAG_NO_IMAGE);
+  Carver probe{nullptr};
+  carve_lsqr(probe, m, ni, npad, grid, image);
+  if (image && probe.off > ctx->budget) {
+    image = false;  // fall back to splitting A on the fly in every pass
+    probe = Carver{nullptr};
+    carve_lsqr(probe, m, ni, npad, grid, false);
+  }
+  if (!native && !image && !(vec_ok(A, lda) && n % 2 == 0) && lsqr_native_ok(n)) {
+    // without the image every pass streams A through the bulk-copy ring,
+    // which needs even n and lda and an aligned A (wide rows load directly)
+    native = true;
+    grid = lsqr_grid(ni, vec_ok(A, lda), native, ctx->sms);
+    probe = Carver{nullptr};
+    carve_lsqr(probe, m, ni, npad, grid, false);
+  }
+  if ((s = ensure_ws(ctx, probe.off)) != LSQ_OK) return s;
+  Carver cv{ctx->ws};
+  LsqrWork w = carve_lsqr(cv, m, ni, npad, grid, image);
+  if ((s = reset_small(ctx, st)) != LSQ_OK) return s;
+  CK(transpose_square(M, ni, w.Mt, st));
+  if (x != x0) CK(cudaMemcpyAsync(x, x0, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  if (maxit <= 0) maxit = 1000;
+  // App. C.2: alpha = (1 - eta^2)^2, beta = eta^2
+  const double e2 = eta_hat * eta_hat;
+  const int hmode = (flags & LSQ_FLAG_NO_CHECK) ? 4 : 3;
+  if ((s = run_lsqr(ctx, A, m, ni, lda, b, M, w.Mt, x, tol, maxit, hmode, w, grid, npad, native, st,
+                    (1.0 - e2) * (1.0 - e2), e2)) != LSQ_OK)
+    return s;
+  uint32_t bits = 0;
+  double out[kOutSlots];
+  if ((s = read_small(ctx, st, &bits, nullptr, out)) != LSQ_OK) return s;
+  s = status_from_bits(ctx, bits);
+  fill_info(info, out, s, 0);
+  return s;
+}
+
 lsq_status lsq_check(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
                      const double* x, const double* M, lsq_info* info, void* stream) {
   lsq_status s;
@@ -738,9 +793,13 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
     }
     return s;
   }
-  const int mode = (o->flags & LSQ_FLAG_NO_CHECK) ? 2 : 0;
-  if ((s = run_lsqr(ctx, A, m, ni, lda_dev, b, M, lw.Mt, xd, o->tol, maxit, mode, lw, grid, npad, native, st)) !=
-      LSQ_OK)
+  const bool hbm = (o->flags & LSQ_FLAG_HBM) != 0;
+  const bool nocheck = (o->flags & LSQ_FLAG_NO_CHECK) != 0;
+  const int mode = hbm ? (nocheck ? 4 : 3) : (nocheck ? 2 : 0);
+  // heavy-ball momentum: App. C.2 parameters with the distortion estimate sqrt(n/d)
+  const double e2 = (double)n / (double)d;
+  if ((s = run_lsqr(ctx, A, m, ni, lda_dev, b, M, lw.Mt, xd, o->tol, maxit, mode, lw, grid, npad, native, st,
+                    hbm ? (1.0 - e2) * (1.0 - e2) : 0.0, hbm ? e2 : 0.0)) != LSQ_OK)
     return s;
   if (timing) CK(cudaEventRecord(ev[4], st));
   if (host) CK(cudaMemcpyAsync(x, xd, sizeof(double) * n, cudaMemcpyDeviceToHost, st));

@@ -65,7 +65,9 @@ struct LsqrParams {
   double* part;      // grid * 4
   double tol;
   int64_t maxit;
-  int mode;          // 0 = LSQR then check, 1 = check only, 2 = LSQR only
+  int mode;          // 0 = LSQR then check, 1 = check only, 2 = LSQR only,
+                     // 3 = heavy-ball momentum then check, 4 = heavy-ball momentum only
+  double hbm_alpha, hbm_beta;  // step and momentum of modes 3 and 4
   int gidx, gcount;  // this block's index among the blocks sharing the problem (set in-kernel)
   GridBarrier* bar;
   uint32_t* status;

@@ -11,7 +11,8 @@
 //   barrier
 //
 // Every block derives the same scalars from the same partial sums in the same
-// order, so all blocks take the same branch at the stopping test.  After the
+// order, so all blocks take the same branch at the stopping test.  Modes 3
+// and 4 run heavy-ball momentum (Algorithm 6) over the same passes instead.  After the
 // loop the same pass structure computes r = b - A x, A^T r and ||A||_F (the
 // accuracy check) and the backward-error bounds.
 #include "lsqr_device.cuh"
@@ -27,7 +28,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_native(LsqrParams p) {
   NativePass<T, VEC> pass{s_g, s_scal};
   p.gidx = blockIdx.x;
   p.gcount = gridDim.x;
-  lsqr_body(p, pass, s_scal);
+  if (p.mode >= 3)
+    hbm_body(p, pass, s_scal);
+  else
+    lsqr_body(p, pass, s_scal);
 }
 
 template <int T>
@@ -44,7 +48,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_df(LsqrParams p) {
   DfPass<32, T> pass{s_ring, s_bars, s_scal, 0u, s_w};
   p.gidx = blockIdx.x;
   p.gcount = gridDim.x;
-  lsqr_body(p, pass, s_scal);
+  if (p.mode >= 3)
+    hbm_body(p, pass, s_scal);
+  else
+    lsqr_body(p, pass, s_scal);
 }
 
 // n > 512: PW warps per row (column panels of at most 512); ring of panel
@@ -63,7 +70,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_dfp(LsqrParams p) {
   DfPass<32, 8, false, PW> pass{s_ring, s_bars, s_scal, 0u, s_w};
   p.gidx = blockIdx.x;
   p.gcount = gridDim.x;
-  lsqr_body(p, pass, s_scal);
+  if (p.mode >= 3)
+    hbm_body(p, pass, s_scal);
+  else
+    lsqr_body(p, pass, s_scal);
 }
 
 size_t dfp_smem(int n) { return (size_t)kWarps * kNbuf * 512 * sizeof(double) + (size_t)((n + 1) / 2 * 2) * 8; }

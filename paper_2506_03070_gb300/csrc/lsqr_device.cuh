@@ -136,6 +136,10 @@ struct NativePass {
     p.gparts = p.gcount;
     pass_native<T, VEC, true, true>(p, p.x, -1.0, p.b, -1.0, nullptr, s_g, s_scal);
   }
+  __device__ void residual(LsqrParams& p, bool) {  // y = b - A x; sum y^2, b^2
+    p.gparts = p.gcount;
+    pass_native<T, VEC, false, true>(p, p.x, -1.0, p.b, -1.0, nullptr, s_g, s_scal);
+  }
 };
 
 // g[j] = sum over blocks of gpart[blk][j], block order.
@@ -709,6 +713,31 @@ struct DfPass {
     else
       run<false, false, true, false, false, false>(p, p.wv, 1.0, gamma);
   }
+  // y = b - A x with A^T y, sum y^2 and sum b^2 (heavy-ball momentum); the
+  // first call writes the float-pair image, later ones stream it.
+  __device__ void residual(LsqrParams& p, bool first) {
+    if (PW > 1) {
+      p.gparts = p.gcount * (kWarps / PW);
+      if (p.asplit && first) {
+        run_panel<true, true, false, false, true, false>(p, p.x, -1.0, -1.0);
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+      } else if (p.asplit) {
+        run_panel<true, true, false, true, false, false>(p, p.x, -1.0, -1.0);
+      } else {
+        run_panel<true, true, false, false, false, false>(p, p.x, -1.0, -1.0);
+      }
+      return;
+    }
+    p.gparts = p.gcount * kWarps;
+    if (p.asplit && first) {
+      run<true, true, false, false, true, false>(p, p.x, -1.0, -1.0);
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+    } else if (p.asplit) {
+      run<true, true, false, true, false, false>(p, p.x, -1.0, -1.0);
+    } else {
+      run<true, true, false, false, false, false>(p, p.x, -1.0, -1.0);
+    }
+  }
   // Accuracy pass: native FP64 on the original A (single-problem kernel), or
   // in pair arithmetic on the image (batched problems, p.check_df).
   __device__ void check(LsqrParams& p) {
@@ -740,8 +769,11 @@ struct DfPass {
 // Algorithm 2 around a pass policy (see the file header for the order).
 // --------------------------------------------------------------------------
 template <class Pass>
+__device__ void finish_body(LsqrParams& p, Pass& pass, double* s_scal, int64_t iters, int stop, double normal_rel,
+                            double bnorm, double anorm_est, bool skip_check);
+
+template <class Pass>
 __device__ void lsqr_body(LsqrParams& p, Pass& pass, double* s_scal) {
-  uint32_t* status = p.status;
   double alpha = 0.0, beta = 0.0, rhobar = 0.0, phibar = 0.0, anorm2 = 0.0, bnorm = 0.0, normal_rel = 0.0;
   int64_t iters = 0;
   int stop = 0;
@@ -802,13 +834,23 @@ __device__ void lsqr_body(LsqrParams& p, Pass& pass, double* s_scal) {
     }
   }
 
-  if (p.mode == 2) {
+  finish_body(p, pass, s_scal, iters, stop, normal_rel, bnorm, sqrt(anorm2), p.mode == 2);
+}
+
+// Outputs of an iteration (LSQR or heavy-ball momentum), then -- unless
+// skip_check -- the accuracy pass: y = b - A x, g = A^T y, ||A||_F and the
+// backward-error bounds.
+template <class Pass>
+__device__ void finish_body(LsqrParams& p, Pass& pass, double* s_scal, int64_t iters, int stop, double normal_rel,
+                            double bnorm, double anorm_est, bool skip_check) {
+  uint32_t* status = p.status;
+  if (skip_check) {
     if (p.gidx == 0 && threadIdx.x == 0) {
       p.out[OUT_ITERS] = (double)iters;
       p.out[OUT_STOP] = (double)stop;
       p.out[OUT_NORMAL_REL] = normal_rel;
       p.out[OUT_BNORM] = bnorm;
-      p.out[OUT_ANORM_EST] = sqrt(anorm2);
+      p.out[OUT_ANORM_EST] = anorm_est;
       if (stop == 3) atomicOr(status, DS_NOCONV);
     }
     return;
@@ -846,10 +888,74 @@ __device__ void lsqr_body(LsqrParams& p, Pass& pass, double* s_scal) {
       p.out[OUT_ETA_NE] = (fro > 0.0 && rnorm > 0.0) ? arn / (fro * rnorm) : 0.0;
       p.out[OUT_ETA_PRE] = (fro > 0.0 && xn > 0.0) ? marn / (fro * xn) : 0.0;
       p.out[OUT_MARNORM] = marn;
-      p.out[OUT_ANORM_EST] = sqrt(anorm2);
+      p.out[OUT_ANORM_EST] = anorm_est;
       if (stop == 3) atomicOr(status, DS_NOCONV);
     }
   }
+}
+
+// x_t = x_{t-1} + alpha M q + beta (x_{t-1} - x_{t-2}) with q = vhat = M^T A^T r
+// (one warp per row i of the upper triangular M); w holds x_{t-2}.
+__device__ void hbm_update(const LsqrParams& p) {
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int gw = p.gidx * kWarps + wib, nw = p.gcount * kWarps;
+  for (int i = gw; i < p.n; i += nw) {
+    const double* mi = p.M + (int64_t)i * p.n;
+    double s = 0.0;
+    for (int k = i + lane; k < p.n; k += 32) s = fma(mi[k], p.vhat[k], s);
+    s = warp_allreduce_sum(s);
+    if (lane == 0) {
+      const double xi = p.x[i];
+      p.x[i] = fma(p.hbm_alpha, s, fma(p.hbm_beta, xi - p.w[i], xi));
+      p.w[i] = xi;
+    }
+  }
+}
+
+// Algorithm 6 (gradient descent with heavy-ball momentum) from x0:
+//   x_{-1} = x_0;  g_t = M M^T A^T (b - A x_{t-1});
+//   x_t = x_{t-1} + alpha g_t + beta (x_{t-1} - x_{t-2}).
+// Per iteration one pass over A forms r = b - A x_{t-1} and, with each row on
+// chip, A^T r and ||r||^2; then q = M^T A^T r and the update.  Test before each
+// update: ||q|| <= tol ||b|| (bounds ||A (x - x_*)|| by tol ||b|| / sigma_min(AM),
+// the Sec. 4.3 accuracy target), ||r|| <= tol ||b||, or maxit updates.
+template <class Pass>
+__device__ void hbm_body(LsqrParams& p, Pass& pass, double* s_scal) {
+  for (int i = p.gidx * kThreads + threadIdx.x; i < p.n; i += p.gcount * kThreads) p.w[i] = p.x[i];
+  if (!group_sync(p)) return;
+  int64_t iters = 0;
+  int stop = 0;
+  double rel = 0.0, bn = 0.0;
+  bool first = true;
+  for (;;) {
+    pass.residual(p, first);
+    first = false;
+    if (!group_sync(p)) return;
+    reduce_g(p);
+    if (!group_sync(p)) return;
+    mt_apply(p, 1.0, 0.0, 2, s_scal);  // vhat = M^T g; ||vhat||^2 -> part slot 2
+    if (!group_sync(p)) return;
+    const double rn = sqrt(sum_part(p, 0)), qn = sqrt(sum_part(p, 2));
+    bn = sqrt(sum_part(p, 1));
+    rel = bn > 0.0 ? qn / bn : 0.0;
+    if (qn <= p.tol * bn) {
+      stop = 1;
+      break;
+    }
+    if (rn <= p.tol * bn) {
+      stop = 2;
+      break;
+    }
+    if (iters >= p.maxit) {
+      stop = 3;
+      break;
+    }
+    hbm_update(p);
+    ++iters;
+    if (!group_sync(p)) return;
+  }
+  if (!group_sync(p)) return;
+  finish_body(p, pass, s_scal, iters, stop, rel, bn, 0.0, p.mode == 4);
 }
 
 }  // namespace

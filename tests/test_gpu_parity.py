@@ -347,6 +347,38 @@ def test_solve_automatic_embedding_dimension(ctx, orc):
     assert np.linalg.norm(A @ (x.cpu().numpy() - xt)) <= 1e-10 * np.linalg.norm(b)
 
 
+@pytest.mark.parametrize("m,n,d", [(20000, 100, 400), (12000, 600, 2400)])
+def test_hbm_matches_oracle(ctx, orc, m, n, d):
+    """Heavy-ball momentum (Algorithm 6): the iterates after k updates follow
+    the oracle's, and the converged solve takes the oracle's iteration count."""
+    A, b, xt = _problem(m, n, 1e6, m + n + 1)
+    Yo = orc.sketch_apply(A, b, d, 8, 3)
+    Ro = np.linalg.qr(Yo, mode="r")
+    Mo = orc.tri_inverse(Ro[:n, :n])
+    x0 = Mo @ Ro[:n, n]
+    eta = np.sqrt(n / d)
+    a, beta = orc.hbm_params(eta)
+    bn = np.linalg.norm(b)
+    for k in (3, 12):
+        ref = orc.hbm(A, b, Mo, x0, a, beta, 1e-30, k)
+        x, info = ctx.lsq_hbm(_dev(A), _dev(b), _dev(Mo), _dev(x0), 1e-30, k, eta)
+        assert info["iters"] == k and info["status"] == -7 and info["stop"] == 3
+        assert np.linalg.norm(A @ (x.cpu().numpy() - ref["x"])) <= 1e-10 * bn
+    ref = orc.hbm(A, b, Mo, x0, a, beta, 1e-12, 500)
+    x, info = ctx.lsq_hbm(_dev(A), _dev(b), _dev(Mo), _dev(x0), 1e-12, 500, eta)
+    assert ref["stop"] in (1, 2) and info["status"] == 0
+    assert abs(info["iters"] - ref["iters"]) <= 2, (info["iters"], ref["iters"])
+    assert orc.backward_error_kw(A, b, x.cpu().numpy()) <= 1e-10
+
+
+def test_solve_with_hbm_flag(ctx, orc):
+    import paper_2506_03070_gb300 as P
+    A, b, xt = _problem(30000, 128, 1e8, 62)
+    x, info = ctx.lsq_solve(_dev(A), _dev(b), 512, seed=4, tol=1e-12, flags=P.FLAG_HBM)
+    assert info["status"] == 0
+    assert orc.backward_error_kw(A, b, x.cpu().numpy()) <= 1e-10
+
+
 def test_solve_consistent_system(ctx, orc):
     rng = np.random.default_rng(3)
     A = rng.standard_normal((4000, 30))
