@@ -564,6 +564,59 @@ def run_mixed(args):
     ctx.close()
 
 
+def run_sparse(args):
+    """The paper's 5e5_500_sparse workload (Sec. 4.1): 500,000 x 500, entries
+    nonzero with probability 1/100, random signs; d = 2000, zeta = 8."""
+    import torch
+
+    import paper_2506_03070_gb300 as P
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2506_03070_gb300 import synth
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    m, n, d = args.m or 500_000, args.n or 500, 2000
+    p = synth.sparse_sign_problem(m, n, 0.01, seed=55, device=f"cuda:{local}")
+    ctx = P.Context(local)
+    stream = torch.cuda.current_stream()
+    nnz = p["values"].numel()
+
+    def solve():
+        return ctx.lsq_solve_csr(p["row_ptr"], p["col_idx"], p["values"], p["b"], n, d, seed=8, tol=1e-12,
+                                 flags=P.FLAG_TIMING, stream=stream)
+
+    for _ in range(args.warmup):
+        x, info = solve()
+    ms = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x, info = solve()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    import oracle
+    A = synth.csr_to_dense(p)
+    bwd = oracle.backward_error_kw(A, p["b"], x)
+    del A
+    t = statistics.mean(ms)
+    # bytes per pass: values (8) + column indices (4) per nonzero, row offsets and u (8 + 16 per row)
+    pass_bytes = 12.0 * nnz + 24.0 * m
+    it = info["iters"]
+    lsqr_gbs = pass_bytes * (it + 2) / (info["t_lsqr_ms"] / 1e3) / 1e9
+    peaks, peak_src = _peaks()
+    line = {"metric": "ls_solves_per_sec", "value": 1e3 / t, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"sparse_sign_{m}x{n}_p0.01_d{d}_zeta8_tol1e-12", "nnz": nnz},
+            "phases_ms": {"sketch": info["t_sketch_ms"], "precond": info["t_precond_ms"],
+                          "lsqr_and_check": info["t_lsqr_ms"]},
+            "lsqr_iters": it, "lsqr_pass_gbs": lsqr_gbs, "hbm_peak_gbs": float(peaks["hbm_gbs"]),
+            "accuracy": {"backward_error_kw": bwd}}
+    print(json.dumps(line))
+    ctx.close()
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -763,6 +816,7 @@ def main():
     ap.add_argument("--no-check", action="store_true", help="skip the accuracy pass (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-auto-d", action="store_true", help="skip the extra solve with the chosen embedding dimension")
+    ap.add_argument("--sparse", action="store_true", help="the paper's 5e5_500_sparse workload (CSR path)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -772,6 +826,8 @@ def main():
         run_batch(args)
     elif args.config == 4:
         run_serve(args)
+    elif args.sparse:
+        run_sparse(args)
     else:
         run_gpu(args)
 

@@ -255,6 +255,27 @@ lsq_status lsq_check_noalloc(const double* A, int64_t m, int64_t n, int64_t lda,
 lsq_status lsq_solve(lsq_ctx* ctx, const lsq_problem* problem, const lsq_opts* opts, double* x, lsq_info* info,
                      void* stream);
 
+/* ---- Sparse A (CSR) --------------------------------------------------------
+ * Algorithm 1 for A given by its nonzeros (the paper's sparse workloads): the
+ * sketch touches only the nonzeros (O(zeta nnz); the sketch columns are the
+ * dense path's, so S is the same), Householder QR and M = R^{-1} as for dense
+ * A, then LSQR (or heavy-ball momentum with LSQ_FLAG_HBM) whose passes run over
+ * the nonzeros in FP64.  row_ptr: m+1 int64 offsets (row_ptr[0] = 0,
+ * nondecreasing, row_ptr[m] = nnz); col_idx: nnz int32 in [0, n) (any order
+ * within a row, duplicates add); values: nnz doubles; b: m doubles; x: n
+ * doubles.  All device memory.  opts as for lsq_solve (FP64 form only; d = 0
+ * chooses d with the dense model); lsq_info as for lsq_solve. */
+typedef struct {
+  const int64_t* row_ptr;
+  const int32_t* col_idx;
+  const double* values;
+  const double* b;
+  int64_t m, n, nnz;
+} lsq_csr_problem;
+
+lsq_status lsq_solve_csr(lsq_ctx* ctx, const lsq_csr_problem* problem, const lsq_opts* opts, double* x, lsq_info* info,
+                         void* stream);
+
 /* ---- Batched solves -------------------------------------------------------
  * Many independent problems in one persistent launch: every block takes whole
  * problems from a device work counter (largest m*n first) and runs all of

@@ -35,7 +35,7 @@ EXPORTS = ("lsq_create", "lsq_destroy", "lsq_last_error", "lsq_status_string", "
            "lsq_sketch_indices", "lsq_sketch", "lsq_precond", "lsq_lsqr", "lsq_check", "lsq_solve",
            "lsq_check_noalloc", "lsq_solve_batch", "lsq_submit", "lsq_poll", "lsq_serve_config",
            "lsq_serve_stats_get", "lsq_set_qr_mode", "lsq_choose_d", "lsq_d_from_model", "lsq_lambert_w0",
-           "lsq_hbm")
+           "lsq_hbm", "lsq_solve_csr")
 QR_AUTO, QR_UNBLOCKED, QR_BLOCKED = 0, 1, 2
 
 
@@ -69,6 +69,11 @@ class Info(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class CsrProblem(ctypes.Structure):
+    _fields_ = [("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("values", ctypes.c_void_p),
+                ("b", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64)]
 
 
 class BatchItem(ctypes.Structure):
@@ -122,6 +127,8 @@ def load(path: str = LIB_PATH):
     L.lsq_precond.argtypes = [P, P, i64, i64, i64, i32, i32, P, P, P, P]
     L.lsq_lsqr.argtypes = [P, P, i64, i64, i64, P, P, P, f64, i64, i32, P, P, P]
     L.lsq_hbm.argtypes = [P, P, i64, i64, i64, P, P, P, f64, i64, f64, i32, P, P, P]
+    L.lsq_solve_csr.argtypes = [P, ctypes.POINTER(CsrProblem), ctypes.POINTER(Opts), P, ctypes.POINTER(Info), P]
+    L.lsq_solve_csr.restype = i32
     L.lsq_hbm.restype = i32
     L.lsq_check.argtypes = [P, P, i64, i64, i64, P, P, P, P, P]
     L.lsq_solve.argtypes = [P, ctypes.POINTER(Problem), ctypes.POINTER(Opts), P, ctypes.POINTER(Info), P]
@@ -279,6 +286,24 @@ class Context:
         st = self.lib.lsq_hbm(self.h, _ptr(A), m, n, lda, _ptr(b), _ptr(M), _ptr(x0), tol, maxit, eta_hat, flags,
                               _ptr(x), ctypes.byref(info), _stream(stream))
         self._check(st, allow=(LSQ_OK, LSQ_ERR_NOCONV))
+        return x, info.as_dict()
+
+    def lsq_solve_csr(self, row_ptr, col_idx, values, b, n, d, zeta=8, seed=0, tol=1e-12, maxit=0, flags=0,
+                      stream=None, allow_noconv=False):
+        """Algorithm 1 for a sparse A in CSR form (CUDA tensors: int64 row_ptr,
+        int32 col_idx, float64 values, float64 b).  Returns (x, info)."""
+        import torch
+        if row_ptr.dtype != torch.int64 or col_idx.dtype != torch.int32 or values.dtype != torch.float64:
+            raise TypeError("row_ptr int64, col_idx int32, values float64")
+        _dev_f64(b, "b")
+        m = row_ptr.numel() - 1
+        x = torch.empty((n,), dtype=torch.float64, device=b.device)
+        pr = CsrProblem(_ptr(row_ptr), _ptr(col_idx), _ptr(values), _ptr(b), m, n, values.numel())
+        op = Opts(d, zeta, PREC_FP64, seed, tol, maxit, flags, 0)
+        info = Info()
+        st = self.lib.lsq_solve_csr(self.h, ctypes.byref(pr), ctypes.byref(op), _ptr(x), ctypes.byref(info),
+                                    _stream(stream))
+        self._check(st, allow=(LSQ_OK, LSQ_ERR_NOCONV) if allow_noconv else (LSQ_OK,))
         return x, info.as_dict()
 
     def lsq_check(self, A, b, x, M=None, stream=None):

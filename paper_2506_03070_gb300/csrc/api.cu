@@ -864,6 +864,127 @@ static lsq_status lsq_solve_d(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opt
   return s;
 }
 
+lsq_status lsq_solve_csr(lsq_ctx* ctx, const lsq_csr_problem* pr, const lsq_opts* o_in, double* x, lsq_info* info,
+                         void* stream) {
+  lsq_status s;
+  if ((s = check_ctx(ctx)) != LSQ_OK) return s;
+  if (!pr || !o_in || !x) return fail(ctx, LSQ_ERR_ARG, "null problem, options or x");
+  const int64_t m = pr->m, n = pr->n;
+  if (m < 1 || n < 1 || n > kLsqrMaxN || pr->nnz < 0 || !pr->row_ptr || !pr->b || (pr->nnz > 0 && (!pr->col_idx ||
+      !pr->values)))
+    return fail(ctx, LSQ_ERR_ARG, "need m >= 1, 1 <= n <= 4096, nnz >= 0 and the CSR arrays");
+  if (o_in->prec != LSQ_PREC_FP64) return fail(ctx, LSQ_ERR_UNSUPPORTED, "sparse A: FP64 form only");
+  lsq_opts o = *o_in;
+  if (o.d == 0 && (s = lsq_choose_d(ctx, m, n, o.tol, &o.d)) != LSQ_OK) return s;
+  const int64_t d = o.d;
+  if ((s = check_sketch_args(ctx, d, o.zeta)) != LSQ_OK) return s;
+  if (d < n + 1) return fail(ctx, LSQ_ERR_ARG, "need d >= n + 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool timing = (o.flags & LSQ_FLAG_TIMING) != 0;
+  const int ni = (int)n, npad = (int)((n + 31) / 32 * 32);
+  const int64_t ncol = n + 1;
+  const int grid = lsqr_csr_grid(ctx->sms);
+  if (grid < 1) return fail(ctx, LSQ_ERR_CUDA, "no launchable CSR LSQR configuration");
+  const int64_t maxit = o.maxit > 0 ? o.maxit : default_maxit(n, d, o.tol);
+  auto carve = [&](Carver& cv, double** Y, PrecondBuffers* pb, double** R, double** M, LsqrWork* lw) {
+    *Y = cv.take<double>((size_t)d * ncol);
+    pb->W = cv.take<double>((size_t)ncol * d);
+    pb->rdiag = cv.take<double>(npad);
+    pb->blk = cv.take<char>(precond_blocked_bytes(d, n));
+    pb->R = nullptr;
+    *R = cv.take<double>((size_t)n * n);
+    *M = cv.take<double>((size_t)n * n);
+    *lw = carve_lsqr(cv, m, ni, npad, grid, false);
+    pb->Mt = lw->Mt;
+  };
+  double *Y, *R, *M;
+  PrecondBuffers pb;
+  LsqrWork lw;
+  {
+    Carver probe{nullptr};
+    carve(probe, &Y, &pb, &R, &M, &lw);
+    if ((s = ensure_ws(ctx, probe.off)) != LSQ_OK) return s;
+  }
+  Carver cv{ctx->ws};
+  carve(cv, &Y, &pb, &R, &M, &lw);
+  pb.bar = ctx->d_bar;
+  pb.status = ctx->d_status;
+  pb.blas = blas_handle(ctx);
+  pb.mode = ctx->qr_mode;
+  cudaEvent_t ev[4] = {};
+  if (timing)
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+  if (timing) CK(cudaEventRecord(ev[0], st));
+  if ((s = reset_small(ctx, st)) != LSQ_OK) return s;
+  CK(cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)d * ncol, st));
+  CK(sketch_csr(pr->row_ptr, pr->col_idx, pr->values, pr->b, m, n, d, o.zeta, o.seed, Y, ncol, ctx->d_status,
+                ctx->d_max_rounds, ctx->sms, st));
+  if (timing) CK(cudaEventRecord(ev[1], st));
+  CK(precond<double>(Y, d, n, ncol, 1, R, M, x, pb, ctx->sms, st));
+  if (timing) CK(cudaEventRecord(ev[2], st));
+  uint32_t bits = 0;
+  int32_t rounds = 0;
+  double out[kOutSlots] = {0};
+  if ((s = read_small(ctx, st, &bits, &rounds, nullptr)) != LSQ_OK) return s;
+  if (bits) {
+    s = status_from_bits(ctx, bits);
+    fill_info(info, out, s, rounds);
+    return s;
+  }
+  LsqrParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.m = m;
+  p.n = ni;
+  p.npad = npad;
+  p.lda = n;
+  p.b = pr->b;
+  p.ldi = (n + 1) / 2 * 2;
+  p.ring_k = 1;
+  p.M = M;
+  p.Mt = lw.Mt;
+  p.x = x;
+  p.u = lw.u;
+  p.v = lw.v;
+  p.vhat = lw.vhat;
+  p.w = lw.w;
+  p.wv = lw.wv;
+  p.g = lw.g;
+  p.gpart = lw.gpart;
+  p.part = lw.part;
+  p.tol = o.tol;
+  p.maxit = maxit;
+  const bool hbm = (o.flags & LSQ_FLAG_HBM) != 0, nocheck = (o.flags & LSQ_FLAG_NO_CHECK) != 0;
+  p.mode = hbm ? (nocheck ? 4 : 3) : (nocheck ? 2 : 0);
+  const double e2 = (double)n / (double)d;
+  p.hbm_alpha = hbm ? (1.0 - e2) * (1.0 - e2) : 0.0;
+  p.hbm_beta = hbm ? e2 : 0.0;
+  p.bar = ctx->d_bar;
+  p.status = ctx->d_status;
+  p.out = ctx->d_out;
+  CK(transpose_square(M, ni, lw.Mt, st));
+  CK(cudaMemsetAsync(ctx->d_bar, 0, sizeof(GridBarrier), st));
+  CK(lsqr_csr_run(p, pr->row_ptr, pr->col_idx, pr->values, grid, st));
+  if (timing) CK(cudaEventRecord(ev[3], st));
+  if ((s = read_small(ctx, st, &bits, nullptr, out)) != LSQ_OK) return s;
+  s = status_from_bits(ctx, bits);
+  fill_info(info, out, s, rounds);
+  if (info) {
+    info->d_used = d;
+    if (timing) {
+      float t;
+      cudaEventElapsedTime(&t, ev[0], ev[1]);
+      info->t_sketch_ms = t;
+      cudaEventElapsedTime(&t, ev[1], ev[2]);
+      info->t_precond_ms = t;
+      cudaEventElapsedTime(&t, ev[2], ev[3]);
+      info->t_lsqr_ms = t;
+    }
+  }
+  if (timing)
+    for (auto& e : ev) cudaEventDestroy(e);
+  return s;
+}
+
 lsq_status lsq_solve_batch(lsq_ctx* ctx, const lsq_batch_item* items, int64_t count, double tol, int64_t maxit,
                            int32_t flags, lsq_batch_result* results, void* stream) {
   lsq_status s;

@@ -136,3 +136,35 @@ def large_problem(m, n, cond, *, seed, device="cuda", chunk_rows=1 << 18, dtype=
     b.add_(g, alpha=1e-6 / float(torch.linalg.vector_norm(g)))
     del g
     return {"A": A, "b": b, "x_true": x_true, "cond": cond}
+
+
+def sparse_sign_problem(m, n, density, *, seed, device="cpu"):
+    """The paper's 5e5_500_sparse recipe (Sec. 4.1): each entry independently
+    nonzero with probability ``density``, nonzero values random signs; plus one
+    nonzero per column at a seeded row so no column is empty.  CSR arrays
+    (int64 row_ptr, int32 col_idx, float64 values) and b = A x_true +
+    1e-6 g / ||g||, x_true ~ N(0, 1)."""
+    dev = torch.device(device)
+    gen = _gen(dev, seed)
+    mask = torch.rand(m, n, generator=gen, device=dev) < density
+    rows = torch.randint(0, m, (n,), generator=gen, device=dev)
+    mask[rows, torch.arange(n, device=dev)] = True
+    r, cidx = torch.nonzero(mask, as_tuple=True)  # row-major order
+    del mask
+    vals = torch.where(torch.rand(r.numel(), generator=gen, device=dev) < 0.5, -1.0, 1.0).to(torch.float64)
+    counts = torch.bincount(r, minlength=m)
+    row_ptr = torch.zeros(m + 1, dtype=torch.int64, device=dev)
+    row_ptr[1:] = torch.cumsum(counts, 0)
+    x_true = torch.randn(n, generator=gen, device=dev, dtype=torch.float64)
+    Ax = torch.zeros(m, dtype=torch.float64, device=dev)
+    Ax.index_add_(0, r, vals * x_true[cidx])
+    g = torch.randn(m, generator=gen, device=dev, dtype=torch.float64)
+    b = Ax + 1e-6 * g / torch.linalg.vector_norm(g)
+    return {"row_ptr": row_ptr, "col_idx": cidx.to(torch.int32), "values": vals, "b": b, "x_true": x_true,
+            "m": m, "n": n, "rows": r}
+
+
+def csr_to_dense(p):
+    A = torch.zeros(p["m"], p["n"], dtype=torch.float64, device=p["values"].device)
+    A[p["rows"], p["col_idx"].long()] = p["values"]
+    return A

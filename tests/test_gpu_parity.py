@@ -379,6 +379,33 @@ def test_solve_with_hbm_flag(ctx, orc):
     assert orc.backward_error_kw(A, b, x.cpu().numpy()) <= 1e-10
 
 
+@pytest.mark.parametrize("m,n,density,d", [(20000, 50, 0.02, 200), (30000, 120, 0.05, 480), (8000, 600, 0.1, 2400)])
+def test_solve_csr_matches_oracle_and_dense(ctx, orc, m, n, density, d):
+    """Sparse A in CSR form (the paper's random-sign sparse recipe; (20000, 50,
+    0.02) leaves most rows empty): the same sketch columns as the dense path, so
+    the solve follows the oracle run on the dense form of A."""
+    from paper_2506_03070_gb300 import synth
+    p = synth.sparse_sign_problem(m, n, density, seed=m + n, device="cuda")
+    A = synth.csr_to_dense(p).cpu().numpy()
+    b = p["b"].cpu().numpy()
+    x, info = ctx.lsq_solve_csr(p["row_ptr"], p["col_idx"], p["values"], p["b"], n, d, seed=6, tol=1e-12)
+    x = x.cpu().numpy()
+    ref = orc.solve(A, b, d, 8, 6, 1e-12, orc.default_maxit(n, d, 1e-12))
+    bn = np.linalg.norm(b)
+    assert info["status"] == 0 and info["d_used"] == d
+    assert abs(info["iters"] - ref["iters"]) <= 2, (info["iters"], ref["iters"])
+    assert np.linalg.norm(A @ (x - ref["x"])) <= 1e-10 * bn
+    assert orc.backward_error_kw(A, b, x) <= 1e-10
+    xd, _ = ctx.lsq_solve(_dev(A), _dev(b), d, seed=6, tol=1e-12)
+    assert np.linalg.norm(A @ (x - xd.cpu().numpy())) <= 1e-10 * bn
+    # heavy-ball momentum and automatic d on the same sparse problem
+    import paper_2506_03070_gb300 as P
+    xh, ih = ctx.lsq_solve_csr(p["row_ptr"], p["col_idx"], p["values"], p["b"], n, 0, seed=6, tol=1e-12,
+                               flags=P.FLAG_HBM)
+    assert ih["status"] == 0 and ih["d_used"] > n
+    assert orc.backward_error_kw(A, b, xh.cpu().numpy()) <= 1e-10
+
+
 def test_solve_consistent_system(ctx, orc):
     rng = np.random.default_rng(3)
     A = rng.standard_normal((4000, 30))
