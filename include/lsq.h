@@ -264,7 +264,9 @@ lsq_status lsq_solve(lsq_ctx* ctx, const lsq_problem* problem, const lsq_opts* o
  * nondecreasing, row_ptr[m] = nnz); col_idx: nnz int32 in [0, n) (any order
  * within a row, duplicates add); values: nnz doubles; b: m doubles; x: n
  * doubles.  All device memory.  opts as for lsq_solve (FP64 form only; d = 0
- * chooses d with the dense model); lsq_info as for lsq_solve. */
+ * chooses d with the dense model); lsq_info as for lsq_solve.  The structure
+ * is checked on the device before any kernel indexes by it (one extra stream
+ * synchronisation): malformed offsets or indices give LSQ_ERR_ARG. */
 typedef struct {
   const int64_t* row_ptr;
   const int32_t* col_idx;

@@ -35,6 +35,22 @@ lsq_status cuda_fail(lsq_ctx* c, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
   } while (0)
 
+// CUDA events destroyed on every return path.
+template <int N>
+struct Events {
+  cudaEvent_t e[N] = {};
+  cudaError_t create() {
+    for (auto& x : e)
+      if (cudaError_t r = cudaEventCreate(&x); r != cudaSuccess) return r;
+    return cudaSuccess;
+  }
+  cudaEvent_t& operator[](int i) { return e[i]; }
+  ~Events() {
+    for (auto x : e)
+      if (x) cudaEventDestroy(x);
+  }
+};
+
 struct Carver {
   char* base;
   size_t off = 0;
@@ -268,9 +284,9 @@ lsq_status calibrate_d(lsq_ctx* ctx, int64_t n64, lsq_ctx::DCalib* out) {
   CK(fill_hash(b, mc, 1, 1, 12, ctx->sms, st));
   CK(fill_identity(M, n, ctx->sms, st));
   CK(transpose_square(M, n, lw.Mt, st));
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
+  Events<2> ce;
+  CK(ce.create());
+  cudaEvent_t e0 = ce[0], e1 = ce[1];
   auto timed = [&](auto&& fn) -> float {
     float ms = -1.f;
     if (cudaEventRecord(e0, st) != cudaSuccess) return ms;
@@ -297,8 +313,6 @@ lsq_status calibrate_d(lsq_ctx* ctx, int64_t n64, lsq_ctx::DCalib* out) {
   timed([&] { return qr_d(d1); });
   const float q1 = timed([&] { return qr_d(d1); });
   const float q2 = timed([&] { return qr_d(d2); });
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   if (t2 < 0 || t6 < 0 || q1 < 0 || q2 < 0) return fail(ctx, LSQ_ERR_CUDA, "embedding-dimension calibration failed");
   lsq_ctx::DCalib cal;
   cal.t_iter_per_row = std::max(1e-15, (double)(t6 - t2) * 1e-3 / 4.0 / (double)mc);
@@ -754,9 +768,8 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
   pb.blas = blas_handle(ctx);
   pb.mode = ctx->qr_mode;
 
-  cudaEvent_t ev[6] = {};
-  if (timing)
-    for (auto& e : ev) CK(cudaEventCreate(&e));
+  Events<6> ev;
+  if (timing) CK(ev.create());
   if (timing) CK(cudaEventRecord(ev[0], st));
   if (host) {
     if (lda == n)  // packed rows: one flat copy
@@ -820,8 +833,6 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
     cudaEventElapsedTime(&t, ev[4], ev[5]);
     info->t_d2h_ms = t;
   }
-  if (timing)
-    for (auto& e : ev) cudaEventDestroy(e);
   return s;
 }
 
@@ -883,7 +894,8 @@ lsq_status lsq_solve_csr(lsq_ctx* ctx, const lsq_csr_problem* pr, const lsq_opts
   const bool timing = (o.flags & LSQ_FLAG_TIMING) != 0;
   const int ni = (int)n, npad = (int)((n + 31) / 32 * 32);
   const int64_t ncol = n + 1;
-  const int grid = lsqr_csr_grid(ctx->sms);
+  const int lanes = csr_lanes(m, pr->nnz);
+  const int grid = lsqr_csr_grid(ctx->sms, lanes);
   if (grid < 1) return fail(ctx, LSQ_ERR_CUDA, "no launchable CSR LSQR configuration");
   const int64_t maxit = o.maxit > 0 ? o.maxit : default_maxit(n, d, o.tol);
   auto carve = [&](Carver& cv, double** Y, PrecondBuffers* pb, double** R, double** M, LsqrWork* lw) {
@@ -911,11 +923,18 @@ lsq_status lsq_solve_csr(lsq_ctx* ctx, const lsq_csr_problem* pr, const lsq_opts
   pb.status = ctx->d_status;
   pb.blas = blas_handle(ctx);
   pb.mode = ctx->qr_mode;
-  cudaEvent_t ev[4] = {};
-  if (timing)
-    for (auto& e : ev) CK(cudaEventCreate(&e));
+  Events<4> ev;
+  if (timing) CK(ev.create());
   if (timing) CK(cudaEventRecord(ev[0], st));
   if ((s = reset_small(ctx, st)) != LSQ_OK) return s;
+  {
+    // no kernel indexes by row_ptr or col_idx before they are known to be well formed
+    CK(check_csr(pr->row_ptr, pr->col_idx, m, n, pr->nnz, ctx->d_status, ctx->sms, st));
+    uint32_t cbits = 0;
+    if ((s = read_small(ctx, st, &cbits, nullptr, nullptr)) != LSQ_OK) return s;
+    if (cbits & DS_CSR)
+      return fail(ctx, LSQ_ERR_ARG, "malformed CSR: need row_ptr[0] = 0, nondecreasing, row_ptr[m] = nnz, col_idx in [0, n)");
+  }
   CK(cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)d * ncol, st));
   CK(sketch_csr(pr->row_ptr, pr->col_idx, pr->values, pr->b, m, n, d, o.zeta, o.seed, Y, ncol, ctx->d_status,
                 ctx->d_max_rounds, ctx->sms, st));
@@ -963,7 +982,7 @@ lsq_status lsq_solve_csr(lsq_ctx* ctx, const lsq_csr_problem* pr, const lsq_opts
   p.out = ctx->d_out;
   CK(transpose_square(M, ni, lw.Mt, st));
   CK(cudaMemsetAsync(ctx->d_bar, 0, sizeof(GridBarrier), st));
-  CK(lsqr_csr_run(p, pr->row_ptr, pr->col_idx, pr->values, grid, st));
+  CK(lsqr_csr_run(p, pr->row_ptr, pr->col_idx, pr->values, grid, lanes, st));
   if (timing) CK(cudaEventRecord(ev[3], st));
   if ((s = read_small(ctx, st, &bits, nullptr, out)) != LSQ_OK) return s;
   s = status_from_bits(ctx, bits);
@@ -980,8 +999,6 @@ lsq_status lsq_solve_csr(lsq_ctx* ctx, const lsq_csr_problem* pr, const lsq_opts
       info->t_lsqr_ms = t;
     }
   }
-  if (timing)
-    for (auto& e : ev) cudaEventDestroy(e);
   return s;
 }
 
@@ -1051,9 +1068,9 @@ lsq_status lsq_solve_batch(lsq_ctx* ctx, const lsq_batch_item* items, int64_t co
       }
       float best_ms = 1e30f;
       int best = cand.back();
-      cudaEvent_t e0, e1;
-      CK(cudaEventCreate(&e0));
-      CK(cudaEventCreate(&e1));
+      Events<2> te;
+      CK(te.create());
+      cudaEvent_t e0 = te[0], e1 = te[1];
       for (int shp : cand) {
         batch_items_fill(host_items.data(), items, count, nullptr);
         for (int32_t i : sub) batch_set_item_shape(host_items.data(), i, shp);
@@ -1072,8 +1089,6 @@ lsq_status lsq_solve_batch(lsq_ctx* ctx, const lsq_batch_item* items, int64_t co
           best = shp;
         }
       }
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
       batch_set_shape(ctx->tuning, bk, best);
     }
   }

@@ -16,6 +16,7 @@ enum : uint32_t {
   DS_TIMEOUT = 4u,    // a grid barrier wait gave up
   DS_RANK = 8u,       // zero/negligible diagonal of R
   DS_NOCONV = 16u,    // LSQR reached maxit
+  DS_CSR = 32u,       // malformed CSR structure (row offsets or column indices)
 };
 
 constexpr int kMaxZeta = 64;

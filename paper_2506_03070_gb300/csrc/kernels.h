@@ -108,14 +108,18 @@ int lsqr_gparts(int grid);
 int lsqr_grid(int n, bool vec, bool native, int sms);
 cudaError_t lsqr_run(const LsqrParams& p, bool vec, bool native, int grid, cudaStream_t st);
 
-// Sparse A in CSR form (sparse.cu): sketch of the nonzeros (Y zeroed by the
+// Sparse A in CSR form (sparse.cu): structure check (sets DS_CSR), sketch of the nonzeros (Y zeroed by the
 // caller, ldy >= n + 1 with b), and the LSQR kernel over the nonzeros.
+cudaError_t check_csr(const int64_t* rp, const int32_t* ci, int64_t m, int64_t n, int64_t nnz, uint32_t* status,
+                      int sms, cudaStream_t st);
 cudaError_t sketch_csr(const int64_t* rp, const int32_t* ci, const double* va, const double* b, int64_t m, int64_t n,
                        int64_t d, int zeta, uint64_t seed, double* Y, int64_t ldy, uint32_t* status,
                        int32_t* max_rounds, int sms, cudaStream_t st);
-int lsqr_csr_grid(int sms);
+// lanes: lanes per row of the LSQR pass (csr_lanes picks it from the mean row length).
+int csr_lanes(int64_t m, int64_t nnz);
+int lsqr_csr_grid(int sms, int lanes);
 cudaError_t lsqr_csr_run(const LsqrParams& p, const int64_t* rp, const int32_t* ci, const double* va, int grid,
-                         cudaStream_t st);
+                         int lanes, cudaStream_t st);
 
 // Calibration fills (calib.cu): hash values in [-1, 1) into rows x cols (ld), M = I.
 cudaError_t fill_hash(double* p, int64_t rows, int64_t cols, int64_t ld, uint64_t seed, int sms, cudaStream_t st);

@@ -5,11 +5,11 @@
 // Two factorisations of the column-major copy W of Y, same reflectors and
 // same storage (R's diagonal in a separate array, R[k][j] left in W[j][k]):
 //
-// Unblocked (small sketches, see kBlockedMinBytes): one cooperative kernel.  Step k: every block
-// recomputes ||Y[k+1:,k]|| (same order, same result in all blocks), builds the
-// reflector scalars, and the grid's warps update the trailing columns j > k,
-// one warp per column.  Column k itself is never written, so one grid barrier
-// per column suffices.
+// Unblocked (small sketches, see kBlockedMinBytes): one cooperative kernel, one
+// block per SM.  Step k: every block recomputes ||Y[k+1:,k]|| (same order, same
+// result in all blocks), builds the reflector scalars, and updates its share
+// of the trailing columns j > k, two at a time.  Column k itself is never
+// written, so one grid barrier per column suffices.
 //
 // Blocked (compact WY, as LAPACK's geqrf/larft/larfb): panels of nb columns.
 // A panel kernel factors the panel with the reflectors of the unblocked
@@ -63,42 +63,102 @@ __device__ __forceinline__ T block_sum_t(T v, T* scratch) {
   return s;
 }
 
+// V fixed-order block sums at once, each in block_sum_t's order (so each
+// result equals a separate block_sum_t call), with one set of barriers.
+template <typename T, int V>
+__device__ __forceinline__ void block_sum_multi(T (&a)[V], T* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int v = 0; v < V; ++v)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a[v] += __shfl_xor_sync(0xffffffffu, a[v], o);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int v = 0; v < V; ++v) scratch[v * 32 + wid] = a[v];
+  __syncthreads();
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    T s = 0;
+    for (int i = 0; i < nw; ++i) s += scratch[v * 32 + i];
+    a[v] = s;
+  }
+  __syncthreads();
+}
+
+// Trailing columns a block takes through one pass of loads and one block sum.
+constexpr int kHhCols = 2;
+
 // TW = double (plain form) or float (mixed form: FP32 factorisation).
-// One block per trailing column (columns j = k+1+blockIdx.x, step gridDim.x):
-// its 256 threads share the column's dot product (fixed-order block sum) and
-// its update, so every SM's FP64 pipe works on the step -- on GB300 the FP64
-// rate, not memory, bounds a column step on few SMs.
+// One block per SM; block g owns the trailing columns j = k+1+g, k+1+g+G, ...
+// of step k and takes them kHhCols at a time: one loop over the rows loads
+// x = W[k+1:, k] and the group's columns and forms ||x||^2 (first group only:
+// every block computes it, in the same order, so every block derives the same
+// reflector) and the dot products, one block sum reduces them all, and a
+// second loop applies the reflector.  A step is bound by the dependent
+// memory round trips and block sums, not by the FP64 pipe, so folding the
+// norm and up to two columns into one round trip, on one block per SM, beats
+// one column per block on two blocks per SM by ~20% (d x n = 800 x 200 to
+// 4000 x 1000).  Column k is only read in step k: one grid barrier per column.
 template <typename TW>
 __global__ void __launch_bounds__(256) k_householder(TW* __restrict__ W, int64_t d, int n, int ncol,
                                                      double* __restrict__ rdiag, GridBarrier* bar, uint32_t* status) {
-  __shared__ TW scratch[32];
+  constexpr int CB = kHhCols;
+  __shared__ TW scratch[(CB + 1) * 32];
   const int kmax = n < d ? n : (int)d;
+  const int t = threadIdx.x, G = gridDim.x;
   for (int k = 0; k < kmax; ++k) {
     if (!grid_sync(bar, status)) return;
     const TW* wk = W + (int64_t)k * d;
-    TW part = 0;
-    for (int64_t i = k + 1 + threadIdx.x; i < d; i += blockDim.x) part = fma(wk[i], wk[i], part);
-    const TW sigma = block_sum_t<TW>(part, scratch);
     const TW alpha = wk[k];
+    const int j0 = k + 1 + blockIdx.x;
+    const int nc = j0 < ncol ? (ncol - j0 + G - 1) / G : 0;
     TW beta = alpha, tau = 0, inv_v0 = 0;
-    if (sigma != (TW)0) {
-      const TW nrm = sqrt(fma(alpha, alpha, sigma));
-      beta = alpha >= (TW)0 ? -nrm : nrm;
-      tau = (beta - alpha) / beta;
-      inv_v0 = (TW)1 / (alpha - beta);
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) rdiag[k] = (double)beta;
-    if (tau == (TW)0) continue;
-    for (int j = k + 1 + blockIdx.x; j < ncol; j += gridDim.x) {
-      TW* wj = W + (int64_t)j * d;
-      const TW wjk = wj[k];  // every thread reads it before thread 0 rewrites it (after the block sum)
-      TW s = 0;
-      for (int64_t i = k + 1 + threadIdx.x; i < d; i += blockDim.x) s = fma(wk[i], wj[i], s);
-      s = block_sum_t<TW>(s, scratch);
-      const TW f = tau * fma(inv_v0, s, wjk);
-      const TW fv = f * inv_v0;
-      if (threadIdx.x == 0) wj[k] = wjk - f;
-      for (int64_t i = k + 1 + threadIdx.x; i < d; i += blockDim.x) wj[i] = fma(-fv, wk[i], wj[i]);
+    // block 0 writes R's diagonal even when it owns no column
+    for (int c0 = 0; c0 < nc || (c0 == 0 && blockIdx.x == 0); c0 += CB) {
+      const bool first = c0 == 0;
+      const int cn = nc - c0 < CB ? nc - c0 : CB;
+      TW acc[CB + 1], wjk[CB];
+      TW* wc[CB];
+#pragma unroll
+      for (int c = 0; c < CB; ++c) {
+        acc[c] = 0;
+        wc[c] = W + (int64_t)(j0 + G * (c0 + c)) * d;  // dereferenced only for c < cn
+        wjk[c] = c < cn ? wc[c][k] : (TW)0;  // read by every thread before thread 0 rewrites it (after the block sum)
+      }
+      acc[CB] = 0;
+      for (int64_t i = k + 1 + t; i < d; i += blockDim.x) {
+        const TW x = wk[i];
+        if (first) acc[CB] = fma(x, x, acc[CB]);
+#pragma unroll
+        for (int c = 0; c < CB; ++c)
+          if (c < cn) acc[c] = fma(x, wc[c][i], acc[c]);
+      }
+      block_sum_multi<TW, CB + 1>(acc, scratch);
+      if (first) {
+        const TW sigma = acc[CB];
+        if (sigma != (TW)0) {
+          const TW nrm = sqrt(fma(alpha, alpha, sigma));
+          beta = alpha >= (TW)0 ? -nrm : nrm;
+          tau = (beta - alpha) / beta;
+          inv_v0 = (TW)1 / (alpha - beta);
+        }
+        if (blockIdx.x == 0 && t == 0) rdiag[k] = (double)beta;
+      }
+      if (tau == (TW)0) break;  // H = I: the same in every block
+      TW fv[CB];
+#pragma unroll
+      for (int c = 0; c < CB; ++c) {
+        const TW f = tau * fma(inv_v0, acc[c], wjk[c]);
+        fv[c] = f * inv_v0;
+        if (c < cn && t == 0) wc[c][k] = wjk[c] - f;
+      }
+      for (int64_t i = k + 1 + t; i < d; i += blockDim.x) {
+        const TW x = wk[i];
+#pragma unroll
+        for (int c = 0; c < CB; ++c)
+          if (c < cn) wc[c][i] = fma(-fv[c], x, wc[c][i]);
+      }
     }
   }
   grid_sync(bar, status);
@@ -444,9 +504,9 @@ cudaError_t precond(const TY* Y, int64_t d, int64_t n64, int64_t ldy, int has_b,
     int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_householder<TY>, 256, 0)) != cudaSuccess)
       return e;
-    // one block per trailing column, at most 2 per SM
+    // one block per SM (at most one per trailing column)
     int blocks = ncol - 1;
-    const int cap = (per_sm < 2 ? per_sm : 2) * sms;
+    const int cap = per_sm >= 1 ? sms : 0;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     int64_t dd = d;

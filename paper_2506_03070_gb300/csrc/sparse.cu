@@ -9,9 +9,10 @@
 // each row's nonzeros and adds +-a/sqrt(zeta) into the zeta rows of Y with L2
 // reductions; lane 0 adds the row's b entry into column n.
 //
-// LSQR pass: one warp per row.  Lanes stride over the row's nonzeros for the
-// dot with the pass vector (gathered through the read-only path), the warp
-// sum gives y_i = s A_i . w - gamma u_i, and the lanes add y_i a into the
+// LSQR pass: L lanes per row (1, 4 or 32 by the mean row length).  A row's
+// lanes stride over its nonzeros for the dot with the pass vector (gathered
+// through the read-only path), their sum gives y_i = s A_i . w - gamma u_i,
+// and the lanes add y_i a into the
 // block's own partial row of A^T y with FP64 L2 reductions (blocks never
 // share a partial row); the fixed-order sum over blocks (reduce_g) follows as
 // in the dense kernels.  u is FP64.
@@ -20,6 +21,25 @@
 
 namespace lsq {
 namespace {
+
+// The structure every later kernel indexes by: row_ptr[0] = 0, nondecreasing,
+// row_ptr[m] = nnz, and every column index in [0, n).
+__global__ void __launch_bounds__(256) k_check_csr(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                   int64_t m, int64_t n, int64_t nnz, uint32_t* status) {
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= m; i += stride) {
+    const int64_t r = __ldcs(rp + i);
+    if (i == 0) bad |= r != 0;
+    if (i == m) bad |= r != nnz;
+    if (i < m) bad |= __ldcs(rp + i + 1) < r;
+  }
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nnz; q += stride) {
+    const int32_t j = __ldcs(ci + q);
+    bad |= j < 0 || (int64_t)j >= n;
+  }
+  if (bad) atomicOr(status, DS_CSR);
+}
 
 __global__ void __launch_bounds__(256) k_sketch_csr(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                                     const double* __restrict__ va, const double* __restrict__ b,
@@ -72,6 +92,12 @@ __global__ void __launch_bounds__(256) k_sketch_csr(const int64_t* __restrict__ 
   if (bad) atomicOr(status, DS_NONFINITE);
 }
 
+// A pass over the rows with L lanes per row (32 / L rows per warp at a time):
+// few nonzeros per row leave most of a warp idle and a warp's rows latency
+// bound one after another, so short rows take one lane each (L = 1), medium
+// rows four and long rows the whole warp.  Each lane gathers up to four
+// nonzeros at a time so their loads overlap.
+template <int L>
 struct CsrPass {
   const int64_t* rp;
   const int32_t* ci;
@@ -84,7 +110,9 @@ struct CsrPass {
   template <bool UIN2, bool FRO>
   __device__ void run(LsqrParams& p, const double* __restrict__ wvec, double wsign, const double* __restrict__ uin,
                       double gamma, double* __restrict__ uout) {
+    constexpr int R = 32 / L;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int sub = lane / L, sl = lane % L;
     const int G = p.gcount, blk = p.gidx;
     p.gparts = G;
     double* gp = p.gpart + (int64_t)blk * p.npad;
@@ -92,22 +120,48 @@ struct CsrPass {
     __syncthreads();
     const int64_t r0 = (p.m * blk) / G, r1 = (p.m * (blk + 1)) / G;
     double ss = 0.0, bb = 0.0, fro = 0.0;
-    for (int64_t i = r0 + wib; i < r1; i += kWarps) {
-      const int64_t q0 = __ldg(rp + i), q1 = __ldg(rp + i + 1);
+    for (int64_t i0 = r0 + (int64_t)wib * R; i0 < r1; i0 += (int64_t)kWarps * R) {
+      const int64_t i = i0 + sub;
+      const bool live = i < r1;
+      int64_t q0 = 0, q1 = 0;
+      if (live) {
+        q0 = __ldg(rp + i);
+        q1 = __ldg(rp + i + 1);
+      }
       double dot = 0.0;
-      for (int64_t q = q0 + lane; q < q1; q += 32) dot = fma(__ldg(va + q), __ldg(wvec + __ldg(ci + q)), dot);
-      dot = warp_allreduce_sum(dot);
-      const double ui = uin[i];
-      const double y = fma(-gamma, ui, wsign * dot);
-      if (uout && lane == 0) uout[i] = y;
-      ss = fma(y, y, ss);
-      if (UIN2) bb = fma(ui, ui, bb);
-      for (int64_t q = q0 + lane; q < q1; q += 32) {
-        const double a = __ldg(va + q);
-        atomicAdd(gp + __ldg(ci + q), y * a);
-        if (FRO) fro = fma(a, a, fro);
+      for (int64_t q = q0 + sl; q < q1; q += 4 * L) {
+        int32_t c[4];
+        double a[4], w[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int64_t qq = q + (int64_t)t * L;
+          c[t] = qq < q1 ? __ldg(ci + qq) : -1;
+          a[t] = qq < q1 ? __ldg(va + qq) : 0.0;
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) w[t] = c[t] >= 0 ? __ldg(wvec + c[t]) : 0.0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) dot = fma(a[t], w[t], dot);
+      }
+#pragma unroll
+      for (int o = L / 2; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+      if (live) {
+        const double ui = uin[i];
+        const double y = fma(-gamma, ui, wsign * dot);
+        if (sl == 0) {
+          if (uout) uout[i] = y;
+          ss = fma(y, y, ss);
+          if (UIN2) bb = fma(ui, ui, bb);
+        }
+        for (int64_t q = q0 + sl; q < q1; q += L) {
+          const double a = __ldg(va + q);
+          atomicAdd(gp + __ldg(ci + q), y * a);
+          if (FRO) fro = fma(a, a, fro);
+        }
       }
     }
+    ss = warp_allreduce_sum(ss);
+    if (UIN2) bb = warp_allreduce_sum(bb);
     if (FRO) fro = warp_allreduce_sum(fro);
     if (lane == 0) {
       s_scal[wib * 4 + 0] = ss;
@@ -134,9 +188,10 @@ struct CsrArgs {
   const double* va;
 };
 
+template <int L>
 __global__ void __launch_bounds__(kThreads, 2) k_lsqr_csr(LsqrParams p, CsrArgs c) {
   __shared__ double s_scal[kWarps * 4];
-  CsrPass pass{c.rp, c.ci, c.va, s_scal};
+  CsrPass<L> pass{c.rp, c.ci, c.va, s_scal};
   p.gidx = blockIdx.x;
   p.gcount = gridDim.x;
   if (p.mode >= 3)
@@ -145,7 +200,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_lsqr_csr(LsqrParams p, CsrArgs 
     lsqr_body(p, pass, s_scal);
 }
 
+const void* csr_kernel(int lanes) {
+  return lanes == 1 ? (const void*)k_lsqr_csr<1> : lanes == 4 ? (const void*)k_lsqr_csr<4> : (const void*)k_lsqr_csr<32>;
+}
+
 }  // namespace
+
+cudaError_t check_csr(const int64_t* rp, const int32_t* ci, int64_t m, int64_t n, int64_t nnz, uint32_t* status,
+                      int sms, cudaStream_t st) {
+  const int64_t work = (m > nnz ? m : nnz) + 1;
+  const int blocks = (int)std::min<int64_t>((work + 255) / 256, (int64_t)sms * 8);
+  k_check_csr<<<blocks, 256, 0, st>>>(rp, ci, m, n, nnz, status);
+  return cudaGetLastError();
+}
 
 cudaError_t sketch_csr(const int64_t* rp, const int32_t* ci, const double* va, const double* b, int64_t m, int64_t n,
                        int64_t d, int zeta, uint64_t seed, double* Y, int64_t ldy, uint32_t* status,
@@ -156,19 +223,25 @@ cudaError_t sketch_csr(const int64_t* rp, const int32_t* ci, const double* va, c
   return cudaGetLastError();
 }
 
-int lsqr_csr_grid(int sms) {
+int csr_lanes(int64_t m, int64_t nnz) {
+  const int64_t avg = m > 0 ? nnz / m : 0;
+  return avg <= 8 ? 1 : avg <= 48 ? 4 : 32;
+}
+
+int lsqr_csr_grid(int sms, int lanes) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lsqr_csr, kThreads, 0) != cudaSuccess || per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_kernel(lanes), kThreads, 0) != cudaSuccess ||
+      per_sm < 1)
     return 0;
   return (per_sm > 2 ? 2 : per_sm) * sms;
 }
 
 cudaError_t lsqr_csr_run(const LsqrParams& p, const int64_t* rp, const int32_t* ci, const double* va, int grid,
-                         cudaStream_t st) {
+                         int lanes, cudaStream_t st) {
   LsqrParams q = p;
   CsrArgs c{rp, ci, va};
   void* args[] = {&q, &c};
-  return cudaLaunchCooperativeKernel((const void*)k_lsqr_csr, grid, kThreads, args, 0, st);
+  return cudaLaunchCooperativeKernel(csr_kernel(lanes), grid, kThreads, args, 0, st);
 }
 
 }  // namespace lsq

@@ -379,11 +379,13 @@ def test_solve_with_hbm_flag(ctx, orc):
     assert orc.backward_error_kw(A, b, x.cpu().numpy()) <= 1e-10
 
 
-@pytest.mark.parametrize("m,n,density,d", [(20000, 50, 0.02, 200), (30000, 120, 0.05, 480), (8000, 600, 0.1, 2400)])
+@pytest.mark.parametrize("m,n,density,d", [(20000, 50, 0.02, 200), (30000, 120, 0.05, 480), (12000, 300, 0.06, 1200),
+                                          (8000, 600, 0.1, 2400)])
 def test_solve_csr_matches_oracle_and_dense(ctx, orc, m, n, density, d):
     """Sparse A in CSR form (the paper's random-sign sparse recipe; (20000, 50,
     0.02) leaves most rows empty): the same sketch columns as the dense path, so
-    the solve follows the oracle run on the dense form of A."""
+    the solve follows the oracle run on the dense form of A.  Mean row lengths
+    1, 6, 18 and 60 take the pass with 1, 1, 4 and 32 lanes per row."""
     from paper_2506_03070_gb300 import synth
     p = synth.sparse_sign_problem(m, n, density, seed=m + n, device="cuda")
     A = synth.csr_to_dense(p).cpu().numpy()
@@ -404,6 +406,31 @@ def test_solve_csr_matches_oracle_and_dense(ctx, orc, m, n, density, d):
                                flags=P.FLAG_HBM)
     assert ih["status"] == 0 and ih["d_used"] > n
     assert orc.backward_error_kw(A, b, xh.cpu().numpy()) <= 1e-10
+
+
+def test_solve_csr_rejects_malformed_structure(ctx):
+    """Row offsets and column indices are checked on the device before any
+    kernel indexes by them: a column index out of [0, n), offsets that
+    decrease or that do not end at nnz give LSQ_ERR_ARG."""
+    import paper_2506_03070_gb300 as P
+    from paper_2506_03070_gb300 import synth
+    p = synth.sparse_sign_problem(3000, 40, 0.05, seed=8, device="cuda")
+    x, info = ctx.lsq_solve_csr(p["row_ptr"], p["col_idx"], p["values"], p["b"], 40, 160, seed=1)
+    assert info["status"] == 0
+    for what in ("col_n", "col_neg", "rp_dec", "rp_end"):
+        rp, ci = p["row_ptr"].clone(), p["col_idx"].clone()
+        if what == "col_n":
+            ci[len(ci) // 2] = 40
+        elif what == "col_neg":
+            ci[7] = -1
+        elif what == "rp_dec":
+            k = 1500
+            rp[k] = rp[k + 1] + 1
+        else:
+            rp[-1] = rp[-1] - 1
+        with pytest.raises(P.LsqError) as e:
+            ctx.lsq_solve_csr(rp, ci, p["values"], p["b"], 40, 160, seed=1)
+        assert e.value.status == -1, what
 
 
 def test_solve_consistent_system(ctx, orc):
