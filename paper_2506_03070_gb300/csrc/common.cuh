@@ -156,17 +156,26 @@ __device__ __forceinline__ float warp_allreduce_sum(float v) {
 }
 
 // Block-wide sum in a fixed order (deterministic for a fixed block size).
-// `scratch` holds at least 32 doubles.  Result valid in every thread.
+// `scratch` holds at least 32 doubles.  Result valid in every thread.  One
+// thread adds the per-warp sums and shares the total: GB300's FP64 pipe
+// retires ~1.6 lanes per clock per SM, so every thread adding them would cost
+// each warp its own pass through the pipe.  Every thread reads the total
+// before it can reach the next call's first barrier, and the total is only
+// rewritten after that call's second one.
 __device__ __forceinline__ double block_sum(double v, double* scratch) {
+  __shared__ double s_total;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   v = warp_allreduce_sum(v);
   __syncthreads();
   if (lane == 0) scratch[wid] = v;
   __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < nw; ++i) s += scratch[i];
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < nw; ++i) s += scratch[i];
+    s_total = s;
+  }
   __syncthreads();
-  return s;
+  return s_total;
 }
 
 }  // namespace lsq

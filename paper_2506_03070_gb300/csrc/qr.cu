@@ -8,7 +8,7 @@
 // Unblocked (small sketches, see kBlockedMinBytes): one cooperative kernel, one
 // block per SM.  Step k: every block recomputes ||Y[k+1:,k]|| (same order, same
 // result in all blocks), builds the reflector scalars, and updates its share
-// of the trailing columns j > k, two at a time.  Column k itself is never
+// of the trailing columns j > k, two or three at a time.  Column k itself is never
 // written, so one grid barrier per column suffices.
 //
 // Blocked (compact WY, as LAPACK's geqrf/larft/larfb): panels of nb columns.
@@ -48,23 +48,29 @@ __global__ void k_to_colmajor(const TY* __restrict__ Y, int64_t d, int ncol, int
   }
 }
 
-// Fixed-order block sum for float or double.
+// Fixed-order block sum for float or double (thread 0 adds the per-warp sums
+// and shares the total, as block_sum does).
 template <typename T>
 __device__ __forceinline__ T block_sum_t(T v, T* scratch) {
+  __shared__ T s_total;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   __syncthreads();
   if (lane == 0) scratch[wid] = v;
   __syncthreads();
-  T s = 0;
-  for (int i = 0; i < nw; ++i) s += scratch[i];
+  if (threadIdx.x == 0) {
+    T s = 0;
+    for (int i = 0; i < nw; ++i) s += scratch[i];
+    s_total = s;
+  }
   __syncthreads();
-  return s;
+  return s_total;
 }
 
-// V fixed-order block sums at once, each in block_sum_t's order (so each
-// result equals a separate block_sum_t call), with one set of barriers.
+// V fixed-order block sums at once, each in block_sum_t's order: lanes v < V
+// of warp 0 add the per-warp sums of value v; the totals land in
+// scratch[32 V + v] (scratch holds 33 V values) and in a[] of every thread.
 template <typename T, int V>
 __device__ __forceinline__ void block_sum_multi(T (&a)[V], T* scratch) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -77,43 +83,41 @@ __device__ __forceinline__ void block_sum_multi(T (&a)[V], T* scratch) {
 #pragma unroll
     for (int v = 0; v < V; ++v) scratch[v * 32 + wid] = a[v];
   __syncthreads();
-#pragma unroll
-  for (int v = 0; v < V; ++v) {
+  if (threadIdx.x < V) {
     T s = 0;
-    for (int i = 0; i < nw; ++i) s += scratch[v * 32 + i];
-    a[v] = s;
+    for (int i = 0; i < nw; ++i) s += scratch[threadIdx.x * 32 + i];
+    scratch[V * 32 + threadIdx.x] = s;
   }
   __syncthreads();
+#pragma unroll
+  for (int v = 0; v < V; ++v) a[v] = scratch[V * 32 + v];
 }
-
-// Trailing columns a block takes through one pass of loads and one block sum.
-constexpr int kHhCols = 2;
 
 // TW = double (plain form) or float (mixed form: FP32 factorisation).
 // One block per SM; block g owns the trailing columns j = k+1+g, k+1+g+G, ...
-// of step k and takes them kHhCols at a time: one loop over the rows loads
+// of step k and takes them CB at a time: one loop over the rows loads
 // x = W[k+1:, k] and the group's columns and forms ||x||^2 (first group only:
 // every block computes it, in the same order, so every block derives the same
-// reflector) and the dot products, one block sum reduces them all, and a
-// second loop applies the reflector.  A step is bound by the dependent
-// memory round trips and block sums, not by the FP64 pipe, so folding the
-// norm and up to two columns into one round trip, on one block per SM, beats
-// one column per block on two blocks per SM by ~20% (d x n = 800 x 200 to
-// 4000 x 1000).  Column k is only read in step k: one grid barrier per column.
-template <typename TW>
+// reflector) and the dot products, one block sum reduces them all, thread 0
+// forms the reflector and the column scalars and shares them, and a second
+// loop applies the reflector.  A step is bound by dependent round trips and
+// by the FP64 pipe of the SM that owns the most columns (GB300 retires ~1.6
+// FP64 lanes per clock per SM), so the work that is not per row -- the sums
+// over warps, sqrt and the divisions -- runs on one lane, not on every
+// thread.  Column k is only read in step k: one grid barrier per column.
+template <typename TW, int CB>
 __global__ void __launch_bounds__(256) k_householder(TW* __restrict__ W, int64_t d, int n, int ncol,
                                                      double* __restrict__ rdiag, GridBarrier* bar, uint32_t* status) {
-  constexpr int CB = kHhCols;
-  __shared__ TW scratch[(CB + 1) * 32];
+  __shared__ TW scratch[(CB + 1) * 33];
+  __shared__ TW s_sc[CB + 1];  // fv of the group's columns, then tau
   const int kmax = n < d ? n : (int)d;
   const int t = threadIdx.x, G = gridDim.x;
   for (int k = 0; k < kmax; ++k) {
     if (!grid_sync(bar, status)) return;
     const TW* wk = W + (int64_t)k * d;
-    const TW alpha = wk[k];
     const int j0 = k + 1 + blockIdx.x;
     const int nc = j0 < ncol ? (ncol - j0 + G - 1) / G : 0;
-    TW beta = alpha, tau = 0, inv_v0 = 0;
+    TW tau = 0, inv_v0 = 0;  // thread 0's copy (from the first group) is the one used
     // block 0 writes R's diagonal even when it owns no column
     for (int c0 = 0; c0 < nc || (c0 == 0 && blockIdx.x == 0); c0 += CB) {
       const bool first = c0 == 0;
@@ -124,7 +128,7 @@ __global__ void __launch_bounds__(256) k_householder(TW* __restrict__ W, int64_t
       for (int c = 0; c < CB; ++c) {
         acc[c] = 0;
         wc[c] = W + (int64_t)(j0 + G * (c0 + c)) * d;  // dereferenced only for c < cn
-        wjk[c] = c < cn ? wc[c][k] : (TW)0;  // read by every thread before thread 0 rewrites it (after the block sum)
+        wjk[c] = (c < cn && t == 0) ? wc[c][k] : (TW)0;  // thread 0 rewrites it after the block sum
       }
       acc[CB] = 0;
       for (int64_t i = k + 1 + t; i < d; i += blockDim.x) {
@@ -135,24 +139,38 @@ __global__ void __launch_bounds__(256) k_householder(TW* __restrict__ W, int64_t
           if (c < cn) acc[c] = fma(x, wc[c][i], acc[c]);
       }
       block_sum_multi<TW, CB + 1>(acc, scratch);
-      if (first) {
-        const TW sigma = acc[CB];
-        if (sigma != (TW)0) {
-          const TW nrm = sqrt(fma(alpha, alpha, sigma));
-          beta = alpha >= (TW)0 ? -nrm : nrm;
-          tau = (beta - alpha) / beta;
-          inv_v0 = (TW)1 / (alpha - beta);
+      if (t == 0) {
+        if (first) {
+          const TW alpha = wk[k];
+          const TW sigma = acc[CB];
+          TW beta = alpha;
+          if (sigma != (TW)0) {
+            const TW nrm = sqrt(fma(alpha, alpha, sigma));
+            beta = alpha >= (TW)0 ? -nrm : nrm;
+            tau = (beta - alpha) / beta;
+            inv_v0 = (TW)1 / (alpha - beta);
+          }
+          if (blockIdx.x == 0) rdiag[k] = (double)beta;
         }
-        if (blockIdx.x == 0 && t == 0) rdiag[k] = (double)beta;
+        s_sc[CB] = tau;
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+          TW fv = 0;
+          if (c < cn && tau != (TW)0) {
+            const TW f = tau * fma(inv_v0, acc[c], wjk[c]);
+            fv = f * inv_v0;
+            wc[c][k] = wjk[c] - f;
+          }
+          s_sc[c] = fv;
+        }
       }
-      if (tau == (TW)0) break;  // H = I: the same in every block
+      __syncthreads();
+      const TW tau_b = s_sc[CB];
       TW fv[CB];
 #pragma unroll
-      for (int c = 0; c < CB; ++c) {
-        const TW f = tau * fma(inv_v0, acc[c], wjk[c]);
-        fv[c] = f * inv_v0;
-        if (c < cn && t == 0) wc[c][k] = wjk[c] - f;
-      }
+      for (int c = 0; c < CB; ++c) fv[c] = s_sc[c];
+      __syncthreads();  // s_sc is rewritten by the next group
+      if (tau_b == (TW)0) break;  // H = I: the same in every block
       for (int64_t i = k + 1 + t; i < d; i += blockDim.x) {
         const TW x = wk[i];
 #pragma unroll
@@ -501,22 +519,22 @@ cudaError_t precond(const TY* Y, int64_t d, int64_t n64, int64_t ldy, int has_b,
   if (buf.blk && buf.blas && blocked && (size_t)kPanelMax * ncol <= ((size_t)1 << 31)) {
     if ((e = householder_blocked<TY>(W, d, n, ncol, buf.rdiag, buf, sms, st)) != cudaSuccess) return e;
   } else {
-    int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_householder<TY>, 256, 0)) != cudaSuccess)
-      return e;
-    // one block per SM (at most one per trailing column)
-    int blocks = ncol - 1;
-    const int cap = per_sm >= 1 ? sms : 0;
-    if (blocks > cap) blocks = cap;
+    // one block per SM (at most one per trailing column); three columns per
+    // group once a block owns more than two (measured: 2000 x 501 5.3 vs 5.7
+    // ms, 4000 x 1001 21 vs 23 ms; 800 x 201 1.35 ms with two)
+    int blocks = ncol - 1 < sms ? ncol - 1 : sms;
     if (blocks < 1) blocks = 1;
+    const void* fn = ncol - 1 > 2 * blocks ? (const void*)k_householder<TY, 3> : (const void*)k_householder<TY, 2>;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0)) != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
     int64_t dd = d;
     int nn = n, nc = ncol;
     double* rd = buf.rdiag;
     GridBarrier* bar = buf.bar;
     uint32_t* status = buf.status;
     void* args[] = {&W, &dd, &nn, &nc, &rd, &bar, &status};
-    if ((e = cudaLaunchCooperativeKernel((const void*)k_householder<TY>, blocks, 256, args, 0, st)) != cudaSuccess)
-      return e;
+    if ((e = cudaLaunchCooperativeKernel(fn, blocks, 256, args, 0, st)) != cudaSuccess) return e;
   }
   double* Rw = R ? R : buf.R;
   k_extract_r<TY><<<(unsigned)std::min<int64_t>(((int64_t)n * n + 255) / 256, 1024), 256, 0, st>>>(
