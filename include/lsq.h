@@ -163,7 +163,7 @@ lsq_status lsq_precond(lsq_ctx* ctx, const void* Y, int64_t d, int64_t n, int64_
  * the blocked factorisation (compact WY: panels factored by a cooperative
  * kernel, trailing updates as tensor-core GEMMs -- DGEMM for FP64, FP32
  * emulated with three BF16 terms for the mixed form) once the d x (n+1)
- * working copy reaches 32 MiB and n >= 128, the unblocked one (one grid
+ * working copy reaches 32 MiB and n >= 1700, the unblocked one (one grid
  * barrier per column) below.  Both compute the same reflectors. */
 /* ---- Embedding dimension (Sec. 4.3 "Selecting the embedding dimension") ----
  * The solve time is modelled as T(d) = T_qr(d) + (t(d) + 2) T_iter(m): the

@@ -5,7 +5,7 @@
 // Two factorisations of the column-major copy W of Y, same reflectors and
 // same storage (R's diagonal in a separate array, R[k][j] left in W[j][k]):
 //
-// Unblocked (small sketches, see kBlockedMinBytes): one cooperative kernel, one
+// Unblocked (all but wide sketches, see kBlockedMinN): one cooperative kernel, one
 // block per SM.  Step k: every block recomputes ||Y[k+1:,k]|| (same order, same
 // result in all blocks), builds the reflector scalars, and updates its share
 // of the trailing columns j > k, two or three at a time.  Column k itself is never
@@ -402,11 +402,13 @@ cudaError_t householder_blocked(TW* W, int64_t d, int n, int ncol, double* rdiag
   return cudaSuccess;
 }
 
-// Automatic choice: the blocked path once the working copy W no longer sits
-// comfortably in L2 (the unblocked kernel then streams the trailing matrix
-// from HBM for every column); below that the unblocked kernel's single
+// Automatic choice: the blocked path for wide sketches whose working copy W
+// no longer sits comfortably in L2; below that the unblocked kernel's single
 // barrier per column is cheaper than the panel's two plus the GEMM launches.
-constexpr int kBlockedMinN = 128;
+// Measured precond times, unblocked vs blocked (ms): FP64 d x n = 2000 x 500
+// 6.8 vs 16.9, 9600 x 500 21.6 vs 26.2, 6000 x 1500 73.6 vs 84.1, 8000 x 2000
+// 191 vs 142; FP32 4000 x 1000 17.3 vs 37.7, 8000 x 2000 102 vs 81.
+constexpr int kBlockedMinN = 1700;
 constexpr size_t kBlockedMinBytes = (size_t)32 << 20;
 
 // R (row-major n x n, upper), z = W[n][0:n] (x0 slot), and the rank test
