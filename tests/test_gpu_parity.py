@@ -304,7 +304,14 @@ def test_solve_host_memory_equals_device(ctx, orc, prec):
     bn = np.linalg.norm(b)
     assert np.linalg.norm(A @ (xd.cpu().numpy() - xh)) <= 1e-10 * bn
     assert orc.backward_error_kw(A, b, xh) <= 1e-10
-    assert abs(infod["iters"] - infoh["iters"]) <= 1
+    # FP64: the two runs differ only in the order of the sketch's L2 reductions
+    # (Y moves at the 1e-16 level), so the iteration counts agree to one.  Mixed
+    # form: Y is accumulated in FP32 in that arbitrary order (1e-7 relative) and
+    # the FP32 QR carries it into M, so kappa(AM) -- about 4 here, where
+    # cond(A) = 1e8 meets FP32's 6e-8 unit roundoff -- moves by a few percent
+    # between runs and LSQR's count (~55) with it.
+    slack = 1 if prec == 0 else max(1, int(0.1 * infod["iters"]))
+    assert abs(infod["iters"] - infoh["iters"]) <= slack, (infod["iters"], infoh["iters"])
 
 
 def test_solve_edge_shapes(ctx, orc):
