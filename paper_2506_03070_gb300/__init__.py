@@ -177,6 +177,26 @@ def _dev_f64(t, name):
     return t
 
 
+def _vec(t, length, name, device=None):
+    """A CUDA float64 tensor holding exactly `length` contiguous elements (on
+    `device` when given): the C calls read or write that many from its first
+    element, so a shorter or strided tensor is refused here."""
+    _dev_f64(t, name)
+    if t.numel() != length or not t.is_contiguous():
+        raise ValueError(f"{name} must hold {length} contiguous float64 elements, got shape {tuple(t.shape)}")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, A on {device}")
+    return t
+
+
+def _host_vec(a, length, name):
+    """A contiguous float64 numpy copy (or view) of `a` with `length` elements."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.size != length:
+        raise ValueError(f"{name} must hold {length} elements, got shape {a.shape}")
+    return a
+
+
 def _rowmajor(A):
     if A.dim() != 2 or A.stride(1) != 1:
         raise ValueError("A must be a row-major 2-D tensor (unit column stride)")
@@ -243,7 +263,7 @@ class Context:
         _dev_f64(A, "A")
         m, n, lda = _rowmajor(A)
         if b is not None:
-            _dev_f64(b, "b")
+            _vec(b, m, "b", A.device)
         ncol = n + (b is not None)
         if ldy is None:
             ldy = ncol if prec == PREC_FP64 else (ncol + 3) // 4 * 4
@@ -254,6 +274,8 @@ class Context:
 
     def lsq_precond(self, Y, n, has_b=True, prec=None, want_R=True, stream=None):
         import torch
+        if Y.dim() != 2 or Y.stride(1) != 1 or Y.shape[1] < n + int(bool(has_b)):
+            raise ValueError("Y must be a row-major d x (n + has_b) tensor (unit column stride)")
         d, ldy = Y.shape[0], Y.stride(0)
         if prec is None:
             prec = PREC_FP64 if Y.dtype == torch.float64 else PREC_MIXED
@@ -269,6 +291,10 @@ class Context:
         import torch
         _dev_f64(A, "A")
         m, n, lda = _rowmajor(A)
+        _vec(b, m, "b", A.device)
+        _vec(M, n * n, "M", A.device)
+        if x0 is not None:
+            _vec(x0, n, "x0", A.device)
         x = torch.empty((n,), dtype=torch.float64, device=A.device)
         info = Info()
         st = self.lib.lsq_lsqr(self.h, _ptr(A), m, n, lda, _ptr(b), _ptr(M), _ptr(x0), tol, maxit, flags, _ptr(x),
@@ -281,6 +307,10 @@ class Context:
         import torch
         _dev_f64(A, "A")
         m, n, lda = _rowmajor(A)
+        _vec(b, m, "b", A.device)
+        _vec(M, n * n, "M", A.device)
+        if x0 is not None:
+            _vec(x0, n, "x0", A.device)
         x = torch.empty((n,), dtype=torch.float64, device=A.device)
         info = Info()
         st = self.lib.lsq_hbm(self.h, _ptr(A), m, n, lda, _ptr(b), _ptr(M), _ptr(x0), tol, maxit, eta_hat, flags,
@@ -295,8 +325,14 @@ class Context:
         import torch
         if row_ptr.dtype != torch.int64 or col_idx.dtype != torch.int32 or values.dtype != torch.float64:
             raise TypeError("row_ptr int64, col_idx int32, values float64")
-        _dev_f64(b, "b")
         m = row_ptr.numel() - 1
+        dev = row_ptr.device
+        for t, name in ((row_ptr, "row_ptr"), (col_idx, "col_idx"), (values, "values")):
+            if not t.is_cuda or not t.is_contiguous() or t.device != dev:
+                raise ValueError(f"{name} must be a contiguous CUDA tensor on {dev}")
+        if m < 1 or col_idx.numel() != values.numel():
+            raise ValueError("need m >= 1 (row_ptr holds m + 1 offsets) and one column index per value")
+        _vec(b, m, "b", dev)
         x = torch.empty((n,), dtype=torch.float64, device=b.device)
         pr = CsrProblem(_ptr(row_ptr), _ptr(col_idx), _ptr(values), _ptr(b), m, n, values.numel())
         op = Opts(d, zeta, PREC_FP64, seed, tol, maxit, flags, 0)
@@ -309,6 +345,10 @@ class Context:
     def lsq_check(self, A, b, x, M=None, stream=None):
         _dev_f64(A, "A")
         m, n, lda = _rowmajor(A)
+        _vec(b, m, "b", A.device)
+        _vec(x, n, "x", A.device)
+        if M is not None:
+            _vec(M, n * n, "M", A.device)
         info = Info()
         self._check(self.lib.lsq_check(self.h, _ptr(A), m, n, lda, _ptr(b), _ptr(x), _ptr(M), ctypes.byref(info),
                                        _stream(stream)))
@@ -334,20 +374,24 @@ class Context:
         if isinstance(A, np.ndarray):
             if A.dtype != np.float64 or A.ndim != 2 or A.strides[1] != 8:
                 raise ValueError("host A must be a row-major float64 array")
-            b = np.ascontiguousarray(b, dtype=np.float64)
             m, n = A.shape
+            b = _host_vec(b, m, "b")
             lda = A.strides[0] // 8
             mem = MEM_HOST
             if x is None:
                 x = np.empty(n, dtype=np.float64)
+            elif not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.size == n and x.flags.c_contiguous):
+                raise ValueError(f"host x must be a contiguous float64 array of {n} elements")
             strm = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
         else:
             _dev_f64(A, "A")
-            _dev_f64(b, "b")
             m, n, lda = _rowmajor(A)
+            _vec(b, m, "b", A.device)
             mem = MEM_DEVICE
             if x is None:
                 x = torch.empty((n,), dtype=torch.float64, device=A.device)
+            else:
+                _vec(x, n, "x", A.device)
             strm = _stream(stream)
         pr = Problem(_ptr(A), _ptr(b), m, n, lda, mem, 0)
         op = Opts(d, zeta, prec, seed, tol, maxit, flags, 0)
@@ -371,19 +415,23 @@ class Context:
         if isinstance(A, np.ndarray):
             if A.dtype != np.float64 or A.ndim != 2 or A.strides[1] != 8:
                 raise ValueError("host A must be a row-major float64 array")
-            b = np.ascontiguousarray(b, dtype=np.float64)
             m, n = A.shape
+            b = _host_vec(b, m, "b")
             lda = A.strides[0] // 8
             mem = MEM_HOST
             if x is None:
                 x = np.empty(n, dtype=np.float64)
+            elif not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.size == n and x.flags.c_contiguous):
+                raise ValueError(f"host x must be a contiguous float64 array of {n} elements")
         else:
             _dev_f64(A, "A")
-            _dev_f64(b, "b")
             m, n, lda = _rowmajor(A)
+            _vec(b, m, "b", A.device)
             mem = MEM_DEVICE
             if x is None:
                 x = torch.empty((n,), dtype=torch.float64, device=A.device)
+            else:
+                _vec(x, n, "x", A.device)
         pr = Problem(_ptr(A), _ptr(b), m, n, lda, mem, 0)
         op = Opts(d, zeta, PREC_FP64, seed, tol, maxit, flags, 0)
         t = ctypes.c_int64()
@@ -452,11 +500,13 @@ def _batch_items(problems):
     for i, pr in enumerate(problems):
         A, b = pr["A"], pr["b"]
         _dev_f64(A, "A")
-        _dev_f64(b, "b")
         m, n, lda = _rowmajor(A)
+        _vec(b, m, "b", A.device)
         x = pr.get("x")
         if x is None:
             x = torch.empty((n,), dtype=torch.float64, device=A.device)
+        else:
+            _vec(x, n, "x", A.device)
         xs.append(x)
         items[i] = BatchItem(_ptr(A), _ptr(b), _ptr(x), m, n, lda, pr.get("d", 4 * n), pr.get("zeta", 8), 0,
                              pr.get("seed", 0))
