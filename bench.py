@@ -131,6 +131,10 @@ def _workload(p, prec):
 # capture summarised in profiles/lsqr_df_1000000x500.md (1e6 x 500, 5 passes:
 # 25.33 GB measured for 24.08 GB algorithmic); traffic grows with passes x rows.
 LSQR_DF_TRAFFIC_RATIO = 25.33 / 24.08
+# The kernel's block sums changed after that capture (the per-warp totals are
+# now added on one lane), so its counters no longer describe the code that
+# runs: the bench line reports traffic as null until the next capture.
+LSQR_DF_TRAFFIC_CURRENT = False
 
 
 def lsqr_algorithmic_bytes(m, n, iters):
@@ -716,8 +720,11 @@ def run_gpu(args):
         "config": dict(_workload(p, args.prec), parallelism="replicas" if world > 1 else "single"),
         "roofline": {"bound": "hbm", "kernel": "k_lsqr_native" if args.native else "k_lsqr_df", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None if (args.native or n > 512 or args.prec != "fp64")
+                     "traffic": None if (args.native or n > 512 or args.prec != "fp64" or not LSQR_DF_TRAFFIC_CURRENT)
                      else LSQR_DF_TRAFFIC_RATIO * alg_bytes,
+                     "traffic_last_capture": {"ratio_to_algorithmic": round(LSQR_DF_TRAFFIC_RATIO, 4),
+                                              "summary": "profiles/lsqr_df_1000000x500.md",
+                                              "current": LSQR_DF_TRAFFIC_CURRENT},
                      "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
                      else "fallback 6.8 TB/s"},
         "gpu_launches": 8 * args.steps,
