@@ -242,10 +242,6 @@ def default_maxit(n, d, tol):
     return int(10 * np.ceil(np.log(tol) / np.log(rate)))
 
 
-if __name__ == "__main__":  # pragma: no cover
-    print(build(force="--force" in sys.argv))
-
-
 def hbm_params(eta_hat):
     """App. C.2 ("Gradient methods"): step alpha = (1 - eta^2)^2 and momentum
     beta = eta^2, rate sqrt(beta).  These are the optimal heavy-ball
@@ -300,3 +296,7 @@ def hbm(A, b, M, x0, alpha, beta, tol, maxit, trace=False):
     if trace:
         out["trace"] = np.array(tr).reshape(len(tr), -1)
     return out
+
+
+if __name__ == "__main__":  # pragma: no cover
+    print(build(force="--force" in sys.argv))

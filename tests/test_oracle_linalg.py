@@ -265,3 +265,15 @@ def test_solve_end_to_end(orc):
     assert np.linalg.norm(A @ (out["x"] - xt)) < 1e-10 * np.linalg.norm(b)
     n = 40
     assert np.allclose(out["M"] @ out["R"], np.eye(n), atol=1e-6)
+
+
+def test_default_maxit_is_ten_times_the_rate_estimate(orc):
+    """Reading of the stopping rule: ten times the Sec. 4.3 estimate
+    t = log(tol) / log(sqrt(n/d)) iterations, rounded up."""
+    assert orc.default_maxit(200, 800, 1e-12) == 400  # sqrt(1/4) = 1/2: 39.9 -> 40
+    assert orc.default_maxit(500, 2000, 1e-12) == 400
+    assert orc.default_maxit(100, 400, 1e-10) == 340  # 33.2 -> 34
+    assert orc.default_maxit(2000, 8000, 1e-12) == 400
+    for n, d, tol in [(50, 200, 1e-12), (300, 1200, 1e-8), (64, 1000, 1e-14)]:
+        k = orc.default_maxit(n, d, tol) // 10
+        assert np.sqrt(n / d) ** k <= tol < np.sqrt(n / d) ** (k - 1)
