@@ -50,3 +50,50 @@ def test_create_fails_loudly_without_gpu(libpath):
     import paper_2506_03070_gb300 as P
     with pytest.raises(P.LsqError):
         P.Context(0)
+
+
+def _c_kind(t):
+    t = t.strip()
+    if "*" in t:
+        return "ptr"
+    t = re.sub(r"\bconst\b", "", t).split()[0]
+    return {"double": "f64", "uint64_t": "u64", "size_t": "u64", "int64_t": "i64", "lsq_ticket": "i64",
+            "int32_t": "i32", "int": "i32", "lsq_status": "i32"}[t]
+
+
+def _py_kind(ct):
+    if ct is None:
+        return "i32"  # ctypes' default return type
+    if ct in (ctypes.c_void_p, ctypes.c_char_p) or hasattr(ct, "_type_") and isinstance(ct._type_, type):
+        return "ptr"
+    size, signed = ctypes.sizeof(ct), ct(-1).value == -1 if ct is not ctypes.c_double else None
+    if ct is ctypes.c_double:
+        return "f64"
+    return {(8, True): "i64", (8, False): "u64", (4, True): "i32", (4, False): "u32"}[(size, signed)]
+
+
+def _prototypes():
+    src = open(os.path.join(ROOT, "include", "lsq.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for ret, name, args in re.findall(r"^([A-Za-z_][\w ]*?\**)\s*\b(lsq_[a-z_0-9]+)\(([^)]*)\);", src, flags=re.M):
+        params = [a for a in (p.strip() for p in args.split(",")) if a and a != "void"]
+        # drop the parameter name: everything up to the last identifier
+        kinds = [_c_kind(re.sub(r"\b\w+$", "", p) if not p.endswith("*") else p) for p in params]
+        out[name] = (_c_kind(ret), kinds)
+    return out
+
+
+def test_binding_argtypes_match_the_prototypes(libpath):
+    """Every entry point the binding calls is declared to ctypes with the
+    header's parameter kinds (pointer, 32/64-bit integer, double), so no
+    argument is truncated or passed in the wrong register."""
+    import paper_2506_03070_gb300 as P
+    L = P.load(libpath)
+    protos = _prototypes()
+    assert set(protos) == set(_declared())
+    for name, (ret, kinds) in protos.items():
+        fn = getattr(L, name)
+        assert fn.argtypes is not None, f"{name}: no argtypes in the binding"
+        assert [_py_kind(a) for a in fn.argtypes] == kinds, name
+        assert _py_kind(fn.restype) == ret, name
