@@ -50,12 +50,26 @@ typedef int32_t lsq_status;
 #define LSQ_ERR_TIMEOUT (-8)     /* a device-side wait gave up; the context stays usable */
 #define LSQ_ERR_NONFINITE (-9)   /* A or b holds NaN or Inf */
 #define LSQ_ERR_UNSUPPORTED (-10) /* shape/precision combination not built */
+#define LSQ_ERR_ACCURACY (-11)   /* the final accuracy pass's backward-error bound exceeds the
+                                    gate (lsq_opts.gate); x still holds the solution */
 
-/* Arithmetic of the sketch and of the QR. LSQR matvecs, residuals and
- * recurrences are FP64-accurate in both forms. */
+/* Arithmetic of the sketch and of the QR.  In both forms A, b and x stay FP64
+ * in memory, the LSQR recurrences (Givens scalars, x, w, v) are FP64, and the
+ * final accuracy pass (r = b - A x, A^T r, backward errors) runs in native
+ * FP64.  The LSQR passes over A form A v and A^T u in double-float arithmetic
+ * on the FP32/integer pipes (each FP64 entry split exactly into two floats
+ * holding its top 47 significant bits, products exact, sums as float pairs:
+ * relative matvec error about 1e-14 against 1e-16 in FP64), unless
+ * LSQ_FLAG_NATIVE_FP64 asks for the FP64 pipe (n <= 512).  The
+ * pair image is taken of A 2^-s, b 2^-t with exact power-of-two shifts s, t
+ * chosen from the largest entries, so any finite FP64 data is in range; only
+ * entries below 2^-103 of the largest entry of A (or b) are flushed. */
 typedef enum {
   LSQ_PREC_FP64 = 0,  /* sketch accumulated and factored in FP64 */
-  LSQ_PREC_MIXED = 1  /* sketch accumulated and factored in FP32 */
+  LSQ_PREC_MIXED = 1  /* sketch accumulated in FP32 (compensated: every atomic add's exact
+                         rounding error is accumulated in a second FP32 array, so the sum
+                         matches the FP64 sketch to about u_fp32^2 sqrt(terms per entry)),
+                         rounded once to FP32 and factored in FP32 */
 } lsq_prec;
 
 typedef enum { LSQ_MEM_DEVICE = 0, LSQ_MEM_HOST = 1 } lsq_mem;
@@ -84,6 +98,12 @@ typedef struct {
   int64_t maxit;  /* LSQR iteration cap; <= 0 selects 10*ceil(log(tol)/log(sqrt(n/d))) */
   int32_t flags;  /* LSQ_FLAG_* */
   int32_t reserved;
+  double gate;    /* accuracy gate: the solve returns LSQ_ERR_ACCURACY when the final accuracy
+                     pass finds min(backward_error_ne, backward_error_pre) above it.  0 selects
+                     max(1e-10, tol); < 0 disables the gate.  Both bounds are computed in
+                     FP64 from r = b - A x (see lsq_info); backward_error_ne is Stewart's
+                     rigorous bound, backward_error_pre bounds the Karlson-Walden estimate
+                     up to the sketch's distortion.  Not applied with LSQ_FLAG_NO_CHECK. */
 } lsq_opts;
 
 #define LSQ_FLAG_TIMING 1      /* record per-phase device times in lsq_info */
@@ -108,6 +128,9 @@ typedef struct {
   int32_t precond_fallback;  /* 1: the mixed form's preconditioner stalled LSQR and the
                                 plain form solved the problem again */
   float t_sketch_ms, t_precond_ms, t_lsqr_ms, t_check_ms, t_h2d_ms, t_d2h_ms;
+  /* t_lsqr_ms (LSQ_FLAG_TIMING): LSQR and the accuracy pass (one kernel);
+   * t_check_ms (always when the pass ran): the accuracy pass alone, from the
+   * device clock (%globaltimer) */
   /* lsq_submit / lsq_poll only: host monotonic clock (CLOCK_MONOTONIC) in
    * seconds when the request was submitted, handed to the device, and seen
    * complete; the number of blocks that solved it together and how long its
@@ -121,7 +144,9 @@ typedef struct {
 } lsq_info;
 
 /* Context on `device` with a workspace budget of hbm_budget_bytes (0 = 90% of
- * the device's free memory at creation). */
+ * the device's free memory at creation).  Device-side waits (grid barriers,
+ * bulk-copy completions) of the context's synchronous calls give up after
+ * 20 s (LSQ_ERR_TIMEOUT) unless lsq_set_wait_limit sets another limit. */
 lsq_status lsq_create(lsq_ctx** out, int device, size_t hbm_budget_bytes);
 lsq_status lsq_destroy(lsq_ctx* ctx);
 const char* lsq_last_error(const lsq_ctx* ctx);
@@ -144,8 +169,10 @@ lsq_status lsq_sketch_indices(lsq_ctx* ctx, uint64_t seed, int64_t row0, int64_t
 /* Y = S [A | b]  (Algorithm 1 "Form Y = SA"; S never stored).
  * A: device, m x n (lda >= n); b: device m or NULL.
  * Y: device, d x ldy row-major, ldy >= n + (b != NULL); FP64 (prec FP64) or
- * FP32 (prec MIXED).  Y is overwritten.  Errors: LSQ_ERR_ARG, LSQ_ERR_SKETCH,
- * LSQ_ERR_NONFINITE (A or b not finite). */
+ * FP32 (prec MIXED; compensated accumulation, rounded once to FP32, when
+ * ldy % 4 == 0 and Y is 16-byte aligned; plain FP32 accumulation otherwise).
+ * Y is overwritten.  Errors: LSQ_ERR_ARG, LSQ_ERR_SKETCH, LSQ_ERR_NONFINITE
+ * (A or b not finite). */
 lsq_status lsq_sketch(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d,
                       int32_t zeta, uint64_t seed, int32_t prec, void* Y, int64_t ldy, void* stream);
 
@@ -184,6 +211,18 @@ int64_t lsq_d_from_model(int64_t m, int64_t n, double tol, double t_iter_per_row
 /* Principal branch W0 of the Lambert W function on [-1/e, inf) (NaN outside). */
 double lsq_lambert_w0(double x);
 
+/* Limit of every device-side wait of this context's later synchronous calls
+ * and of serving requests staged after the call (0 < seconds <= 4000; 0
+ * restores the built-in 20 s).  A wait that runs out raises LSQ_ERR_TIMEOUT:
+ * every block of the launch leaves at its next barrier, bulk copies already
+ * issued are waited for, and the context stays usable. */
+lsq_status lsq_set_wait_limit(lsq_ctx* ctx, double seconds);
+/* Self-test of that mechanism (no counterpart in the paper): kind 0 launches
+ * a grid barrier of two co-resident blocks that expects three arrivals, kind 1
+ * an mbarrier phase that nothing completes; both must give up after the wait
+ * limit.  Returns LSQ_ERR_TIMEOUT when the wait gave up as designed. */
+lsq_status lsq_selftest_wait(lsq_ctx* ctx, int32_t kind, void* stream);
+
 #define LSQ_QR_AUTO 0
 #define LSQ_QR_UNBLOCKED 1
 #define LSQ_QR_BLOCKED 2
@@ -219,10 +258,9 @@ lsq_status lsq_hbm(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t 
 
 /* Accuracy of a candidate solution: one pass over A computing r = b - A x,
  * A^T r, ||A||_F and the two backward-error bounds of lsq_info (M may be NULL;
- * then backward_error_pre is 0).  All device pointers.  For n <= 512 the pass
- * runs on the FP64 pipe; wider rows are summed in double-float arithmetic on
- * A's entries split to 47 significant bits, which moves the reported backward
- * error by at most 2^-47 (it is the backward error for A + E, |E| <= 2^-47 |A|). */
+ * then backward_error_pre is 0), all in native FP64 (one warp per row for
+ * n <= 512, PW warps sharing a row in column panels above).  All device
+ * pointers.  No gate: the bounds are reported, not judged. */
 lsq_status lsq_check(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
                      const double* x, const double* M, lsq_info* info, void* stream);
 
@@ -232,9 +270,11 @@ lsq_status lsq_check(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_
  * a memory plan fixed at start-up -- and so cannot create an lsq_ctx: it takes
  * no context and calls no allocator.  Its scratch is one static device array
  * of about 4.1 MB that every GPU loading the library keeps until the process
- * exits.  Limits: n <= 512 (otherwise LSQ_ERR_ARG, nothing launched).  The
- * first call on a device looks up that array's device address (with the
- * device current); make that first call before any stream capture.  All calls
+ * exits.  Limits: n <= 512 (otherwise LSQ_ERR_ARG, nothing launched); a
+ * device whose co-resident grid for the pass would exceed the array's 512
+ * per-block rows returns LSQ_ERR_UNSUPPORTED.  The first call on a device
+ * (and driver context) looks up that array's device address (with the device
+ * current); make that first call before any stream capture.  All calls
  * on a device share the array: calls whose GPU work overlaps (other streams,
  * other host threads) race and must be serialised by the caller.  Runs on the
  * current device and `stream`, synchronises `stream`, fills the accuracy
@@ -246,12 +286,14 @@ lsq_status lsq_check_noalloc(const double* A, int64_t m, int64_t n, int64_t lda,
 /* Algorithm 1 end to end: sketch, precondition, LSQR, accuracy pass.
  * x: n doubles, device memory for LSQ_MEM_DEVICE problems, host memory for
  * LSQ_MEM_HOST problems.  info may be NULL.
- * prec = LSQ_PREC_MIXED accumulates the sketch and factors it in FP32; that
- * preconditioner is good while cond(A) * 6e-8 * sqrt(m zeta / d) << 1.  The
- * mixed LSQR is capped at twice the iterations the Sec. 4.3 rate estimate
- * predicts (2 ceil(log(tol)/log(sqrt(n/d))) + 5); if it stalls, the problem is
- * solved again in the plain form (info->precond_fallback = 1) unless
- * LSQ_FLAG_NO_FALLBACK is set. */
+ * prec = LSQ_PREC_MIXED accumulates the sketch in FP32 (compensated) and
+ * factors it in FP32; the preconditioner then carries FP32 rounding, good while
+ * cond(A) * 6e-8 * sqrt(n) stays below about one.  The mixed LSQR is capped at
+ * twice the iterations the Sec. 4.3 rate estimate predicts
+ * (2 ceil(log(tol)/log(sqrt(n/d))) + 5); if it stalls, fails the accuracy
+ * gate, or max|A| or max|b| lies outside [2^-60, 2^101) (the FP32 sketch's
+ * safe range), the problem is solved again in the plain form
+ * (info->precond_fallback = 1) unless LSQ_FLAG_NO_FALLBACK is set. */
 lsq_status lsq_solve(lsq_ctx* ctx, const lsq_problem* problem, const lsq_opts* opts, double* x, lsq_info* info,
                      void* stream);
 
@@ -318,8 +360,9 @@ lsq_status lsq_solve_batch(lsq_ctx* ctx, const lsq_batch_item* items, int64_t co
  * (and fills info), after which the ticket is gone.
  *
  * Behind it runs a persistent request loop: one cooperative kernel keeps
- * every block of the GPU resident and takes requests from a queue in mapped
- * host memory as they arrive.  A request is solved by a group of G blocks
+ * every block of the GPU resident and takes requests from a ring in device
+ * memory (filled by copy-engine copies from the host; completion records are
+ * in mapped host memory) as they arrive.  A request is solved by a group of G blocks
  * (G from the problem's size: 1 for small problems, up to the whole grid for
  * the largest), which claim it in arrival order, so requests that arrive
  * while others are on the GPU start as soon as blocks free up and run beside

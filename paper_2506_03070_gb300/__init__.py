@@ -24,8 +24,8 @@ LIB_PATH = os.path.join(_HERE, "liblsq.so")
 LSQ_OK, LSQ_PENDING = 0, 1
 STATUS = {0: "LSQ_OK", 1: "LSQ_PENDING", -1: "LSQ_ERR_ARG", -2: "LSQ_ERR_CUDA", -3: "LSQ_ERR_OOM",
           -4: "LSQ_ERR_BUDGET", -5: "LSQ_ERR_SKETCH", -6: "LSQ_ERR_RANK", -7: "LSQ_ERR_NOCONV",
-          -8: "LSQ_ERR_TIMEOUT", -9: "LSQ_ERR_NONFINITE", -10: "LSQ_ERR_UNSUPPORTED"}
-LSQ_ERR_ARG, LSQ_ERR_NOCONV = -1, -7
+          -8: "LSQ_ERR_TIMEOUT", -9: "LSQ_ERR_NONFINITE", -10: "LSQ_ERR_UNSUPPORTED", -11: "LSQ_ERR_ACCURACY"}
+LSQ_ERR_ARG, LSQ_ERR_NOCONV, LSQ_ERR_TIMEOUT, LSQ_ERR_ACCURACY = -1, -7, -8, -11
 PREC_FP64, PREC_MIXED = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
 FLAG_TIMING, FLAG_NO_CHECK, FLAG_NATIVE_FP64, FLAG_NO_IMAGE, FLAG_NO_FALLBACK = 1, 2, 4, 8, 16
@@ -35,7 +35,7 @@ EXPORTS = ("lsq_create", "lsq_destroy", "lsq_last_error", "lsq_status_string", "
            "lsq_sketch_indices", "lsq_sketch", "lsq_precond", "lsq_lsqr", "lsq_check", "lsq_solve",
            "lsq_check_noalloc", "lsq_solve_batch", "lsq_submit", "lsq_poll", "lsq_serve_config",
            "lsq_serve_stats_get", "lsq_set_qr_mode", "lsq_choose_d", "lsq_d_from_model", "lsq_lambert_w0",
-           "lsq_hbm", "lsq_solve_csr")
+           "lsq_hbm", "lsq_solve_csr", "lsq_set_wait_limit", "lsq_selftest_wait")
 QR_AUTO, QR_UNBLOCKED, QR_BLOCKED = 0, 1, 2
 
 
@@ -53,7 +53,7 @@ class Problem(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int64), ("zeta", ctypes.c_int32), ("prec", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("tol", ctypes.c_double), ("maxit", ctypes.c_int64), ("flags", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("gate", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -148,7 +148,9 @@ def load(path: str = LIB_PATH):
     L.lsq_lambert_w0.argtypes = [f64]
     L.lsq_lambert_w0.restype = f64
     L.lsq_serve_stats_get.argtypes = [P, ctypes.POINTER(ServeStats)]
-    for name in ("lsq_create", "lsq_destroy", "lsq_sketch_indices", "lsq_sketch", "lsq_precond", "lsq_lsqr",
+    L.lsq_set_wait_limit.argtypes = [P, f64]
+    L.lsq_selftest_wait.argtypes = [P, i32, P]
+    for name in ("lsq_set_wait_limit", "lsq_selftest_wait", "lsq_create", "lsq_destroy", "lsq_sketch_indices", "lsq_sketch", "lsq_precond", "lsq_lsqr",
                  "lsq_check", "lsq_solve", "lsq_submit", "lsq_poll", "lsq_serve_config", "lsq_serve_stats_get"):
         getattr(L, name).restype = i32
     _lib = L
@@ -241,6 +243,15 @@ class Context:
     def lsq_set_qr_mode(self, mode):
         self._check(self.lib.lsq_set_qr_mode(self.h, mode))
 
+    def lsq_set_wait_limit(self, seconds):
+        """Limit of every device-side wait of later calls (0: the built-in 20 s)."""
+        self._check(self.lib.lsq_set_wait_limit(self.h, float(seconds)))
+
+    def lsq_selftest_wait(self, kind, stream=None):
+        """Run a device wait that can never be satisfied (kind 0: grid barrier,
+        1: mbarrier) and return its status (LSQ_ERR_TIMEOUT when it gave up)."""
+        return self.lib.lsq_selftest_wait(self.h, int(kind), _stream(stream))
+
     @property
     def workspace_bytes(self):
         return self.lib.lsq_workspace_bytes(self.h)
@@ -319,7 +330,7 @@ class Context:
         return x, info.as_dict()
 
     def lsq_solve_csr(self, row_ptr, col_idx, values, b, n, d, zeta=8, seed=0, tol=1e-12, maxit=0, flags=0,
-                      stream=None, allow_noconv=False):
+                      stream=None, allow_noconv=False, gate=0.0):
         """Algorithm 1 for a sparse A in CSR form (CUDA tensors: int64 row_ptr,
         int32 col_idx, float64 values, float64 b).  Returns (x, info)."""
         import torch
@@ -335,7 +346,7 @@ class Context:
         _vec(b, m, "b", dev)
         x = torch.empty((n,), dtype=torch.float64, device=b.device)
         pr = CsrProblem(_ptr(row_ptr), _ptr(col_idx), _ptr(values), _ptr(b), m, n, values.numel())
-        op = Opts(d, zeta, PREC_FP64, seed, tol, maxit, flags, 0)
+        op = Opts(d, zeta, PREC_FP64, seed, tol, maxit, flags, 0, gate)
         info = Info()
         st = self.lib.lsq_solve_csr(self.h, ctypes.byref(pr), ctypes.byref(op), _ptr(x), ctypes.byref(info),
                                     _stream(stream))
@@ -366,10 +377,11 @@ class Context:
         return xs, [r.as_dict() for r in res]
 
     def lsq_solve(self, A, b, d, zeta=8, seed=0, tol=1e-12, maxit=0, prec=PREC_FP64, flags=0, x=None, stream=None,
-                  allow_noconv=False):
+                  allow_noconv=False, gate=0.0, allow=None):
         """Algorithm 1 end to end.  A, b: CUDA float64 tensors (device
         problem) or numpy float64 arrays (host problem: copies inside the
-        call).  Returns (x, info dict)."""
+        call).  gate: accuracy gate (0: max(1e-10, tol); < 0: none).  allow:
+        statuses returned instead of raised.  Returns (x, info dict)."""
         import torch
         if isinstance(A, np.ndarray):
             if A.dtype != np.float64 or A.ndim != 2 or A.strides[1] != 8:
@@ -394,17 +406,19 @@ class Context:
                 _vec(x, n, "x", A.device)
             strm = _stream(stream)
         pr = Problem(_ptr(A), _ptr(b), m, n, lda, mem, 0)
-        op = Opts(d, zeta, prec, seed, tol, maxit, flags, 0)
+        op = Opts(d, zeta, prec, seed, tol, maxit, flags, 0, gate)
         info = Info()
         st = self.lib.lsq_solve(self.h, ctypes.byref(pr), ctypes.byref(op), _ptr(x), ctypes.byref(info), strm)
-        self._check(st, allow=(LSQ_OK, LSQ_ERR_NOCONV) if allow_noconv else (LSQ_OK,))
+        if allow is None:
+            allow = (LSQ_OK, LSQ_ERR_NOCONV) if allow_noconv else (LSQ_OK,)
+        self._check(st, allow=allow)
         return x, info.as_dict()
 
     # -- serving -------------------------------------------------------------
     def lsq_serve_config(self, arena_bytes=0, cta_bytes=0.0, max_group=0):
         self._check(self.lib.lsq_serve_config(self.h, arena_bytes, cta_bytes, max_group))
 
-    def lsq_submit(self, A, b, d, zeta=8, seed=0, tol=1e-12, maxit=0, flags=0, x=None, stream=None):
+    def lsq_submit(self, A, b, d, zeta=8, seed=0, tol=1e-12, maxit=0, flags=0, x=None, stream=None, gate=0.0):
         """Queue a problem for the persistent request loop; returns a ticket.
         A, b: CUDA float64 tensors or numpy float64 arrays (host problem).
         They (and x) are kept referenced here until lsq_poll reports the
@@ -433,7 +447,7 @@ class Context:
             else:
                 _vec(x, n, "x", A.device)
         pr = Problem(_ptr(A), _ptr(b), m, n, lda, mem, 0)
-        op = Opts(d, zeta, PREC_FP64, seed, tol, maxit, flags, 0)
+        op = Opts(d, zeta, PREC_FP64, seed, tol, maxit, flags, 0, gate)
         t = ctypes.c_int64()
         self._check(self.lib.lsq_submit(self.h, ctypes.byref(pr), ctypes.byref(op), _ptr(x), ctypes.byref(t),
                                         _stream(stream)))

@@ -84,12 +84,22 @@ lsq_status ensure_ws(lsq_ctx* ctx, size_t bytes) {
 }
 
 lsq_status status_from_bits(lsq_ctx* ctx, uint32_t bits) {
-  if (bits & DS_TIMEOUT) return fail(ctx, LSQ_ERR_TIMEOUT, "a device-side grid barrier timed out");
+  if (bits & DS_TIMEOUT) return fail(ctx, LSQ_ERR_TIMEOUT, "a device-side wait gave up (grid barrier or bulk copy)");
   if (bits & DS_NONFINITE) return fail(ctx, LSQ_ERR_NONFINITE, "A or b contains NaN or Inf");
   if (bits & DS_SKETCH) return fail(ctx, LSQ_ERR_SKETCH, "rejection sampling exceeded its round cap");
   if (bits & DS_RANK) return fail(ctx, LSQ_ERR_RANK, "R has a negligible diagonal entry (rank-deficient sketch)");
   if (bits & DS_NOCONV) return fail(ctx, LSQ_ERR_NOCONV, "LSQR reached maxit before the stopping test held");
+  if (bits & DS_ACCURACY)
+    return fail(ctx, LSQ_ERR_ACCURACY, "the accuracy pass's backward-error bound exceeds the gate (x is written)");
   return LSQ_OK;
+}
+
+// Gate of the accuracy pass for a solve with tolerance tol: the gate in
+// opts when set (> 0; < 0 disables it), else max(1e-10, tol).
+double solve_gate(double tol, double opt_gate) {
+  if (opt_gate < 0.0) return 0.0;
+  if (opt_gate > 0.0) return opt_gate;
+  return std::max(1e-10, tol);
 }
 
 lsq_status check_ctx(lsq_ctx* ctx) {
@@ -106,9 +116,13 @@ lsq_status check_sketch_args(lsq_ctx* ctx, int64_t d, int32_t zeta) {
   return LSQ_OK;
 }
 
-// reset the small device words on the stream
+// reset the small device words on the stream, except the barrier's wait
+// limit (a context setting, lsq_set_wait_limit)
 lsq_status reset_small(lsq_ctx* ctx, cudaStream_t st) {
-  CK(cudaMemsetAsync(ctx->d_status, 0, kSmallBytes, st));
+  char* base = reinterpret_cast<char*>(ctx->d_status);
+  const size_t lim = reinterpret_cast<char*>(&ctx->d_bar->limit_us) - base;
+  CK(cudaMemsetAsync(base, 0, lim, st));
+  CK(cudaMemsetAsync(base + lim + sizeof(uint32_t), 0, kSmallBytes - lim - sizeof(uint32_t), st));
   return LSQ_OK;
 }
 
@@ -181,12 +195,15 @@ void fill_info(lsq_info* info, const double* out, lsq_status st, int32_t rounds)
   info->xnorm = out[OUT_XNORM];
   info->bnorm = out[OUT_BNORM];
   info->sketch_rounds_max = rounds;
+  if (out[OUT_T_CHECK1] > out[OUT_T_CHECK0] && out[OUT_T_CHECK0] > 0.0)
+    info->t_check_ms = (float)((out[OUT_T_CHECK1] - out[OUT_T_CHECK0]) * 1e-6);
 }
 
 // Launch the LSQR / check kernel (native: FP64-pipe pass; else double-float pass).
 lsq_status run_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int n, int64_t lda, const double* b, const double* M,
                     const double* Mt, double* x, double tol, int64_t maxit, int mode, const LsqrWork& w, int grid,
-                    int npad, bool native, cudaStream_t st, double hbm_alpha = 0.0, double hbm_beta = 0.0) {
+                    int npad, bool native, cudaStream_t st, double hbm_alpha = 0.0, double hbm_beta = 0.0,
+                    double gate = 0.0) {
   LsqrParams p;
   p.A = A;
   p.m = m;
@@ -198,8 +215,9 @@ lsq_status run_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int n, int64_t lda
   p.ldi = (n + 1) / 2 * 2;
   p.vec = vec_ok(A, lda);
   p.a_ring = p.vec && (n % 2 == 0);
-  p.check_df = false;
   p.ring_k = 1;
+  p.range = ctx->d_range;
+  p.gate = gate;
   p.M = M;
   p.Mt = Mt;
   p.x = x;
@@ -219,7 +237,7 @@ lsq_status run_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int n, int64_t lda
   p.bar = ctx->d_bar;
   p.status = ctx->d_status;
   p.out = ctx->d_out;
-  CK(cudaMemsetAsync(ctx->d_bar, 0, sizeof(GridBarrier), st));
+  CK(cudaMemsetAsync(&ctx->d_bar->count, 0, sizeof(unsigned int), st));
   CK(lsqr_run(p, vec_ok(A, lda), native, grid, st));
   return LSQ_OK;
 }
@@ -357,6 +375,7 @@ lsq_status lsq_create(lsq_ctx** out, int device, size_t hbm_budget_bytes) {
   ctx->d_max_rounds = reinterpret_cast<int32_t*>(small + 64);
   ctx->d_bar = reinterpret_cast<GridBarrier*>(small + 128);
   ctx->d_out = reinterpret_cast<double*>(small + 256);
+  ctx->d_range = reinterpret_cast<uint32_t*>(small + 1024);
   if (cudaMallocHost(&ctx->h_small, kSmallBytes) != cudaSuccess) {
     cudaFree(small);
     delete ctx;
@@ -398,6 +417,7 @@ const char* lsq_status_string(lsq_status s) {
     case LSQ_ERR_TIMEOUT: return "LSQ_ERR_TIMEOUT";
     case LSQ_ERR_NONFINITE: return "LSQ_ERR_NONFINITE";
     case LSQ_ERR_UNSUPPORTED: return "LSQ_ERR_UNSUPPORTED";
+    case LSQ_ERR_ACCURACY: return "LSQ_ERR_ACCURACY";
     default: return "LSQ_UNKNOWN";
   }
 }
@@ -460,6 +480,32 @@ lsq_status lsq_choose_d(lsq_ctx* ctx, int64_t m, int64_t n, double tol, int64_t*
   return LSQ_OK;
 }
 
+lsq_status lsq_set_wait_limit(lsq_ctx* ctx, double seconds) {
+  lsq_status s;
+  if ((s = check_ctx(ctx)) != LSQ_OK) return s;
+  if (!(seconds >= 0.0) || seconds > 4000.0) return fail(ctx, LSQ_ERR_ARG, "need 0 <= seconds <= 4000");
+  uint32_t us = (uint32_t)std::llround(seconds * 1e6);
+  if (seconds > 0.0 && us == 0) us = 1;
+  // stream-ordered after all earlier work of the device (a synchronous copy)
+  CK(cudaMemcpy(&ctx->d_bar->limit_us, &us, sizeof(us), cudaMemcpyHostToDevice));
+  ctx->wait_limit_us = us;
+  if (ctx->server) server_set_wait_limit(ctx->server, us);
+  return LSQ_OK;
+}
+
+lsq_status lsq_selftest_wait(lsq_ctx* ctx, int32_t kind, void* stream) {
+  lsq_status s;
+  if ((s = check_ctx(ctx)) != LSQ_OK) return s;
+  if (kind != 0 && kind != 1) return fail(ctx, LSQ_ERR_ARG, "kind must be 0 (grid barrier) or 1 (mbarrier)");
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((s = reset_small(ctx, st)) != LSQ_OK) return s;
+  CK(wait_selftest(kind, ctx->d_bar, ctx->d_status, 2, st));
+  uint32_t bits = 0;
+  if ((s = read_small(ctx, st, &bits, nullptr, nullptr)) != LSQ_OK) return s;
+  // the barrier's abort bit stays set until the next launch zeroes the counter
+  return status_from_bits(ctx, bits);
+}
+
 lsq_status lsq_set_qr_mode(lsq_ctx* ctx, int32_t mode) {
   if (!ctx) return LSQ_ERR_ARG;
   if (mode != LSQ_QR_AUTO && mode != LSQ_QR_UNBLOCKED && mode != LSQ_QR_BLOCKED)
@@ -496,12 +542,21 @@ lsq_status lsq_sketch(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64
   if ((s = reset_small(ctx, st)) != LSQ_OK) return s;
   const size_t esz = prec == LSQ_PREC_FP64 ? 8 : 4;
   CK(cudaMemsetAsync(Y, 0, (size_t)d * ldy * esz, st));
-  if (prec == LSQ_PREC_FP64)
+  if (prec == LSQ_PREC_FP64) {
     CK(sketch_apply<double>(A, m, n, lda, b, d, zeta, seed, 0, (double*)Y, ldy, ctx->d_status, ctx->d_max_rounds,
-                            ctx->sms, st));
-  else
+                            nullptr, ctx->sms, st));
+  } else if (ldy % 4 == 0 && (uintptr_t)Y % 16 == 0) {
+    // compensated FP32 accumulation (error terms in workspace), then Y += Ylo
+    if ((s = ensure_ws(ctx, align_up((size_t)d * ldy * sizeof(float)))) != LSQ_OK) return s;
+    float* Ylo = reinterpret_cast<float*>(ctx->ws);
+    CK(cudaMemsetAsync(Ylo, 0, (size_t)d * ldy * sizeof(float), st));
+    CK(sketch_apply_f32c(A, m, n, lda, b, d, zeta, seed, 0, (float*)Y, Ylo, ldy, ctx->d_status, ctx->d_max_rounds,
+                         nullptr, ctx->sms, st));
+    CK(add_lo((float*)Y, Ylo, d * ldy, ctx->sms, st));
+  } else {
     CK(sketch_apply<float>(A, m, n, lda, b, d, zeta, seed, 0, (float*)Y, ldy, ctx->d_status, ctx->d_max_rounds,
-                           ctx->sms, st));
+                           nullptr, ctx->sms, st));
+  }
   uint32_t bits = 0;
   if ((s = read_small(ctx, st, &bits, nullptr, nullptr)) != LSQ_OK) return s;
   return status_from_bits(ctx, bits);
@@ -581,6 +636,8 @@ lsq_status lsq_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t
   Carver cv{ctx->ws};
   LsqrWork w = carve_lsqr(cv, m, ni, npad, grid, image);
   if ((s = reset_small(ctx, st)) != LSQ_OK) return s;
+  // exponent range of A and b for the double-float passes (and a finiteness check)
+  if (!native) CK(range_scan(A, m, n, lda, b, ctx->d_range, ctx->d_status, ctx->sms, st));
   CK(transpose_square(M, ni, w.Mt, st));
   if (x != x0) CK(cudaMemcpyAsync(x, x0, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   if (maxit <= 0) maxit = 1000;
@@ -630,6 +687,7 @@ lsq_status lsq_hbm(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t 
   Carver cv{ctx->ws};
   LsqrWork w = carve_lsqr(cv, m, ni, npad, grid, image);
   if ((s = reset_small(ctx, st)) != LSQ_OK) return s;
+  if (!native) CK(range_scan(A, m, n, lda, b, ctx->d_range, ctx->d_status, ctx->sms, st));
   CK(transpose_square(M, ni, w.Mt, st));
   if (x != x0) CK(cudaMemcpyAsync(x, x0, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   if (maxit <= 0) maxit = 1000;
@@ -637,7 +695,7 @@ lsq_status lsq_hbm(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t 
   const double e2 = eta_hat * eta_hat;
   const int hmode = (flags & LSQ_FLAG_NO_CHECK) ? 4 : 3;
   if ((s = run_lsqr(ctx, A, m, ni, lda, b, M, w.Mt, x, tol, maxit, hmode, w, grid, npad, native, st,
-                    (1.0 - e2) * (1.0 - e2), e2)) != LSQ_OK)
+                    (1.0 - e2) * (1.0 - e2), e2, solve_gate(tol, 0.0))) != LSQ_OK)
     return s;
   uint32_t bits = 0;
   double out[kOutSlots];
@@ -656,7 +714,8 @@ lsq_status lsq_check(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_
   if (n > kLsqrMaxN) return fail(ctx, LSQ_ERR_UNSUPPORTED, "check kernels built for n <= 4096");
   cudaStream_t st = (cudaStream_t)stream;
   const int ni = (int)n, npad = (int)((n + 31) / 32 * 32);
-  // FP64 pass for n <= 512; wider rows go through the pair-arithmetic panel pass
+  // native FP64 pass: one warp per row for n <= 512, the panel kernel's
+  // FP64 check pass for wider rows
   const bool native = lsqr_native_ok(n);
   const int grid = lsqr_grid(ni, vec_ok(A, lda), native, ctx->sms);
   if (grid < 1) return fail(ctx, LSQ_ERR_CUDA, "no launchable check configuration");
@@ -720,6 +779,8 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
       *xd = x;
     }
     *Y = cv.take<char>((size_t)d * ldy * yes);
+    // mixed form: the compensated sketch's error terms, same layout as Y
+    pb->Ylo = o->prec == LSQ_PREC_MIXED ? cv.take<float>((size_t)d * ldy) : nullptr;
     pb->W = cv.take<double>((size_t)ncol * d);
     pb->rdiag = cv.take<double>(npad);
     pb->blk = cv.take<char>(precond_blocked_bytes(d, n));
@@ -782,12 +843,18 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
   if (timing) CK(cudaEventRecord(ev[1], st));
   if ((s = reset_small(ctx, st)) != LSQ_OK) return s;
   CK(cudaMemsetAsync(Y, 0, (size_t)d * ldy * yes, st));
-  if (o->prec == LSQ_PREC_FP64)
+  // the sketch also records the exponent range of A and b (ctx->d_range) for
+  // the double-float LSQR passes
+  if (o->prec == LSQ_PREC_FP64) {
     CK(sketch_apply<double>(A, m, n, lda_dev, b, d, o->zeta, o->seed, 0, (double*)Y, ldy, ctx->d_status,
-                            ctx->d_max_rounds, ctx->sms, st));
-  else
-    CK(sketch_apply<float>(A, m, n, lda_dev, b, d, o->zeta, o->seed, 0, (float*)Y, ldy, ctx->d_status,
-                           ctx->d_max_rounds, ctx->sms, st));
+                            ctx->d_max_rounds, ctx->d_range, ctx->sms, st));
+  } else {
+    // compensated FP32 accumulation: Y + Ylo, summed once into the QR's copy
+    CK(cudaMemsetAsync(const_cast<void*>(pb.Ylo), 0, (size_t)d * ldy * sizeof(float), st));
+    CK(sketch_apply_f32c(A, m, n, lda_dev, b, d, o->zeta, o->seed, 0, (float*)Y,
+                         static_cast<float*>(const_cast<void*>(pb.Ylo)), ldy, ctx->d_status, ctx->d_max_rounds,
+                         ctx->d_range, ctx->sms, st));
+  }
   if (timing) CK(cudaEventRecord(ev[2], st));
   if (o->prec == LSQ_PREC_FP64)
     CK(precond<double>((const double*)Y, d, n, ldy, 1, R, M, xd, pb, ctx->sms, st));
@@ -799,6 +866,21 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
   int32_t rounds = 0;
   double out[kOutSlots] = {0};
   if ((s = read_small(ctx, st, &bits, &rounds, nullptr)) != LSQ_OK) return s;
+  if (o->prec == LSQ_PREC_MIXED && !bits) {
+    // the FP32 sketch needs max|A| and max|b| well inside the FP32 range
+    // (sums of many terms must not overflow, entries far below the largest
+    // may flush): exponents in [-60, 100], else the plain form solves it
+    const char* h = static_cast<const char*>(ctx->h_small);
+    const size_t off = (const char*)ctx->d_range - (const char*)ctx->d_status;
+    uint32_t rg[2];
+    std::memcpy(rg, h + off, sizeof(rg));
+    for (uint32_t w : rg) {
+      const int e = (int)(w >> 20) - 1023;
+      if (w && (e < -60 || e > 100))
+        return fail(ctx, LSQ_ERR_UNSUPPORTED, "mixed form: A or b outside the FP32 sketch's range (|max| exponent " +
+                                                  std::to_string(e) + ")");
+    }
+  }
   if (bits) {
     s = status_from_bits(ctx, bits);
     if (info) {
@@ -812,7 +894,7 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
   // heavy-ball momentum: App. C.2 parameters with the distortion estimate sqrt(n/d)
   const double e2 = (double)n / (double)d;
   if ((s = run_lsqr(ctx, A, m, ni, lda_dev, b, M, lw.Mt, xd, o->tol, maxit, mode, lw, grid, npad, native, st,
-                    hbm ? (1.0 - e2) * (1.0 - e2) : 0.0, hbm ? e2 : 0.0)) != LSQ_OK)
+                    hbm ? (1.0 - e2) * (1.0 - e2) : 0.0, hbm ? e2 : 0.0, solve_gate(o->tol, o->gate))) != LSQ_OK)
     return s;
   if (timing) CK(cudaEventRecord(ev[4], st));
   if (host) CK(cudaMemcpyAsync(x, xd, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
@@ -867,7 +949,10 @@ static lsq_status lsq_solve_d(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opt
   const int64_t cap = 2 * (default_maxit(pr->n, o->d, o->tol) / 10) + 5;
   om.maxit = cap < full ? cap : full;
   lsq_status s = solve_once(ctx, pr, &om, x, info, stream);
-  if (s != LSQ_ERR_NOCONV || om.maxit == full) return s;
+  // fall back to the plain form when the FP32 preconditioner stalled LSQR, the
+  // accuracy gate failed, or the data is outside the FP32 sketch's range
+  const bool retry = s == LSQ_ERR_ACCURACY || s == LSQ_ERR_UNSUPPORTED || (s == LSQ_ERR_NOCONV && om.maxit < full);
+  if (!retry) return s;
   lsq_opts op = *o;
   op.prec = LSQ_PREC_FP64;
   s = solve_once(ctx, pr, &op, x, info, stream);
@@ -977,11 +1062,12 @@ lsq_status lsq_solve_csr(lsq_ctx* ctx, const lsq_csr_problem* pr, const lsq_opts
   const double e2 = (double)n / (double)d;
   p.hbm_alpha = hbm ? (1.0 - e2) * (1.0 - e2) : 0.0;
   p.hbm_beta = hbm ? e2 : 0.0;
+  p.gate = solve_gate(o.tol, o.gate);
   p.bar = ctx->d_bar;
   p.status = ctx->d_status;
   p.out = ctx->d_out;
   CK(transpose_square(M, ni, lw.Mt, st));
-  CK(cudaMemsetAsync(ctx->d_bar, 0, sizeof(GridBarrier), st));
+  CK(cudaMemsetAsync(&ctx->d_bar->count, 0, sizeof(unsigned int), st));
   CK(lsqr_csr_run(p, pr->row_ptr, pr->col_idx, pr->values, grid, lanes, st));
   if (timing) CK(cudaEventRecord(ev[3], st));
   if ((s = read_small(ctx, st, &bits, nullptr, out)) != LSQ_OK) return s;

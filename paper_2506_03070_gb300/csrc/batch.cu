@@ -38,7 +38,7 @@ struct BatchParams {
   char* ws;
   size_t slab;  // bytes of workspace per block
   // slab layout (byte offsets)
-  size_t oY, oW, oR, oM, oMt, oRd, oU, oVec, oGpart, oPart, oImg;
+  size_t oY, oW, oR, oM, oMt, oRd, oU, oVec, oGpart, oPart, oImg, oRange;
   int npad_max;
   double tol;
   int64_t maxit;  // <= 0: per-problem default
@@ -82,9 +82,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(BatchParams bp) {
     double* rdiag = reinterpret_cast<double*>(slab + bp.oRd);
     double* vec = reinterpret_cast<double*>(slab + bp.oVec);
 
-    const Group g{0, 1, bp.bar, status};
+    uint32_t* range = reinterpret_cast<uint32_t*>(slab + bp.oRange);
+    const Group g{0, 1, bp.bar, status, range};
     // ---- sketch Y = S [A | b]
     zero_group(Y, (int64_t)d * ldy, g);
+    if (threadIdx.x < 2) range[threadIdx.x] = 0u;
     __syncthreads();
     sketch_group(it.A, it.b, it.m, n, it.lda, d, it.zeta, it.seed, Y, ldy, reinterpret_cast<int32_t*>(s_ring), s_sgn,
                  g);
@@ -113,7 +115,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(BatchParams bp) {
     p.ldi = (n + 1) / 2 * 2;
     p.vec = ((uintptr_t)it.A % 16 == 0) && (it.lda % 2 == 0);
     p.a_ring = p.vec && (n % 2 == 0);
-    p.check_df = true;
+    p.range = range;
+    p.gate = bp.mode == 0 ? fmax(1e-10, bp.tol) : 0.0;
     p.M = M;
     p.Mt = Mt;
     p.x = it.x;
@@ -202,6 +205,7 @@ BatchLayout batch_layout(int64_t m_max, int n_max, int d_max) {
   L.oGpart = o; o += al((size_t)kWarps * npad * 8);
   L.oPart = o; o += al(4 * 8);
   L.oImg = o; o += al((size_t)m_max * ldi * 8);
+  L.oRange = o; o += al(2 * 4);
   L.slab = o;
   L.npad_max = npad;
   return L;
@@ -239,6 +243,7 @@ cudaError_t batch_launch(const void* items_dev, const int32_t* order_dev, int co
   bp.oGpart = L.oGpart;
   bp.oPart = L.oPart;
   bp.oImg = L.oImg;
+  bp.oRange = L.oRange;
   bp.npad_max = L.npad_max;
   bp.tol = tol;
   bp.maxit = maxit;

@@ -17,11 +17,13 @@ enum : uint32_t {
   DS_RANK = 8u,       // zero/negligible diagonal of R
   DS_NOCONV = 16u,    // LSQR reached maxit
   DS_CSR = 32u,       // malformed CSR structure (row offsets or column indices)
+  DS_ACCURACY = 64u,  // the accuracy pass's backward-error bound exceeded the gate
 };
 
 constexpr int kMaxZeta = 64;
 constexpr int kMaxRounds = 10000;
-// A grid barrier gives up after this many nanoseconds of waiting.
+// A device wait (grid barrier, bulk-copy mbarrier) gives up after this many
+// nanoseconds unless the barrier word carries its own limit (limit_us).
 constexpr unsigned long long kBarrierTimeoutNs = 20ull * 1000ull * 1000ull * 1000ull;
 
 // ---------------------------------------------------------------------------
@@ -70,21 +72,28 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // one counter.  Thread 0 of each block arrives with one release atomic
 // (count += 1) and polls the same word with acquire loads until the round's
 // nblocks arrivals are in: target = (arrival / nblocks + 1) * nblocks.  The
-// counter is zeroed by the host before a launch and advances by nblocks per
-// barrier, so it stays a multiple of nblocks between barriers (a launch with a
+// host zeroes `count` before a launch and it advances by nblocks per barrier,
+// so it stays a multiple of nblocks between barriers (a launch with a
 // different block count needs it zeroed again).  Abort is the top bit of the
 // same word, seen by every arrival and poll without an extra load.  Every wait
-// is bounded by kBarrierTimeoutNs; on timeout the block raises DS_TIMEOUT and
-// the abort bit, and every block leaves at its next barrier.  Returns false
-// when the caller must exit.
+// is bounded: by limit_us microseconds when the host set it (a run-time
+// setting that outlives the zeroing of `count`), else by kBarrierTimeoutNs.
+// On timeout the block raises DS_TIMEOUT and the abort bit, and every block
+// leaves at its next barrier.  Returns false when the caller must exit.
 // ---------------------------------------------------------------------------
 struct GridBarrier {
-  unsigned int count;  // arrivals (low 31 bits) | kBarrierAbort
-  unsigned int gen;    // unused
-  unsigned int abort;  // unused (kept for layout)
-  unsigned int pad;
+  unsigned int count;     // arrivals (low 31 bits) | kBarrierAbort
+  unsigned int limit_us;  // wait limit of every wait tied to this barrier; 0 = kBarrierTimeoutNs
+  unsigned int pad[2];
 };
 constexpr unsigned int kBarrierAbort = 0x80000000u;
+
+// Wait limit (ns) of the waits tied to `bar` (bulk-copy waits of a pass read
+// it once per pass).
+__device__ __forceinline__ unsigned long long wait_limit_ns(const GridBarrier* bar) {
+  const unsigned int us = bar ? *(volatile const unsigned int*)&bar->limit_us : 0u;
+  return us ? (unsigned long long)us * 1000ull : kBarrierTimeoutNs;
+}
 
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
   unsigned int v;
@@ -115,13 +124,13 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, uint32_t* status, un
       const unsigned int target = (a / nblocks + 1u) * nblocks;
       unsigned int v = ld_acquire_u32(&bar->count);
       if (!(v & kBarrierAbort) && (int)(v - target) < 0) {
-        const unsigned long long t0 = globaltimer_ns();
+        const unsigned long long t0 = globaltimer_ns(), limit = wait_limit_ns(bar);
         unsigned int spins = 0;
         for (;;) {
           __nanosleep(20);
           v = ld_acquire_u32(&bar->count);
           if ((v & kBarrierAbort) || (int)(v - target) >= 0) break;
-          if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+          if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > limit) {
             atomicOr(status, DS_TIMEOUT);
             barrier_abort(bar);
             v = kBarrierAbort;

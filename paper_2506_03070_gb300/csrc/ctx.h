@@ -9,6 +9,8 @@ namespace lsq {
 struct Server;
 // Serving side (serve.cu): stop and free a context's server, if any.
 void server_destroy(Server* s);
+// Wait limit written into the control words of requests staged from now on.
+void server_set_wait_limit(Server* s, uint32_t limit_us);
 }  // namespace lsq
 
 struct lsq_ctx {
@@ -24,6 +26,8 @@ struct lsq_ctx {
   int32_t* d_max_rounds = nullptr;
   lsq::GridBarrier* d_bar = nullptr;
   double* d_out = nullptr;
+  uint32_t* d_range = nullptr;  // [2] exponent maxima of A and b (pass_scale)
+  uint32_t wait_limit_us = 0;   // limit of every device wait (0: the built-in 20 s)
   // pinned host mirror of the small words
   void* h_small = nullptr;
   // batched solves: tuned LSQR pass shapes per n-range

@@ -8,12 +8,17 @@
 //
 //  - split2(a): a = hi + mid + (6 lowest mantissa bits, dropped), by bit
 //    manipulation: hi carries the top 24 significant bits (truncated), mid the
-//    next 23.  Relative representation error < 2^-47.  Exact zero and
-//    |a| < 2^-103 map to (0, 0); finite |a| must be < 2^128 (the caller keeps
-//    the data in range; A's entries are checked to be finite by the sketch).
+//    next 23 (47 significant bits).  Relative representation error < 2^-46.  Exact zero and
+//    |a| < 2^-103 map to (0, 0); finite |a| must be < 2^128.
+//  - split2s(a, s): the same split of a * 2^-s for any FP64 exponent shift s,
+//    folded into the exponent re-bias (no rounding).  The passes over A take s
+//    from the largest exponent of A's entries (found while A is first read),
+//    so that max |A 2^-s| lies in [1, 2): nothing overflows the FP32 range, and
+//    only entries below 2^-103 max|A| are flushed to zero (a relative
+//    perturbation of A below 2^-103 sqrt(mn) in the Frobenius norm).
 //  - two_sum (Knuth): s + e = a + b exactly, branch free.
 //  - products: p + e = a*b exactly via one FMA.
-//  - df_add / df_mul: pair arithmetic with relative error ~2^-47.
+//  - df_add / df_mul: pair arithmetic with relative error ~2^-46.
 //
 // Every operation uses the explicitly rounded intrinsics (__fadd_rn, ...), so
 // the compiler cannot contract or reassociate them.
@@ -105,9 +110,43 @@ __device__ __forceinline__ void split2(double a, float& hi, float& mid) {
   mid = __fsub_rn(__uint_as_float(fb), __uint_as_float(pb));
 }
 
+// Exponent shift of split2s: entries are split as a * 2^-s.  thr: the high
+// word's exponent field must reach it (|a| 2^-s >= 2^-103, a nonzero);
+// rebias: subtracted from the shifted word (exponent 1023 + s -> 127).
+struct SplitShift {
+  uint32_t thr, rebias;
+};
+__host__ __device__ __forceinline__ SplitShift split_shift(int s) {
+  int t = 920 + s;  // biased FP64 exponent of 2^(s - 103)
+  if (t < 1) t = 1;  // zeros and FP64 subnormals always flush
+  SplitShift r;
+  r.thr = (uint32_t)t << 20;
+  r.rebias = ((uint32_t)(384 + s) & 511u) << 23;
+  return r;
+}
+
+// split2 of a * 2^-s (see above); the caller keeps max |a 2^-s| < 2^128.
+__device__ __forceinline__ void split2s(double a, float& hi, float& mid, SplitShift sh) {
+  const uint32_t hw = (uint32_t)__double2hiint(a), lw = (uint32_t)__double2loint(a);
+  const uint32_t t = __funnelshift_l(lw, hw, 3) - sh.rebias;
+  const bool ok = (hw & 0x7FF00000u) >= sh.thr;
+  uint32_t hb = (t & 0x7FFFFFFFu) | (hw & 0x80000000u);
+  hb = ok ? hb : 0u;
+  const uint32_t pb = (hb & 0xFF800000u) - 0x0B800000u;
+  uint32_t fb = pb | ((lw >> 6) & 0x7FFFFFu);
+  fb = ok ? fb : pb;
+  hi = __uint_as_float(hb);
+  mid = __fsub_rn(__uint_as_float(fb), __uint_as_float(pb));
+}
+
 __device__ __forceinline__ df df_from_double(double a) {
   df r;
   split2(a, r.hi, r.lo);
+  return r;
+}
+__device__ __forceinline__ df df_from_double_s(double a, SplitShift sh) {
+  df r;
+  split2s(a, r.hi, r.lo, sh);
   return r;
 }
 
@@ -148,6 +187,23 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
+// Wait for the phase with the given parity to complete, giving up after
+// limit_ns of %globaltimer time.  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  unsigned long long t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  uint32_t it = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if ((++it & 255u) == 0) {
+      unsigned long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (t - t0 > limit_ns) return false;
+    }
+  }
+  return true;
+}
+
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }

@@ -12,10 +12,24 @@ namespace lsq {
 // Sketch (sketch.cu)
 cudaError_t sketch_indices(uint64_t seed, int64_t row0, int64_t rows, int64_t d, int zeta, int32_t* idx, int8_t* sgn,
                            int32_t* rounds, uint32_t* status, int32_t* max_rounds, int sms, cudaStream_t st);
+// range (nullable, [2] words, zeroed by the caller): atomic max of the
+// exponent field (high word & 0x7FF00000) over A's and over b's finite entries.
 template <typename TY>
 cudaError_t sketch_apply(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d, int zeta,
                          uint64_t seed, int64_t row0, TY* Y, int64_t ldy, uint32_t* status, int32_t* max_rounds,
-                         int sms, cudaStream_t st);
+                         uint32_t* range, int sms, cudaStream_t st);
+// Mixed form: FP32 accumulation into Y (ldy % 4 == 0, 16-byte aligned); with
+// Ylo (same shape, zeroed) non-null, compensated: the exact rounding error of
+// every add goes into Ylo, and Y + Ylo is the sketch to about u^2 sqrt(N).
+cudaError_t sketch_apply_f32c(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d,
+                              int zeta, uint64_t seed, int64_t row0, float* Y, float* Ylo, int64_t ldy,
+                              uint32_t* status, int32_t* max_rounds, uint32_t* range, int sms, cudaStream_t st);
+// Y[e] = fl32(Y[e] + Ylo[e]) for e < count.
+cudaError_t add_lo(float* Y, const float* Ylo, int64_t count, int sms, cudaStream_t st);
+// The same range words (and DS_NONFINITE) from one read of A and b, for LSQR
+// calls that do not sketch first.
+cudaError_t range_scan(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, uint32_t* range,
+                       uint32_t* status, int sms, cudaStream_t st);
 
 // Preconditioner (qr.cu).  W: FP64 column-major working copy, ncol x d.
 struct PrecondBuffers {
@@ -28,6 +42,7 @@ struct PrecondBuffers {
   void* blk;       // precond_blocked_bytes(d, n) of scratch for the blocked QR, or null (unblocked)
   void* blas;      // cublasHandle_t for the blocked QR's trailing updates
   int mode;        // 0: choose by size, 1: unblocked, 2: blocked (LSQ_QR_*)
+  const void* Ylo = nullptr;  // compensated FP32 sketch: error terms added to Y (same type and layout), or null
 };
 // Scratch the blocked Householder QR needs for a d x (n+1) sketch.
 size_t precond_blocked_bytes(int64_t d, int64_t n);
@@ -36,6 +51,32 @@ cudaError_t transpose_square(const double* src, int n, double* dst, cudaStream_t
 template <typename TY>
 cudaError_t precond(const TY* Y, int64_t d, int64_t n, int64_t ldy, int has_b, double* R, double* M, double* x0,
                     const PrecondBuffers& buf, int sms, cudaStream_t st);
+
+// Tensor-core GEMMs of the blocked QR's trailing updates (tc_gemm.cu): D = A B^T
+// from exact bf16 slices of A's and B's rows ([S][rows][Kpad], K contiguous,
+// row exponents ea/eb), S = 7 for FP64 data, 3 for FP32.
+struct OzGemm {
+  int S;
+  const void* a;  // __nv_bfloat16 slices of A's M rows
+  const void* b;  // __nv_bfloat16 slices of B's N rows
+  int M, N, K, Kpad;
+  const int* ea;
+  const int* eb;
+  int mode;       // 0: out[a * ldo + b] += D (FP64 atomics, out zeroed by the caller); 1: out[b * ldo + a] -= D
+  int out_f32;    // mode 1: out is float
+  void* out;
+  int64_t ldo;
+  int k_split;    // mode 0: K per CTA, a multiple of 128
+  uint32_t* status;
+  const GridBarrier* bar;
+};
+int oz_kpad(int K);
+// Slices of R rows of length K (row r at X + r ldx), or with T (b x b, K = b)
+// of the rows of U T^T for column-major U (X, ld ldx).
+template <typename TX>
+cudaError_t oz_slice(const TX* X, int R, int K, int64_t ldx, const double* T, int S, void* out, int Kpad, int* ex,
+                     int sms, cudaStream_t st);
+cudaError_t oz_gemm(const OzGemm& g, cudaStream_t st);
 
 // LSQR and the accuracy pass (lsqr.cu).
 struct LsqrParams {
@@ -49,8 +90,9 @@ struct LsqrParams {
   int64_t ldi;       // image row length: n rounded up to even
   bool a_ring;       // A rows can come through bulk copies (n even, lda even, A 16-byte aligned)
   bool vec;          // A rows allow 16-byte vector loads (lda even, A aligned)
-  bool check_df;     // accuracy pass in pair arithmetic on the image (batched problems)
   int ring_k;        // consecutive row steps per ring buffer (1 for the single-problem kernel)
+  const uint32_t* range;  // [2]: largest (high word & 0x7FF00000) over A's and b's entries, or null:
+                          // exponent shifts of the double-float passes (pass_scale)
   const double* M;   // n x n row-major (upper triangular), may be null in check mode
   const double* Mt;  // transpose of M, row-major
   double* x;         // in: start, out: solution
@@ -68,6 +110,7 @@ struct LsqrParams {
   int mode;          // 0 = LSQR then check, 1 = check only, 2 = LSQR only,
                      // 3 = heavy-ball momentum then check, 4 = heavy-ball momentum only
   double hbm_alpha, hbm_beta;  // step and momentum of modes 3 and 4
+  double gate;       // > 0: the accuracy pass raises DS_ACCURACY when min(eta_ne, eta_pre) > gate
   int gidx, gcount;  // this block's index among the blocks sharing the problem (set in-kernel)
   GridBarrier* bar;
   uint32_t* status;
@@ -93,6 +136,10 @@ enum {
   OUT_T_SKETCH,
   OUT_T_PRECOND,
   OUT_T_END,
+  // %globaltimer (ns) when block 0 started the final accuracy pass and when
+  // the pass had finished on every block (the first barrier after it)
+  OUT_T_CHECK0 = 17,
+  OUT_T_CHECK1,
   kOutSlots = 24
 };
 // Widest problem of the LSQR kernels (the panel kernel shares a row among
@@ -107,6 +154,11 @@ int lsqr_gparts(int grid);
 // Grid size the LSQR kernel will use for n (co-resident blocks).
 int lsqr_grid(int n, bool vec, bool native, int sms);
 cudaError_t lsqr_run(const LsqrParams& p, bool vec, bool native, int grid, cudaStream_t st);
+// Self-test of the bounded device waits: kind 0 -- a grid barrier of `blocks`
+// co-resident blocks that expects one block more (it can never fill); kind 1
+// -- an mbarrier phase that nothing completes.  Both give up after the
+// barrier word's limit_us and raise DS_TIMEOUT in *status.
+cudaError_t wait_selftest(int kind, GridBarrier* bar, uint32_t* status, int blocks, cudaStream_t st);
 
 // Sparse A in CSR form (sparse.cu): structure check (sets DS_CSR), sketch of the nonzeros (Y zeroed by the
 // caller, ldy >= n + 1 with b), and the LSQR kernel over the nonzeros.
@@ -130,7 +182,7 @@ struct BatchTuning;
 BatchTuning* batch_tuning_new();
 void batch_tuning_free(BatchTuning* t);
 struct BatchLayout {
-  size_t oY, oW, oR, oM, oMt, oRd, oU, oVec, oGpart, oPart, oImg, slab;
+  size_t oY, oW, oR, oM, oMt, oRd, oU, oVec, oGpart, oPart, oImg, oRange, slab;
   int npad_max;
 };
 BatchLayout batch_layout(int64_t m_max, int n_max, int d_max);

@@ -164,7 +164,36 @@ int panels_for(int n) {
   return 0;
 }
 
+// Self-test kernels of the bounded waits (wait_selftest).  Kind 0: every
+// block arrives at one grid barrier that expects gridDim.x + 1 arrivals, so
+// the round never fills and every block gives up after the barrier's limit.
+// Kind 1: one thread waits on phase 0 of a fresh mbarrier on which nothing
+// arrives.  Neither touches memory other than the status word and the
+// barrier it was given.
+__global__ void k_wait_grid(GridBarrier* bar, uint32_t* status) { grid_sync(bar, status, gridDim.x + 1u); }
+
+__global__ void k_wait_mbar(const GridBarrier* bar, uint32_t* status) {
+  __shared__ __align__(8) uint64_t mb;
+  if (threadIdx.x == 0) {
+    mbar_init(&mb, 1u);
+    fence_proxy_async_smem();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait_bounded(&mb, 0u, wait_limit_ns(bar))) atomicOr(status, DS_TIMEOUT);
+}
+
 }  // namespace
+
+cudaError_t wait_selftest(int kind, GridBarrier* bar, uint32_t* status, int blocks, cudaStream_t st) {
+  if (kind == 1) {
+    k_wait_mbar<<<1, 32, 0, st>>>(bar, status);
+    return cudaGetLastError();
+  }
+  GridBarrier* b = bar;
+  uint32_t* s = status;
+  void* args[] = {&b, &s};
+  return cudaLaunchCooperativeKernel((const void*)k_wait_grid, blocks, 32, args, 0, st);
+}
 
 int lsqr_gparts(int grid) { return grid * kWarps; }
 

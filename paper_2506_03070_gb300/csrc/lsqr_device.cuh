@@ -24,6 +24,44 @@ __device__ __forceinline__ bool group_sync(const LsqrParams& p) {
   return grid_sync(p.bar, p.status, (unsigned int)p.gcount);
 }
 
+// Exponent shifts of the double-float passes (see split2s).  A's entries are
+// split as A 2^-sa, sa from the largest exponent of A (p.range, written by the
+// sketch or by a range scan before the LSQR kernel), so the image holds values
+// up to 1 in magnitude.  A pass that forms y = A w - gamma u (or b - A x)
+// works on y' = y 2^-e with an output exponent e chosen for it: sb (from the
+// largest entry of b) for the residual passes b - A x, whose y has b's scale,
+// and 0 for the LSQR iterations, whose uhat = A M v - alpha u has the scale of
+// ||A M|| ~ 1 whatever the scale of A and b.  Then the pass vector is scaled
+// by 2^(sa-e), b by 2^-e, the stored y' is y 2^-e (the caller rescales gamma
+// by 2^(e_prev - e) for the stored vector it reads), and the FP64 outputs are
+// scaled back by exact powers of two: A^T y by 2^(sa+e), sums of y^2 and b^2
+// by 2^(2e), of A_ij^2 by 2^(2 sa).
+__device__ __forceinline__ void range_exps(const LsqrParams& p, int& sa, int& sb) {
+  sa = sb = 0;
+  if (p.range) {
+    const uint32_t ea = __ldcg(p.range) >> 20, eb = __ldcg(p.range + 1) >> 20;
+    if (ea) sa = (int)ea - 1023;
+    if (eb) sb = (int)eb - 1023;
+  }
+}
+
+struct PassScale {
+  SplitShift a, b;  // A's split (sa) and b's (e)
+  double w, g, y2, a2;
+};
+__device__ __forceinline__ PassScale pass_scale(const LsqrParams& p, int e) {
+  int sa, sb;
+  range_exps(p, sa, sb);
+  PassScale r;
+  r.a = split_shift(sa);
+  r.b = split_shift(e);
+  r.w = ldexp(1.0, sa - e);
+  r.g = ldexp(1.0, sa + e);
+  r.y2 = ldexp(1.0, 2 * e);
+  r.a2 = ldexp(1.0, 2 * sa);
+  return r;
+}
+
 // --------------------------------------------------------------------------
 // The pass over A.  Block `blk` owns rows [m*blk/G, m*(blk+1)/G); its warp k
 // takes rows start+k, start+k+8, ...  Lane l holds columns 2l+64t, 2l+64t+1
@@ -215,6 +253,118 @@ __device__ void m_apply_update(const LsqrParams& p, double ainv, double cx, doub
   }
 }
 
+// Named barrier of one row group (PW warps that share a row; barrier 0 is
+// __syncthreads).
+template <int PW>
+__device__ __forceinline__ void row_group_bar(int rg) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + rg), "r"(32 * PW) : "memory");
+}
+
+// --------------------------------------------------------------------------
+// Native FP64 pass for wide rows (512 < n <= 4096), in the row-group/panel
+// layout of the double-float panel pass: the block's warps form kWarps/PW row
+// groups; warp pw of a group owns columns [c0, c0 + pwid), c0 = pw * pwid,
+// pwid = ceil(n/PW) rounded up to 16 (lane l: columns c0 + 2l + 64t, t < 8).
+// Per row: each warp's partial dot of its panel with x, the partials meet in
+// shared memory at the group's named barrier (double-buffered by row
+// parity), every warp sums them in panel order (the same y in all of them),
+// y = b_i - A_i x, and each warp adds y A_ij into its panel's FP64 column sums.
+// FRO adds sum A_ij^2.  Rows are read directly (16-byte loads when A is
+// aligned and lda even); the pass is bound by the FP64 pipe (two FMA per
+// entry).  Outputs as the other passes: gpart row (block, row group), part
+// slots 0 (y^2), 1 (b^2), 2 (A_ij^2).
+// --------------------------------------------------------------------------
+template <int PW, bool FRO>
+__device__ void pass_native_panel(const LsqrParams& p, double* s_scal) {
+  constexpr int NRG = kWarps / PW, PPL = 8;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int rg = wib / PW, pw = wib % PW;
+  const int G = p.gcount, blk = p.gidx, n = p.n;
+  const int pwid = ((n + PW - 1) / PW + 15) / 16 * 16;
+  const int c0 = pw * pwid, cend = min(c0 + pwid, n);
+  const int64_t r0 = (p.m * blk) / G, r1 = (p.m * (blk + 1)) / G;
+  double* pdot = s_scal + kWarps * 4 + rg * 2 * PW;
+  double xr[2 * PPL], g[2 * PPL];
+#pragma unroll
+  for (int t = 0; t < PPL; ++t) {
+    const int c = c0 + 2 * lane + 64 * t;
+    xr[2 * t] = c < cend ? p.x[c] : 0.0;
+    xr[2 * t + 1] = c + 1 < cend ? p.x[c + 1] : 0.0;
+    g[2 * t] = g[2 * t + 1] = 0.0;
+  }
+  double ss = 0.0, bb = 0.0, fro = 0.0;
+  uint32_t par = 0;
+  for (int64_t i = r0 + rg; i < r1; i += NRG, par ^= 1u) {
+    const double* Ai = p.A + i * p.lda;
+    double2 a[PPL];
+#pragma unroll
+    for (int t = 0; t < PPL; ++t) {
+      const int c = c0 + 2 * lane + 64 * t;
+      if (c + 1 < cend) {
+        if (p.vec) {
+          a[t] = __ldcs(reinterpret_cast<const double2*>(Ai + c));
+        } else {
+          a[t].x = __ldcs(Ai + c);
+          a[t].y = __ldcs(Ai + c + 1);
+        }
+      } else if (c < cend) {
+        a[t].x = __ldcs(Ai + c);
+        a[t].y = 0.0;
+      } else {
+        a[t].x = a[t].y = 0.0;
+      }
+    }
+    const double bi = p.b[i];
+    double dot = 0.0;
+#pragma unroll
+    for (int t = 0; t < PPL; ++t) {
+      dot = fma(a[t].x, xr[2 * t], dot);
+      dot = fma(a[t].y, xr[2 * t + 1], dot);
+    }
+    dot = warp_allreduce_sum(dot);
+    double* slot = pdot + par * PW;
+    if (lane == 0) slot[pw] = dot;
+    row_group_bar<PW>(rg);
+    double ax = slot[0];
+#pragma unroll
+    for (int q = 1; q < PW; ++q) ax += slot[q];
+    const double y = bi - ax;
+    if (pw == 0) {
+      ss = fma(y, y, ss);
+      bb = fma(bi, bi, bb);
+    }
+#pragma unroll
+    for (int t = 0; t < PPL; ++t) {
+      g[2 * t] = fma(y, a[t].x, g[2 * t]);
+      g[2 * t + 1] = fma(y, a[t].y, g[2 * t + 1]);
+      if (FRO) {
+        fro = fma(a[t].x, a[t].x, fro);
+        fro = fma(a[t].y, a[t].y, fro);
+      }
+    }
+  }
+  double* gw = p.gpart + ((int64_t)blk * NRG + rg) * p.npad;
+#pragma unroll
+  for (int t = 0; t < PPL; ++t) {
+    const int c = c0 + 2 * lane + 64 * t;
+    if (c < cend) gw[c] = g[2 * t];
+    if (c + 1 < cend) gw[c + 1] = g[2 * t + 1];
+  }
+  if (FRO) fro = warp_allreduce_sum(fro);
+  if (lane == 0) {
+    s_scal[wib * 4 + 0] = ss;
+    s_scal[wib * 4 + 1] = bb;
+    s_scal[wib * 4 + 2] = fro;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double sum = 0.0;
+    for (int w = 0; w < kWarps; ++w) sum += s_scal[w * 4 + threadIdx.x];
+    p.part[(int64_t)blk * 4 + threadIdx.x] = sum;
+  }
+  __syncthreads();
+}
+
 // --------------------------------------------------------------------------
 // The double-float pass (FP32/INT pipes only in the per-entry and per-row
 // work).  A warp handles R = 32/L rows per step, L lanes per row; lane l
@@ -248,6 +398,7 @@ struct DfPass {
   double* s_scal;
   uint32_t seq;     // ring buffers this warp has consumed (all passes)
   float2* s_w;      // shared [>= ldi]: the pass vector as float pairs
+  int u_exp = 0;    // output exponent of the stored vector u (see range_exps)
 
   // Chunk c of the group's rows: K = p.ring_k consecutive steps of R rows.
   template <bool FROM_IMAGE>
@@ -273,25 +424,16 @@ struct DfPass {
     }
   }
 
-  // Wait (bounded) for the buffer of chunk jc.  Returns false on timeout (warp-uniform).
-  __device__ bool wait(uint32_t jc, uint64_t* mybars) {
+  // Wait (bounded by lim ns) for the buffer of chunk jc.  Returns false on
+  // timeout (warp-uniform).
+  __device__ bool wait(uint32_t jc, uint64_t* mybars, unsigned long long lim) {
     const uint32_t s = seq + jc, b = s % kNbuf, par = (s / kNbuf) & 1u;
-    bool timed_out = false;
-    if (!mbar_try_wait(mybars + b, par)) {
-      const unsigned long long t0 = globaltimer_ns();
-      uint32_t it = 0;
-      while (!mbar_try_wait(mybars + b, par)) {
-        if ((++it & 255u) == 0 && globaltimer_ns() - t0 > kBarrierTimeoutNs) {
-          timed_out = true;
-          break;
-        }
-      }
-    }
+    const bool timed_out = !mbar_wait_bounded(mybars + b, par, lim);
     return !__any_sync(0xffffffffu, timed_out);
   }
 
   // column pairs summed over the R segments, then added to the warp's FP64 row
-  __device__ void flush(df (&Gc)[2 * PPL], double* gw, int cl, int seg, int n, bool& first) {
+  __device__ void flush(df (&Gc)[2 * PPL], double* gw, int cl, int seg, int n, bool& first, double gmul) {
 #pragma unroll
     for (int q = 0; q < 2 * PPL; ++q) {
 #pragma unroll
@@ -303,8 +445,8 @@ struct DfPass {
         const int c = 2 * cl + 2 * L * t;
         if (c < n) {
           double2 g = first ? make_double2(0.0, 0.0) : *reinterpret_cast<const double2*>(gw + c);
-          g.x += df_to_double(Gc[2 * t]);
-          g.y += df_to_double(Gc[2 * t + 1]);
+          g.x += df_to_double(Gc[2 * t]) * gmul;
+          g.y += df_to_double(Gc[2 * t + 1]) * gmul;
           *reinterpret_cast<double2*>(gw + c) = g;
         }
       }
@@ -320,7 +462,7 @@ struct DfPass {
   // sum A_ij^2 (in pair arithmetic) to slot 2.  Warp w takes chunks
   // w, w+8, ... of K steps (K*R consecutive rows), one ring buffer per chunk.
   template <bool UIN_B, bool UIN2, bool STORE, bool FROM_IMAGE, bool WRITE_IMAGE, bool FRO>
-  __device__ void run(const LsqrParams& p, const double* __restrict__ wvec, double wsign, double gamma) {
+  __device__ void run(const LsqrParams& p, const double* __restrict__ wvec, double wsign, double gamma, int e_out) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int seg = lane / L, cl = lane % L;
     const int G = p.gcount, blk = p.gidx;
@@ -334,10 +476,12 @@ struct DfPass {
     uint64_t* mybars = bars + wib * kNbuf;
     float2* ubuf = reinterpret_cast<float2*>(p.u);
     double* gw = p.gpart + ((int64_t)blk * kWarps + wib) * p.npad;
+    const PassScale sc = pass_scale(p, e_out);
+    const unsigned long long lim = wait_limit_ns(p.bar);
 
-    // the pass vector as float pairs in shared memory (read per entry)
+    // the pass vector (scaled by 2^(sa-sb)) as float pairs in shared memory (read per entry)
     for (int c = threadIdx.x; c < p.ldi; c += kThreads) {
-      const double v = c < n ? wsign * wvec[c] : 0.0;
+      const double v = c < n ? wsign * wvec[c] * sc.w : 0.0;
       const float v1 = __double2float_rn(v);
       s_w[c] = make_float2(v1, __double2float_rn(v - (double)v1));
     }
@@ -359,7 +503,7 @@ struct DfPass {
     bool ok = true;
     uint32_t jc = 0;
     for (; jc < count; ++jc) {
-      if (use_ring && !wait(jc, mybars)) {
+      if (use_ring && !wait(jc, mybars, lim)) {
         ok = false;
         break;
       }
@@ -401,8 +545,8 @@ struct DfPass {
               v.x = __ldcs(Ar + c);
               if (c + 1 < n) v.y = __ldcs(Ar + c + 1);
             }
-            split2(v.x, h[2 * t], mm[2 * t]);
-            split2(v.y, h[2 * t + 1], mm[2 * t + 1]);
+            split2s(v.x, h[2 * t], mm[2 * t], sc.a);
+            split2s(v.y, h[2 * t + 1], mm[2 * t + 1], sc.a);
             if (WRITE_IMAGE && in)
               *reinterpret_cast<float4*>(p.asplit + row * p.ldi + c) =
                   make_float4(h[2 * t], mm[2 * t], h[2 * t + 1], mm[2 * t + 1]);
@@ -429,7 +573,7 @@ struct DfPass {
         dot = df_renorm(dot);
         df y{0.f, 0.f};
         if (valid) {
-          const df ui = UIN_B ? df_from_double(bi) : df{uu.x, uu.y};
+          const df ui = UIN_B ? df_from_double_s(bi, sc.b) : df{uu.x, uu.y};
           y = df_add(dot, df_neg(df_mul(gdf, ui)));
           if (STORE && cl == 0) ubuf[row] = make_float2(y.hi, y.lo);
           ss = df_add(ss, df_mul(y, y));
@@ -442,7 +586,7 @@ struct DfPass {
           if (FRO) df_fma_acc(fro, h[q], mm[q], h[q], mm[q]);
         }
         if (FRO) fro = df_renorm(fro);
-        if ((steps & 31u) == 31u) flush(Gc, gw, cl, seg, n, first_flush);
+        if ((steps & 31u) == 31u) flush(Gc, gw, cl, seg, n, first_flush, sc.g);
       }
       __syncwarp();
       if (lane == 0 && use_ring && jc + kNbuf < count) {
@@ -456,10 +600,10 @@ struct DfPass {
         atomicOr(p.status, DS_TIMEOUT);
         barrier_abort(p.bar);
       }
-      for (uint32_t k = jc; k < count && k < jc + kNbuf; ++k) wait(k, mybars);
+      for (uint32_t k = jc; k < count && k < jc + kNbuf; ++k) wait(k, mybars, lim);
     }
     if (use_ring) seq += count;  // ring phases advance only when rows went through it
-    flush(Gc, gw, cl, seg, n, first_flush);
+    flush(Gc, gw, cl, seg, n, first_flush, sc.g);
     // ss and bb: one copy per segment (lanes of a segment agree); fro per lane
 #pragma unroll
     for (int o = L; o < 32; o <<= 1) {
@@ -467,10 +611,10 @@ struct DfPass {
       bb = df_add(bb, shfl_xor_df(bb, o));
     }
     double frow = 0.0;
-    if (FRO) frow = warp_allreduce_sum(df_to_double(fro));
+    if (FRO) frow = warp_allreduce_sum(df_to_double(fro)) * sc.a2;
     if (lane == 0) {
-      s_scal[wib * 4 + 0] = df_to_double(ss);
-      s_scal[wib * 4 + 1] = df_to_double(bb);
+      s_scal[wib * 4 + 0] = df_to_double(ss) * sc.y2;
+      s_scal[wib * 4 + 1] = df_to_double(bb) * sc.y2;
       s_scal[wib * 4 + 2] = frow;
     }
     __syncthreads();
@@ -494,9 +638,7 @@ struct DfPass {
   // warp whose copy wait gives up keeps meeting its group's barriers (on
   // stale data, with DS_TIMEOUT raised) so the group never waits on it.
   // ------------------------------------------------------------------------
-  __device__ __forceinline__ void group_bar(int rg) {
-    asm volatile("bar.sync %0, %1;" ::"r"(1 + rg), "r"(32 * PW) : "memory");
-  }
+  __device__ __forceinline__ void group_bar(int rg) { row_group_bar<PW>(rg); }
 
   template <bool FROM_IMAGE>
   __device__ void issue_panel(const LsqrParams& p, int64_t row, int c0, int cols, uint32_t jc, double* myring,
@@ -512,7 +654,8 @@ struct DfPass {
   }
 
   template <bool UIN_B, bool UIN2, bool STORE, bool FROM_IMAGE, bool WRITE_IMAGE, bool FRO>
-  __device__ void run_panel(const LsqrParams& p, const double* __restrict__ wvec, double wsign, double gamma) {
+  __device__ void run_panel(const LsqrParams& p, const double* __restrict__ wvec, double wsign, double gamma,
+                            int e_out) {
     constexpr int NRG = kWarps / PW;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int rg = wib / PW, pw = wib % PW;
@@ -532,9 +675,11 @@ struct DfPass {
     double* gw = p.gpart + ((int64_t)blk * NRG + rg) * p.npad;
     // s_scal holds kWarps * 6 doubles here: 4 per warp, then [row group][2 parities][PW] pairs
     df* pdot = reinterpret_cast<df*>(s_scal + kWarps * 4) + rg * 2 * PW;
+    const PassScale sc = pass_scale(p, e_out);
+    const unsigned long long lim = wait_limit_ns(p.bar);
 
     for (int c = threadIdx.x; c < p.ldi; c += kThreads) {
-      const double v = c < n ? wsign * wvec[c] : 0.0;
+      const double v = c < n ? wsign * wvec[c] * sc.w : 0.0;
       const float v1 = __double2float_rn(v);
       s_w[c] = make_float2(v1, __double2float_rn(v - (double)v1));
     }
@@ -555,7 +700,7 @@ struct DfPass {
     bool ok = true;
     uint32_t failed_at = count;
     for (uint32_t jc = 0; jc < count; ++jc) {
-      if (use_ring && ok && !wait(jc, mybars)) {
+      if (use_ring && ok && !wait(jc, mybars, lim)) {
         ok = false;
         failed_at = jc;
         if (lane == 0) {
@@ -592,8 +737,8 @@ struct DfPass {
             v.x = __ldcs(Ar + c);
             if (c + 1 < n) v.y = __ldcs(Ar + c + 1);
           }
-          split2(v.x, h[2 * t], mm[2 * t]);
-          split2(v.y, h[2 * t + 1], mm[2 * t + 1]);
+          split2s(v.x, h[2 * t], mm[2 * t], sc.a);
+          split2s(v.y, h[2 * t + 1], mm[2 * t + 1], sc.a);
           if (WRITE_IMAGE && in)
             *reinterpret_cast<float4*>(p.asplit + row * p.ldi + c) =
                 make_float4(h[2 * t], mm[2 * t], h[2 * t + 1], mm[2 * t + 1]);
@@ -618,7 +763,7 @@ struct DfPass {
       dot = slot[0];
 #pragma unroll
       for (int q = 1; q < PW; ++q) dot = df_add(dot, slot[q]);
-      const df ui = UIN_B ? df_from_double(bi) : df{uu.x, uu.y};
+      const df ui = UIN_B ? df_from_double_s(bi, sc.b) : df{uu.x, uu.y};
       const df y = df_add(dot, df_neg(df_mul(gdf, ui)));
       if (pw == 0) {
         if (STORE && lane == 0) ubuf[row] = make_float2(y.hi, y.lo);
@@ -632,7 +777,7 @@ struct DfPass {
         if (FRO) df_fma_acc(fro, h[q], mm[q], h[q], mm[q]);
       }
       if (FRO) fro = df_renorm(fro);
-      if ((jc & 31u) == 31u) flush_panel(Gc, gw, c0, cend, first_flush);
+      if ((jc & 31u) == 31u) flush_panel(Gc, gw, c0, cend, first_flush, sc.g);
       __syncwarp();
       if (lane == 0 && use_ring && ok && jc + kNbuf < count) {
         fence_proxy_async_smem();
@@ -641,15 +786,15 @@ struct DfPass {
     }
     if (!ok) {
       // let the copies already issued land before the ring is reused
-      for (uint32_t k = failed_at; k < count && k < failed_at + kNbuf; ++k) wait(k, mybars);
+      for (uint32_t k = failed_at; k < count && k < failed_at + kNbuf; ++k) wait(k, mybars, lim);
     }
     if (use_ring) seq += count;
-    flush_panel(Gc, gw, c0, cend, first_flush);
+    flush_panel(Gc, gw, c0, cend, first_flush, sc.g);
     double frow = 0.0;
-    if (FRO) frow = warp_allreduce_sum(df_to_double(fro));
+    if (FRO) frow = warp_allreduce_sum(df_to_double(fro)) * sc.a2;
     if (lane == 0) {
-      s_scal[wib * 4 + 0] = df_to_double(ss);
-      s_scal[wib * 4 + 1] = df_to_double(bb);
+      s_scal[wib * 4 + 0] = df_to_double(ss) * sc.y2;
+      s_scal[wib * 4 + 1] = df_to_double(bb) * sc.y2;
       s_scal[wib * 4 + 2] = frow;
     }
     __syncthreads();
@@ -661,15 +806,15 @@ struct DfPass {
     __syncthreads();
   }
 
-  __device__ void flush_panel(df (&Gc)[2 * PPL], double* gw, int c0, int cend, bool& first) {
+  __device__ void flush_panel(df (&Gc)[2 * PPL], double* gw, int c0, int cend, bool& first, double gmul) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int t = 0; t < PPL; ++t) {
       const int c = c0 + 2 * lane + 64 * t;
       if (c < cend) {
         double2 g = first ? make_double2(0.0, 0.0) : *reinterpret_cast<const double2*>(gw + c);
-        g.x += df_to_double(Gc[2 * t]);
-        g.y += df_to_double(Gc[2 * t + 1]);
+        g.x += df_to_double(Gc[2 * t]) * gmul;
+        g.y += df_to_double(Gc[2 * t + 1]) * gmul;
         *reinterpret_cast<double2*>(gw + c) = g;
       }
       Gc[2 * t] = Gc[2 * t + 1] = df{0.f, 0.f};
@@ -678,82 +823,82 @@ struct DfPass {
   }
 
   __device__ void init(LsqrParams& p) {
+    int sa, sb;
+    range_exps(p, sa, sb);
+    u_exp = sb;  // u = b - A x0 carries b's scale
     if (PW > 1) {
       p.gparts = p.gcount * (kWarps / PW);
       if (p.asplit) {
-        run_panel<true, true, true, false, true, false>(p, p.x, -1.0, -1.0);
+        run_panel<true, true, true, false, true, false>(p, p.x, -1.0, -1.0, sb);
         asm volatile("fence.proxy.async.global;" ::: "memory");
       } else {
-        run_panel<true, true, true, false, false, false>(p, p.x, -1.0, -1.0);
+        run_panel<true, true, true, false, false, false>(p, p.x, -1.0, -1.0, sb);
       }
       return;
     }
     p.gparts = p.gcount * kWarps;
     if (p.asplit) {
-      run<true, true, true, false, true, false>(p, p.x, -1.0, -1.0);
+      run<true, true, true, false, true, false>(p, p.x, -1.0, -1.0, sb);
       // the image was written through the generic proxy and is read by bulk
       // copies (async proxy) after the next barrier
       asm volatile("fence.proxy.async.global;" ::: "memory");
     } else {
-      run<true, true, true, false, false, false>(p, p.x, -1.0, -1.0);
+      run<true, true, true, false, false, false>(p, p.x, -1.0, -1.0, sb);
     }
   }
+  // uhat = A wv - gamma uhat_prev at output exponent 0; the stored vector has
+  // exponent u_exp, so gamma is applied as gamma 2^u_exp
   __device__ void iter(LsqrParams& p, double gamma) {
+    const double g = ldexp(gamma, u_exp);
+    u_exp = 0;
     if (PW > 1) {
       p.gparts = p.gcount * (kWarps / PW);
       if (p.asplit)
-        run_panel<false, false, true, true, false, false>(p, p.wv, 1.0, gamma);
+        run_panel<false, false, true, true, false, false>(p, p.wv, 1.0, g, 0);
       else
-        run_panel<false, false, true, false, false, false>(p, p.wv, 1.0, gamma);
+        run_panel<false, false, true, false, false, false>(p, p.wv, 1.0, g, 0);
       return;
     }
     p.gparts = p.gcount * kWarps;
     if (p.asplit)
-      run<false, false, true, true, false, false>(p, p.wv, 1.0, gamma);
+      run<false, false, true, true, false, false>(p, p.wv, 1.0, g, 0);
     else
-      run<false, false, true, false, false, false>(p, p.wv, 1.0, gamma);
+      run<false, false, true, false, false, false>(p, p.wv, 1.0, g, 0);
   }
   // y = b - A x with A^T y, sum y^2 and sum b^2 (heavy-ball momentum); the
   // first call writes the float-pair image, later ones stream it.
   __device__ void residual(LsqrParams& p, bool first) {
+    int sa, sb;
+    range_exps(p, sa, sb);
     if (PW > 1) {
       p.gparts = p.gcount * (kWarps / PW);
       if (p.asplit && first) {
-        run_panel<true, true, false, false, true, false>(p, p.x, -1.0, -1.0);
+        run_panel<true, true, false, false, true, false>(p, p.x, -1.0, -1.0, sb);
         asm volatile("fence.proxy.async.global;" ::: "memory");
       } else if (p.asplit) {
-        run_panel<true, true, false, true, false, false>(p, p.x, -1.0, -1.0);
+        run_panel<true, true, false, true, false, false>(p, p.x, -1.0, -1.0, sb);
       } else {
-        run_panel<true, true, false, false, false, false>(p, p.x, -1.0, -1.0);
+        run_panel<true, true, false, false, false, false>(p, p.x, -1.0, -1.0, sb);
       }
       return;
     }
     p.gparts = p.gcount * kWarps;
     if (p.asplit && first) {
-      run<true, true, false, false, true, false>(p, p.x, -1.0, -1.0);
+      run<true, true, false, false, true, false>(p, p.x, -1.0, -1.0, sb);
       asm volatile("fence.proxy.async.global;" ::: "memory");
     } else if (p.asplit) {
-      run<true, true, false, true, false, false>(p, p.x, -1.0, -1.0);
+      run<true, true, false, true, false, false>(p, p.x, -1.0, -1.0, sb);
     } else {
-      run<true, true, false, false, false, false>(p, p.x, -1.0, -1.0);
+      run<true, true, false, false, false, false>(p, p.x, -1.0, -1.0, sb);
     }
   }
-  // Accuracy pass: native FP64 on the original A (single-problem kernel), or
-  // in pair arithmetic on the image (batched problems, p.check_df).
+  // Accuracy pass (Algorithm 1's final check; App. A.3): always native FP64
+  // on the original A -- one warp per row for n <= 512, the panel layout of
+  // the wide-row pass above.
   __device__ void check(LsqrParams& p) {
     if (PW > 1) {
-      // wide rows: the accuracy pass runs in pair arithmetic as well, on the
-      // image when there is one, else on A split on the fly
       p.gparts = p.gcount * (kWarps / PW);
-      if (p.asplit)
-        run_panel<true, true, false, true, false, true>(p, p.x, -1.0, -1.0);
-      else
-        run_panel<true, true, false, false, false, true>(p, p.x, -1.0, -1.0);
-      return;
-    }
-    if (CHUNKED && p.check_df && p.asplit) {
-      p.gparts = p.gcount * kWarps;
-      run<true, true, false, true, false, true>(p, p.x, -1.0, -1.0);
+      pass_native_panel<PW, true>(p, s_scal);
       return;
     }
     p.gparts = p.gcount;
@@ -856,8 +1001,11 @@ __device__ void finish_body(LsqrParams& p, Pass& pass, double* s_scal, int64_t i
     return;
   }
   // ---- accuracy pass: y = b - A x, g = A^T y, ||A||_F
+  const bool stamp = p.gidx == 0 && threadIdx.x == 0;
+  if (stamp) p.out[OUT_T_CHECK0] = (double)globaltimer_ns();
   pass.check(p);
   if (!group_sync(p)) return;
+  if (stamp) p.out[OUT_T_CHECK1] = (double)globaltimer_ns();
   reduce_g(p);
   if (!group_sync(p)) return;
   if (p.M) mt_apply(p, 1.0, 0.0, 3, s_scal);
@@ -885,11 +1033,18 @@ __device__ void finish_body(LsqrParams& p, Pass& pass, double* s_scal, int64_t i
       p.out[OUT_FRO] = fro;
       p.out[OUT_XNORM] = xn;
       p.out[OUT_BNORM] = bn;
-      p.out[OUT_ETA_NE] = (fro > 0.0 && rnorm > 0.0) ? arn / (fro * rnorm) : 0.0;
-      p.out[OUT_ETA_PRE] = (fro > 0.0 && xn > 0.0) ? marn / (fro * xn) : 0.0;
+      const double eta_ne = (fro > 0.0 && rnorm > 0.0) ? arn / (fro * rnorm) : 0.0;
+      const double eta_pre = (fro > 0.0 && xn > 0.0) ? marn / (fro * xn) : 0.0;
+      p.out[OUT_ETA_NE] = eta_ne;
+      p.out[OUT_ETA_PRE] = eta_pre;
       p.out[OUT_MARNORM] = marn;
       p.out[OUT_ANORM_EST] = anorm_est;
       if (stop == 3) atomicOr(status, DS_NOCONV);
+      // accuracy gate: the smaller of the two backward-error bounds (NaN fails)
+      if (p.gate > 0.0) {
+        const double eta = p.M ? fmin(eta_ne, eta_pre) : eta_ne;
+        if (!(eta <= p.gate)) atomicOr(status, DS_ACCURACY);
+      }
     }
   }
 }

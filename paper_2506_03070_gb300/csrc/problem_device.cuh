@@ -24,6 +24,7 @@ struct Group {
   int gidx, gcount;
   GridBarrier* bar;
   uint32_t* status;
+  uint32_t* range;  // [2] exponent maxima of A and b (zeroed by the host), or null
 };
 
 __device__ __forceinline__ bool gsync(const Group& g) {
@@ -60,7 +61,9 @@ __device__ __forceinline__ void zero_group(double* p, int64_t count, const Group
 // Y (d x ldy row-major, zeroed) += S [A | b] for this group's rows.  Warps
 // take blocks of 32 rows (block q -> warp q mod (G * kWarps) of the group);
 // lane l draws the sketch column of row base+l into shared memory, then the
-// warp adds +-A_ij/sqrt(zeta) into the zeta rows of Y (L2 reductions).
+// warp adds +-A_ij/sqrt(zeta) into the zeta rows of Y (L2 reductions).  The
+// largest exponent fields of A's and b's finite entries go to g.range (the
+// shifts of the double-float LSQR passes).
 __device__ void sketch_group(const double* __restrict__ A, const double* __restrict__ b, int64_t m, int n,
                              int64_t lda, int d, int zeta, uint64_t seed, double* Y, int ldy, int32_t* s_idx,
                              uint64_t* s_sgn, const Group& g) {
@@ -69,6 +72,7 @@ __device__ void sketch_group(const double* __restrict__ A, const double* __restr
   const int ncol = n + 1;
   const double scale = 1.0 / sqrt((double)zeta);
   bool bad = false;
+  uint32_t ea = 0, eb = 0;
   const int64_t wstep = (int64_t)g.gcount * kWarps * 32;
   for (int64_t base = ((int64_t)g.gidx * kWarps + wib) * 32; base < m; base += wstep) {
     const int64_t row = base + lane;
@@ -91,6 +95,13 @@ __device__ void sketch_group(const double* __restrict__ A, const double* __restr
       for (int j = lane; j < ncol; j += 32) {
         const double a = j < n ? __ldcs(Ai + j) : b[i];
         bad |= !isfinite(a);
+        const uint32_t e = (uint32_t)__double2hiint(a) & 0x7FF00000u;
+        if (e != 0x7FF00000u) {
+          if (j < n)
+            ea = max(ea, e);
+          else
+            eb = max(eb, e);
+        }
         const double sa = a * scale;
         for (int k = 0; k < zeta; ++k) {
           const double v =
@@ -102,6 +113,14 @@ __device__ void sketch_group(const double* __restrict__ A, const double* __restr
     __syncwarp();
   }
   if (bad) atomicOr(g.status, DS_NONFINITE);
+  if (g.range) {
+    ea = __reduce_max_sync(0xffffffffu, ea);
+    eb = __reduce_max_sync(0xffffffffu, eb);
+    if (lane == 0) {
+      if (ea) atomicMax(g.range, ea);
+      if (eb) atomicMax(g.range + 1, eb);
+    }
+  }
 }
 
 // Householder QR of the d x ncol column-major W.  Step k: every block of the

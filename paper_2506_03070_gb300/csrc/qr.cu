@@ -30,15 +30,22 @@ namespace lsq {
 namespace {
 
 template <typename TY>
-__global__ void k_to_colmajor(const TY* __restrict__ Y, int64_t d, int ncol, int64_t ldy, TY* __restrict__ W) {
+__global__ void k_to_colmajor(const TY* __restrict__ Y, const TY* __restrict__ Ylo, int64_t d, int ncol, int64_t ldy,
+                              TY* __restrict__ W) {
   // 32x32 tiles through shared memory: read rows of Y, write columns of W.
+  // With Ylo (the compensated sketch's error terms), W = fl(Y + Ylo).
   __shared__ TY tile[32][33];
   const int64_t i0 = (int64_t)blockIdx.x * 32;
   const int j0 = blockIdx.y * 32;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int64_t i = i0 + r;
     const int j = j0 + threadIdx.x;
-    tile[r][threadIdx.x] = (i < d && j < ncol) ? Y[i * ldy + j] : (TY)0;
+    TY v = (TY)0;
+    if (i < d && j < ncol) {
+      v = Y[i * ldy + j];
+      if (Ylo) v += Ylo[i * ldy + j];
+    }
+    tile[r][threadIdx.x] = v;
   }
   __syncthreads();
   for (int c = threadIdx.y; c < 32; c += blockDim.y) {
@@ -380,7 +387,7 @@ cudaError_t householder_blocked(TW* W, int64_t d, int n, int ncol, double* rdiag
     uint32_t* status = buf.status;
     void* args[] = {&Wp, &ld64, &k064, &L64, &bb, &U, &rd, &tau, &part, &rowv, &bar, &status};
     // the ticket barrier's counter restarts for each launch (G changes with L)
-    if (G > 1 && (e = cudaMemsetAsync(buf.bar, 0, sizeof(GridBarrier), st)) != cudaSuccess) return e;
+    if (G > 1 && (e = cudaMemsetAsync(&buf.bar->count, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
     if (G == 1)
       e = cudaLaunchKernel((const void*)k_panel<TW>, 1, 256, args, 0, st);
     else
@@ -512,10 +519,10 @@ cudaError_t precond(const TY* Y, int64_t d, int64_t n64, int64_t ldy, int has_b,
   cudaError_t e;
   {
     dim3 grid((unsigned)((d + 31) / 32), (unsigned)((ncol + 31) / 32)), block(32, 8);
-    k_to_colmajor<TY><<<grid, block, 0, st>>>(Y, d, ncol, ldy, W);
+    k_to_colmajor<TY><<<grid, block, 0, st>>>(Y, reinterpret_cast<const TY*>(buf.Ylo), d, ncol, ldy, W);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  if ((e = cudaMemsetAsync(buf.bar, 0, sizeof(GridBarrier), st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(&buf.bar->count, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
   const bool big = n >= kBlockedMinN && (size_t)d * ncol * sizeof(TY) >= kBlockedMinBytes;
   const bool blocked = buf.mode == 2 || (buf.mode == 0 && big);
   if (buf.blk && buf.blas && blocked && (size_t)kPanelMax * ncol <= ((size_t)1 << 31)) {

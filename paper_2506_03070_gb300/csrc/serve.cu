@@ -35,6 +35,7 @@
 // whole launch (kRetired) so that no group can form on a half-exited server.
 // A block whose request hit a timeout leaves the loop (its copy ring may be
 // out of phase); the host relaunches the server once the rest has drained.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -78,6 +79,7 @@ struct ServeItem {  // written by the host into mapped memory; 8-byte words only
   uint64_t seed;
   double tol;
   int64_t maxit;
+  double gate;  // accuracy gate of the final pass (0: none)
   char* slot;
   uint64_t oCtl, oY, oW, oR, oM, oMt, oRd, oU, oVec, oGpart, oPart, oImg;
   int64_t npad;
@@ -86,11 +88,11 @@ struct ServeItem {  // written by the host into mapped memory; 8-byte words only
 constexpr int kItemWords = sizeof(ServeItem) / 8;
 static_assert(sizeof(ServeItem) % 8 == 0, "item is copied as 8-byte words");
 
-struct ServeCtl {  // per request, in its slot; zeroed by the host before publishing
-  GridBarrier bar;
+struct ServeCtl {  // per request, in its slot; reset by the host before publishing
+  GridBarrier bar;     // bar.limit_us: the context's wait limit when the request was staged
   uint32_t status;
   uint32_t exit;
-  uint32_t pad[2];
+  uint32_t range[2];   // exponent maxima of A and b (the double-float passes' shifts)
   double out[kOutSlots];
 };
 
@@ -174,7 +176,7 @@ __device__ void serve_solve(const ServeItem& it, int gidx, double* s_ring, uint6
                             double* scratch, uint64_t* s_sgn, float2* s_w, uint32_t& seq) {
   char* slot = it.slot;
   ServeCtl* ctl = reinterpret_cast<ServeCtl*>(slot + it.oCtl);
-  const Group g{gidx, it.G, &ctl->bar, &ctl->status};
+  const Group g{gidx, it.G, &ctl->bar, &ctl->status, ctl->range};
   const int n = it.n, d = it.d, ncol = n + 1, ldy = ncol;
   double* Y = reinterpret_cast<double*>(slot + it.oY);
   double* W = reinterpret_cast<double*>(slot + it.oW);
@@ -224,8 +226,9 @@ __device__ void serve_solve(const ServeItem& it, int gidx, double* s_ring, uint6
   p.ldi = (n + 1) / 2 * 2;
   p.vec = ((uintptr_t)it.A % 16 == 0) && (it.lda % 2 == 0);
   p.a_ring = p.vec && (n % 2 == 0);
-  p.check_df = true;
   p.ring_k = 1;
+  p.range = ctl->range;
+  p.gate = it.gate;
   p.M = M;
   p.Mt = Mt;
   p.x = it.x;
@@ -341,6 +344,7 @@ lsq_status status_of_bits(uint32_t bits) {
   if (bits & DS_SKETCH) return LSQ_ERR_SKETCH;
   if (bits & DS_RANK) return LSQ_ERR_RANK;
   if (bits & DS_NOCONV) return LSQ_ERR_NOCONV;
+  if (bits & DS_ACCURACY) return LSQ_ERR_ACCURACY;
   return LSQ_OK;
 }
 
@@ -384,7 +388,8 @@ struct Server {
   uint32_t* d_srv_status = nullptr;
   ServeItem* d_ring = nullptr;
   // pinned host memory: staged entries and tail values (sources of the
-  // publishing copies), constant words, a zero page
+  // publishing copies), constant words, the control-word template (zero but
+  // for the wait limit)
   char* h_pin = nullptr;
   ServeItem* h_items = nullptr;
   unsigned long long* h_tails = nullptr;
@@ -645,6 +650,10 @@ struct Server {
   }
 };
 
+void server_set_wait_limit(Server* s, uint32_t limit_us) {
+  if (s && s->h_zero) reinterpret_cast<volatile uint32_t*>(&reinterpret_cast<ServeCtl*>(s->h_zero)->bar.limit_us)[0] = limit_us;
+}
+
 void server_destroy(Server* s) {
   if (!s) return;
   {
@@ -724,6 +733,7 @@ lsq_status server_create(lsq_ctx* ctx, Server** out) {
   s->h_words[0] = 0u;
   s->h_words[1] = 1u;
   s->h_zero = s->h_pin + sizeof(ServeItem) * kServeCap + sizeof(unsigned long long) * kServeCap + 256;
+  server_set_wait_limit(s, ctx->wait_limit_us);
   const size_t hbytes = sizeof(ServeDone) * kServeCap;
   if (cudaHostAlloc(&s->hmem, hbytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess)
     return bail(LSQ_ERR_OOM, "mapped completion records");
@@ -771,6 +781,7 @@ void plan_request(ServeRequest* r, int max_group, double cta_bytes, const BatchT
   it.seed = r->o.seed;
   it.tol = r->o.tol;
   it.maxit = r->o.maxit;
+  it.gate = it.mode == 0 ? (r->o.gate < 0.0 ? 0.0 : r->o.gate > 0.0 ? r->o.gate : std::max(1e-10, r->o.tol)) : 0.0;
   it.npad = npad;
   size_t o = 0;
   auto take = [&](size_t bytes) {

@@ -35,6 +35,23 @@ __global__ void __launch_bounds__(256) k_sketch_indices(uint64_t seed, int64_t r
   }
 }
 
+// Exponent field of a finite FP64 value into the running maximum (non-finite
+// values are reported separately).
+__device__ __forceinline__ void track_exp(double a, uint32_t& emax) {
+  const uint32_t e = (uint32_t)__double2hiint(a) & 0x7FF00000u;
+  if (e != 0x7FF00000u) emax = max(emax, e);
+}
+// Warp maxima of the A and b exponent fields into range[0], range[1].
+__device__ __forceinline__ void flush_range(uint32_t ea, uint32_t eb, uint32_t* range) {
+  if (!range) return;
+  ea = __reduce_max_sync(0xffffffffu, ea);
+  eb = __reduce_max_sync(0xffffffffu, eb);
+  if ((threadIdx.x & 31) == 0) {
+    if (ea) atomicMax(range, ea);
+    if (eb) atomicMax(range + 1, eb);
+  }
+}
+
 __device__ __forceinline__ void red_add(double* p, double v) { atomicAdd(p, v); }
 __device__ __forceinline__ void red_add(float* p, double v) { atomicAdd(p, (float)v); }
 
@@ -50,13 +67,15 @@ template <int N, typename TY>
 __global__ void __launch_bounds__(256) k_sketch_apply(const double* __restrict__ A, int64_t m, int n, int64_t lda,
                                                       const double* __restrict__ b, uint64_t d, int zeta,
                                                       uint64_t seed, int64_t row0, TY* __restrict__ Y, int64_t ldy,
-                                                      double scale, uint32_t* status, int32_t* max_rounds) {
+                                                      double scale, uint32_t* status, int32_t* max_rounds,
+                                                      uint32_t* range) {
   extern __shared__ int32_t s_idx[];  // [8 warps][32 rows][N]
   __shared__ uint64_t s_sgn[8][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   int32_t* my_idx = s_idx + wib * 32 * N;
   const int ncol = n + (b ? 1 : 0);
   bool bad = false;
+  uint32_t ea = 0, eb = 0;
   for (int64_t base = ((int64_t)blockIdx.x * 8 + wib) * 32; base < m; base += (int64_t)gridDim.x * 8 * 32) {
     const int64_t row = base + lane;
     if (row < m) {
@@ -79,6 +98,7 @@ __global__ void __launch_bounds__(256) k_sketch_apply(const double* __restrict__
       for (int j = lane; j < ncol; j += 32) {
         const double a = j < n ? __ldcs(Ai + j) : b[i];
         bad |= !isfinite(a);
+        track_exp(a, j < n ? ea : eb);
         const double sa = a * scale;
         for (int k = 0; k < zeta; ++k) {
           const double v = flip_sign(sa, ((sg >> k) & 1ull) == 0ull);
@@ -89,6 +109,7 @@ __global__ void __launch_bounds__(256) k_sketch_apply(const double* __restrict__
     __syncwarp();
   }
   if (bad) atomicOr(status, DS_NONFINITE);
+  flush_range(ea, eb, range);
 }
 
 __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
@@ -96,6 +117,25 @@ __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, 
 }
 
 __device__ __forceinline__ float flip_sign_f(float v, bool neg) { return __uint_as_float(__float_as_uint(v) ^ ((uint32_t)neg << 31)); }
+
+// Vector atomic add that returns the four old values.
+__device__ __forceinline__ float4 atom_add_v4(float* p, float a, float b, float c, float d) {
+  float4 o;
+  asm volatile("atom.global.add.v4.f32 {%0, %1, %2, %3}, [%4], {%5, %6, %7, %8};"
+               : "=f"(o.x), "=f"(o.y), "=f"(o.z), "=f"(o.w)
+               : "l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+               : "memory");
+  return o;
+}
+
+// (old + v) - fl(old + v) exactly (Knuth's TwoSum): the rounding error of the
+// atomic add that turned `old` into fl(old + v), recomputed from its inputs.
+__device__ __forceinline__ float add_err(float old, float v) {
+  const float s = __fadd_rn(old, v);
+  const float bp = __fsub_rn(s, old);
+  const float ap = __fsub_rn(s, bp);
+  return __fadd_rn(__fsub_rn(old, ap), __fsub_rn(v, bp));
+}
 
 // FP64 entry -> nearest float using integer ops only (the FP64->FP32
 // conversion instruction runs at about one per clock per SM on this GPU).
@@ -107,13 +147,22 @@ __device__ __forceinline__ float to_float_int(double a) {
 
 // FP32 accumulation (mixed form) with 4-wide vector reductions: lane l owns
 // column groups 4(l + 32t) .. +3; entries past n are b_i (column n) or 0.
-// Requires ldy % 4 == 0 and Y 16-byte aligned.
-template <int N>
+// Requires ldy % 4 == 0 and Y (and Ylo) 16-byte aligned.
+//
+// COMP (compensated): every add into Y is a vector atomic that returns the
+// old values; the exact rounding error of each add (TwoSum of old and the
+// term) goes into Ylo with a vector reduction.  Y + Ylo then equals the exact
+// sum up to Ylo's own FP32 rounding, errors of size u^2 sqrt(N) relative for N
+// terms per entry, instead of u sqrt(N) for plain FP32 accumulation (with
+// about 5000 terms per entry at 5e6 rows and d = 8000, 1e-6 relative against
+// the 2.5e-8 of rounding an FP64 sketch once).  Atomics are issued eight
+// targets at a time so their round trips overlap.
+template <int N, bool COMP>
 __global__ void __launch_bounds__(256) k_sketch_apply_f32v(const double* __restrict__ A, int64_t m, int n, int64_t lda,
                                                            const double* __restrict__ b, uint64_t d, int zeta,
                                                            uint64_t seed, int64_t row0, float* __restrict__ Y,
-                                                           int64_t ldy, float scale, uint32_t* status,
-                                                           int32_t* max_rounds) {
+                                                           float* __restrict__ Ylo, int64_t ldy, float scale,
+                                                           uint32_t* status, int32_t* max_rounds, uint32_t* range) {
   extern __shared__ int32_t s_idx[];  // [8 warps][32 rows][N]
   __shared__ uint64_t s_sgn[8][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -121,6 +170,7 @@ __global__ void __launch_bounds__(256) k_sketch_apply_f32v(const double* __restr
   const int ncol = n + (b ? 1 : 0);
   const int ngroups = (ncol + 3) / 4;
   bool bad = false;
+  uint32_t ea = 0, eb = 0;
   for (int64_t base = ((int64_t)blockIdx.x * 8 + wib) * 32; base < m; base += (int64_t)gridDim.x * 8 * 32) {
     const int64_t row = base + lane;
     if (row < m) {
@@ -147,35 +197,97 @@ __global__ void __launch_bounds__(256) k_sketch_apply_f32v(const double* __restr
           const int j = 4 * g + q;
           const double a = j < n ? __ldcs(Ai + j) : (j == n && b ? b[i] : 0.0);
           bad |= !isfinite(a);
+          track_exp(a, j < n ? ea : eb);
           v[q] = __fmul_rn(to_float_int(a), scale);
         }
-        for (int k = 0; k < zeta; ++k) {
-          const bool neg = ((sg >> k) & 1ull) == 0ull;
-          red_add_v4(Y + (int64_t)ci[k] * ldy + 4 * g, flip_sign_f(v[0], neg), flip_sign_f(v[1], neg),
-                     flip_sign_f(v[2], neg), flip_sign_f(v[3], neg));
+        if (COMP) {
+          for (int k0 = 0; k0 < zeta; k0 += 8) {
+            float4 o[8];
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+              const int k = k0 + kk;
+              if (k < zeta) {
+                const bool neg = ((sg >> k) & 1ull) == 0ull;
+                o[kk] = atom_add_v4(Y + (int64_t)ci[k] * ldy + 4 * g, flip_sign_f(v[0], neg), flip_sign_f(v[1], neg),
+                                    flip_sign_f(v[2], neg), flip_sign_f(v[3], neg));
+              }
+            }
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+              const int k = k0 + kk;
+              if (k < zeta) {
+                const bool neg = ((sg >> k) & 1ull) == 0ull;
+                red_add_v4(Ylo + (int64_t)ci[k] * ldy + 4 * g, add_err(o[kk].x, flip_sign_f(v[0], neg)),
+                           add_err(o[kk].y, flip_sign_f(v[1], neg)), add_err(o[kk].z, flip_sign_f(v[2], neg)),
+                           add_err(o[kk].w, flip_sign_f(v[3], neg)));
+              }
+            }
+          }
+        } else {
+          for (int k = 0; k < zeta; ++k) {
+            const bool neg = ((sg >> k) & 1ull) == 0ull;
+            red_add_v4(Y + (int64_t)ci[k] * ldy + 4 * g, flip_sign_f(v[0], neg), flip_sign_f(v[1], neg),
+                       flip_sign_f(v[2], neg), flip_sign_f(v[3], neg));
+          }
         }
       }
     }
     __syncwarp();
   }
   if (bad) atomicOr(status, DS_NONFINITE);
+  flush_range(ea, eb, range);
+}
+
+// range_scan: one warp per row (grid-stride), lanes over the columns and b_i.
+__global__ void __launch_bounds__(256) k_range_scan(const double* __restrict__ A, int64_t m, int n, int64_t lda,
+                                                    const double* __restrict__ b, uint32_t* range, uint32_t* status) {
+  const int lane = threadIdx.x & 31;
+  uint32_t ea = 0, eb = 0;
+  bool bad = false;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < m; i += nwarps) {
+    const double* Ai = A + i * lda;
+    for (int j = lane; j < n; j += 32) {
+      const double a = __ldcs(Ai + j);
+      bad |= !isfinite(a);
+      track_exp(a, ea);
+    }
+    if (lane == 0 && b) {
+      bad |= !isfinite(b[i]);
+      track_exp(b[i], eb);
+    }
+  }
+  if (bad) atomicOr(status, DS_NONFINITE);
+  flush_range(ea, eb, range);
 }
 
 template <int N>
 cudaError_t launch_apply_f32v(const double* A, int64_t m, int n, int64_t lda, const double* b, int64_t d, int zeta,
-                              uint64_t seed, int64_t row0, float* Y, int64_t ldy, uint32_t* status,
-                              int32_t* max_rounds, int sms, cudaStream_t st) {
+                              uint64_t seed, int64_t row0, float* Y, float* Ylo, int64_t ldy, uint32_t* status,
+                              int32_t* max_rounds, uint32_t* range, int sms, cudaStream_t st) {
   const size_t smem = (size_t)8 * 32 * N * sizeof(int32_t);
-  cudaError_t e =
-      cudaFuncSetAttribute(k_sketch_apply_f32v<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const void* fn = Ylo ? (const void*)k_sketch_apply_f32v<N, true> : (const void*)k_sketch_apply_f32v<N, false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t groups = (m + 255) / 256;
   const int64_t blocks = std::min<int64_t>(groups, (int64_t)sms * 8);
-  if (blocks > 0)
-    k_sketch_apply_f32v<N><<<(unsigned)blocks, 256, smem, st>>>(A, m, n, lda, b, (uint64_t)d, zeta, seed, row0, Y,
-                                                                ldy, (float)(1.0 / sqrt((double)zeta)), status,
-                                                                max_rounds);
+  const float scale = (float)(1.0 / sqrt((double)zeta));
+  if (blocks > 0) {
+    if (Ylo)
+      k_sketch_apply_f32v<N, true><<<(unsigned)blocks, 256, smem, st>>>(A, m, n, lda, b, (uint64_t)d, zeta, seed,
+                                                                        row0, Y, Ylo, ldy, scale, status, max_rounds,
+                                                                        range);
+    else
+      k_sketch_apply_f32v<N, false><<<(unsigned)blocks, 256, smem, st>>>(A, m, n, lda, b, (uint64_t)d, zeta, seed,
+                                                                         row0, Y, nullptr, ldy, scale, status,
+                                                                         max_rounds, range);
+  }
   return cudaGetLastError();
+}
+
+__global__ void k_add_lo(float* __restrict__ Y, const float* __restrict__ Ylo, int64_t count) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+    Y[e] = __fadd_rn(Y[e], Ylo[e]);
 }
 
 template <int N>
@@ -191,7 +303,7 @@ cudaError_t launch_indices(uint64_t seed, int64_t row0, int64_t rows, int64_t d,
 template <int N, typename TY>
 cudaError_t launch_apply(const double* A, int64_t m, int n, int64_t lda, const double* b, int64_t d, int zeta,
                          uint64_t seed, int64_t row0, TY* Y, int64_t ldy, uint32_t* status, int32_t* max_rounds,
-                         int sms, cudaStream_t st) {
+                         uint32_t* range, int sms, cudaStream_t st) {
   const size_t smem = (size_t)8 * 32 * N * sizeof(int32_t);
   cudaError_t e = cudaFuncSetAttribute(k_sketch_apply<N, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -199,7 +311,7 @@ cudaError_t launch_apply(const double* A, int64_t m, int n, int64_t lda, const d
   const int64_t blocks = std::min<int64_t>(groups, (int64_t)sms * 8);
   if (blocks > 0)
     k_sketch_apply<N, TY><<<(unsigned)blocks, 256, smem, st>>>(A, m, n, lda, b, (uint64_t)d, zeta, seed, row0, Y, ldy,
-                                                               1.0 / sqrt((double)zeta), status, max_rounds);
+                                                               1.0 / sqrt((double)zeta), status, max_rounds, range);
   return cudaGetLastError();
 }
 
@@ -216,28 +328,54 @@ cudaError_t sketch_indices(uint64_t seed, int64_t row0, int64_t rows, int64_t d,
 template <typename TY>
 cudaError_t sketch_apply(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d, int zeta,
                          uint64_t seed, int64_t row0, TY* Y, int64_t ldy, uint32_t* status, int32_t* max_rounds,
-                         int sms, cudaStream_t st) {
+                         uint32_t* range, int sms, cudaStream_t st) {
   const int ni = (int)n;
-  if (sizeof(TY) == 4 && ldy % 4 == 0 && (uintptr_t)Y % 16 == 0) {
-    float* Yf = reinterpret_cast<float*>(Y);
-    if (zeta <= 8) return launch_apply_f32v<8>(A, m, ni, lda, b, d, zeta, seed, row0, Yf, ldy, status, max_rounds, sms, st);
-    if (zeta <= 16)
-      return launch_apply_f32v<16>(A, m, ni, lda, b, d, zeta, seed, row0, Yf, ldy, status, max_rounds, sms, st);
-    if (zeta <= 32)
-      return launch_apply_f32v<32>(A, m, ni, lda, b, d, zeta, seed, row0, Yf, ldy, status, max_rounds, sms, st);
-    return launch_apply_f32v<64>(A, m, ni, lda, b, d, zeta, seed, row0, Yf, ldy, status, max_rounds, sms, st);
-  }
-  if (zeta <= 8) return launch_apply<8, TY>(A, m, ni, lda, b, d, zeta, seed, row0, Y, ldy, status, max_rounds, sms, st);
+  if (sizeof(TY) == 4 && ldy % 4 == 0 && (uintptr_t)Y % 16 == 0)
+    return sketch_apply_f32c(A, m, n, lda, b, d, zeta, seed, row0, reinterpret_cast<float*>(Y), nullptr, ldy, status,
+                             max_rounds, range, sms, st);
+  if (zeta <= 8)
+    return launch_apply<8, TY>(A, m, ni, lda, b, d, zeta, seed, row0, Y, ldy, status, max_rounds, range, sms, st);
   if (zeta <= 16)
-    return launch_apply<16, TY>(A, m, ni, lda, b, d, zeta, seed, row0, Y, ldy, status, max_rounds, sms, st);
+    return launch_apply<16, TY>(A, m, ni, lda, b, d, zeta, seed, row0, Y, ldy, status, max_rounds, range, sms, st);
   if (zeta <= 32)
-    return launch_apply<32, TY>(A, m, ni, lda, b, d, zeta, seed, row0, Y, ldy, status, max_rounds, sms, st);
-  return launch_apply<64, TY>(A, m, ni, lda, b, d, zeta, seed, row0, Y, ldy, status, max_rounds, sms, st);
+    return launch_apply<32, TY>(A, m, ni, lda, b, d, zeta, seed, row0, Y, ldy, status, max_rounds, range, sms, st);
+  return launch_apply<64, TY>(A, m, ni, lda, b, d, zeta, seed, row0, Y, ldy, status, max_rounds, range, sms, st);
+}
+
+cudaError_t sketch_apply_f32c(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d,
+                              int zeta, uint64_t seed, int64_t row0, float* Y, float* Ylo, int64_t ldy,
+                              uint32_t* status, int32_t* max_rounds, uint32_t* range, int sms, cudaStream_t st) {
+  const int ni = (int)n;
+  if (ldy % 4 != 0 || (uintptr_t)Y % 16 != 0 || (uintptr_t)Ylo % 16 != 0) return cudaErrorInvalidValue;
+  if (zeta <= 8)
+    return launch_apply_f32v<8>(A, m, ni, lda, b, d, zeta, seed, row0, Y, Ylo, ldy, status, max_rounds, range, sms, st);
+  if (zeta <= 16)
+    return launch_apply_f32v<16>(A, m, ni, lda, b, d, zeta, seed, row0, Y, Ylo, ldy, status, max_rounds, range, sms,
+                                 st);
+  if (zeta <= 32)
+    return launch_apply_f32v<32>(A, m, ni, lda, b, d, zeta, seed, row0, Y, Ylo, ldy, status, max_rounds, range, sms,
+                                 st);
+  return launch_apply_f32v<64>(A, m, ni, lda, b, d, zeta, seed, row0, Y, Ylo, ldy, status, max_rounds, range, sms, st);
+}
+
+cudaError_t add_lo(float* Y, const float* Ylo, int64_t count, int sms, cudaStream_t st) {
+  const int64_t blocks = std::min<int64_t>((count + 255) / 256, (int64_t)sms * 8);
+  if (blocks > 0) k_add_lo<<<(unsigned)blocks, 256, 0, st>>>(Y, Ylo, count);
+  return cudaGetLastError();
+}
+
+cudaError_t range_scan(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, uint32_t* range,
+                       uint32_t* status, int sms, cudaStream_t st) {
+  const int64_t blocks = std::min<int64_t>((m + 7) / 8, (int64_t)sms * 8);
+  if (blocks > 0) k_range_scan<<<(unsigned)blocks, 256, 0, st>>>(A, m, (int)n, lda, b, range, status);
+  return cudaGetLastError();
 }
 
 template cudaError_t sketch_apply<double>(const double*, int64_t, int64_t, int64_t, const double*, int64_t, int,
-                                          uint64_t, int64_t, double*, int64_t, uint32_t*, int32_t*, int, cudaStream_t);
+                                          uint64_t, int64_t, double*, int64_t, uint32_t*, int32_t*, uint32_t*, int,
+                                          cudaStream_t);
 template cudaError_t sketch_apply<float>(const double*, int64_t, int64_t, int64_t, const double*, int64_t, int,
-                                         uint64_t, int64_t, float*, int64_t, uint32_t*, int32_t*, int, cudaStream_t);
+                                         uint64_t, int64_t, float*, int64_t, uint32_t*, int32_t*, uint32_t*, int,
+                                         cudaStream_t);
 
 }  // namespace lsq

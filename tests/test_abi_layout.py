@@ -24,7 +24,7 @@ STRUCTS = {  # C typedef -> binding class name
 }
 CONSTANTS = {  # C macro or enumerator -> binding name
     "LSQ_OK": "LSQ_OK", "LSQ_PENDING": "LSQ_PENDING", "LSQ_ERR_ARG": "LSQ_ERR_ARG",
-    "LSQ_ERR_NOCONV": "LSQ_ERR_NOCONV",
+    "LSQ_ERR_NOCONV": "LSQ_ERR_NOCONV", "LSQ_ERR_TIMEOUT": "LSQ_ERR_TIMEOUT", "LSQ_ERR_ACCURACY": "LSQ_ERR_ACCURACY",
     "LSQ_PREC_FP64": "PREC_FP64", "LSQ_PREC_MIXED": "PREC_MIXED",
     "LSQ_MEM_DEVICE": "MEM_DEVICE", "LSQ_MEM_HOST": "MEM_HOST",
     "LSQ_FLAG_TIMING": "FLAG_TIMING", "LSQ_FLAG_NO_CHECK": "FLAG_NO_CHECK",
