@@ -1,12 +1,16 @@
-"""Benchmark: least-squares solves per second on a dense 2,000,000 x 500 FP64
-problem (singular values 1..1e-10, 1% coherent rows x1e4, ||r_perp|| = 1e-6),
-sparse sign sketch d = 2000, zeta = 8, LSQR tolerance 1e-12.
+"""Benchmark: least-squares solves per second on the largest single-GPU
+configuration, a dense 5,000,000 x 2000 FP64 problem (80 GB; singular values
+geometric 1..1e-8; b = A x_true + 1e-6 g/||g||), sparse sign sketch d = 8000,
+zeta = 8, LSQR tolerance 1e-12, at backward error <= 1e-10.  The headline is
+the plain FP64 form; the mixed form (FP32 compensated sketch, FP32 QR) runs on
+the same A and b beside it, and the 2,000,000 x 500 coherent-row problem
+(d = 2000) is reported as an extra key.
 
 One step = one full solve (sketch + preconditioner + LSQR + accuracy pass)
 through the library's C ABI.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--config 0|1] [--prec fp64|mixed] [--native]
+                  [--config 0|1|2|3|4] [--prec fp64|mixed] [--native]
 
 Under torchrun (N > 1) every rank solves its own copy of the problem on its
 own GPU (the path does not shard in this build: replicas only); the value is
@@ -156,12 +160,21 @@ def lsqr_algorithmic_bytes(m, n, iters):
     return iters * (8.0 * m * n + 16.0 * m + 16.0 * n * n) + 2 * (8.0 * m * n + 16.0 * m)
 
 
-def cpu_oracle_estimate(A_host, b_host, d, zeta, seed, tol, iters, rows=100_000, lsqr_iters=3):
+def host_cores():
+    """Threads this process may run on (sched_getaffinity)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def cpu_oracle_estimate(A_host, b_host, d, zeta, seed, tol, iters, rows=100_000, lsqr_iters=3, qr_cache=None):
     """Time the oracle on a bounded sample of the workload and scale to one
     full solve: sketch and LSQR passes are linear in m (timed on the first
     `rows` rows and scaled by m/rows); the QR + inverse of the d x (n+1)
-    sketch is timed at full size; LSQR is timed for `lsqr_iters` iterations and
-    scaled to `iters` (+2 passes for the initial residual and the check)."""
+    sketch is timed at full size (once, when qr_cache holds it); LSQR is timed
+    for `lsqr_iters` iterations and scaled to `iters` (+2 passes for the
+    initial residual and the check)."""
     import numpy as np
 
     import oracle
@@ -172,10 +185,16 @@ def cpu_oracle_estimate(A_host, b_host, d, zeta, seed, tol, iters, rows=100_000,
     t0 = time.perf_counter()
     Y = oracle.sketch_apply(As, bs, d, zeta, seed)
     t_sketch = (time.perf_counter() - t0) * (m / rows)
-    t0 = time.perf_counter()
-    R, _, _ = oracle.householder_qr(Y)
+    if qr_cache is not None and "t_qr" in qr_cache:
+        t_qr, R = qr_cache["t_qr"], qr_cache["R"]
+    else:
+        t0 = time.perf_counter()
+        R, _, _ = oracle.householder_qr(Y)
+        oracle.tri_inverse(R[:n, :n])
+        t_qr = time.perf_counter() - t0
+        if qr_cache is not None:
+            qr_cache.update(t_qr=t_qr, R=R)
     M = oracle.tri_inverse(R[:n, :n])
-    t_qr = time.perf_counter() - t0
     x0 = M @ R[:n, n]
     t0 = time.perf_counter()
     oracle.lsqr(As, bs, M, x0, 0.0, lsqr_iters)
@@ -185,43 +204,79 @@ def cpu_oracle_estimate(A_host, b_host, d, zeta, seed, tol, iters, rows=100_000,
     t_total = t_sketch + t_qr + per_pass * (1 + 2 * iters + 1)
     return {"t_solve_s": t_total, "t_sketch_s": t_sketch, "t_qr_s": t_qr, "t_pass_s": per_pass,
             "sample": f"first {rows} of {m} rows: oracle sketch and {lsqr_iters} LSQR iterations timed and scaled "
-                      f"by m/rows; QR+inverse of the full {d}x{n + 1} sketch timed; LSQR scaled to {iters} "
+                      f"by m/rows; QR+inverse of the full {d}x{n + 1} sketch timed"
+                      f"{' once per process' if qr_cache is not None else ''}; LSQR scaled to {iters} "
                       f"iterations + 2 passes"}
 
 
+# ---------------------------------------------------------------------------
+# The headline configuration: 5e6 x 2000 (80 GB), plain and mixed forms.
+# ---------------------------------------------------------------------------
+C2 = {"m": 5_000_000, "n": 2000, "cond": 1e8, "d": 8000, "zeta": 8, "tol": 1e-12, "seed": 20, "sketch_seed": 7}
+
+
+def c2_config(m, n, cond, d, zeta, tol):
+    """The config dict both arms print (identical keys and values)."""
+    return {"workload": f"dense_{m}x{n}_cond{cond:.0e}_d{d}_zeta{zeta}_tol{tol:g}",
+            "m": m, "n": n, "d": d, "zeta": zeta, "tol": tol,
+            "construction": "A = (G/sqrt(m)) diag(s) H1 H2 built in place, s geometric 1..1/cond; "
+                            "b = A x_true + 1e-6 g/||g||",
+            "l2_policy": "inputs larger than L2 (A is %.0f GB vs 129 MB L2)" % (8 * m * n / 1e9)}
+
+
+def c2_shape(args):
+    m, n = args.m or C2["m"], args.n or C2["n"]
+    cond = args.cond if args.cond != 1e10 else C2["cond"]
+    return m, n, cond, 4 * n, C2["zeta"], C2["tol"]
+
+
 def run_reference(args):
+    """The reference arm: the CPU oracle (OpenMP build, all host cores) on a
+    bounded sample of this arm's workload (the headline by default), each step
+    re-timing the sample's sketch and LSQR passes (the QR of the full-size
+    sketch is timed once per process)."""
     world, rank, local = _dist()
     if rank != 0:
         return
-    import numpy as np
     import torch
+
     import oracle
-    oracle.build()
+    from paper_2506_03070_gb300 import synth
+    cores = host_cores()
+    oracle.use_parallel(cores)
     dev = "cuda" if torch.cuda.is_available() else "cpu"
-    p = make_problem(args.config, dev if args.config == 1 else "cpu")
-    A, b = p["A"], p["b"]
-    m, n = A.shape
-    rows = min(m, 60_000 if args.config == 1 else m)
-    Ah = A[:rows].cpu().numpy()
-    bh = b[:rows].cpu().numpy()
-    del A
-    iters_est = oracle.default_maxit(n, p["d"], p["tol"]) // 10  # rate estimate of Sec. 4.3
+    if args.config in (0, 1):
+        p = make_problem(args.config, dev if args.config == 1 else "cpu")
+        m, n = p["A"].shape
+        d, zeta, tol, seed = p["d"], p["zeta"], p["tol"], p["seed_sketch"]
+        rows = min(m, 60_000)
+        Ah, bh = p["A"][:rows].cpu().numpy(), p["b"][:rows].cpu().numpy()
+        config = _workload(p, "fp64")
+    else:
+        m, n, cond, d, zeta, tol = c2_shape(args)
+        seed = C2["sketch_seed"]
+        rows = min(m, 20_000)
+        p = synth.large_problem(m, n, cond, seed=C2["seed"], device=dev, rows=rows)
+        Ah, bh = p["A"].cpu().numpy(), p["b"].cpu().numpy()
+        config = c2_config(m, n, cond, d, zeta, tol)
+    del p
+    iters_est = oracle.default_maxit(n, d, tol) // 10  # rate estimate of Sec. 4.3
+    cache = {}
     times = []
     info = None
     for step in range(args.warmup + args.steps):
-        info = cpu_oracle_estimate(_Scaled(Ah, m), bh, p["d"], p["zeta"], p["seed_sketch"], p["tol"], iters_est,
-                                   rows=rows, lsqr_iters=2)
+        info = cpu_oracle_estimate(_Scaled(Ah, m), bh, d, zeta, seed, tol, iters_est, rows=rows, lsqr_iters=2,
+                                   qr_cache=cache)
         if step >= args.warmup:
             times.append(info["t_solve_s"])
     t = statistics.mean(times)
-    cores = 1
     val = 1.0 / t
+    sample = info["sample"] + f" ({'device-generated rows, copied to host' if dev == 'cuda' else 'host-generated'})"
     line = {"metric": "ls_solves_per_sec", "value": val, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _workload(p, "fp64"), "impl": "reference",
-            "cpu_baseline": {"kind": "oracle", "value": val, "unit": "solves/s", "cores": cores,
-                             "sample": info["sample"]},
+            "config": config, "impl": "reference",
+            "cpu_baseline": {"kind": "oracle", "value": val, "unit": "solves/s", "cores": cores, "sample": sample},
             "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -342,7 +397,7 @@ def _oracle_cost_model():
     import numpy as np
 
     import oracle
-    oracle.build()
+    oracle.use_parallel(host_cores())
     from paper_2506_03070_gb300 import synth
     m, n, d = 20000, 200, 800
     p = synth.batched_problem(m, n, 1e6, seed=3, device="cpu")
@@ -499,85 +554,229 @@ def run_serve(args):
             it = 2 * (10 * math.ceil(math.log(1e-12) / math.log(math.sqrt(n / d)))) // 10
             tot += (cm["sketch_per_entry"] * m * (n + 1) + cm["qr_per_flop"] * 2.0 * d * (n + 1) ** 2
                     + cm["pass_per_entry"] * m * n * (2 * it + 2))
-        line["cpu_baseline"] = {"value": len(seq_idx) / tot, "unit": "solves/s", "cores": 1, "kind": "oracle",
+        line["cpu_baseline"] = {"value": len(seq_idx) / tot, "unit": "solves/s", "cores": host_cores(),
+                                "kind": "oracle",
                                 "sample": cm["sample"] + f"; applied to the first {len(seq_idx)} requests "
                                           "(an extrapolation)"}
     print(json.dumps(line))
     ctx.close()
 
 
-def run_mixed(args):
-    """Config 2: the mixed form (FP32 sketch and QR) against the plain FP64 form
-    on the same 5,000,000 x 2000 problem (80 GB), d = 8000, zeta = 8."""
+def _mem_available_bytes():
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
+def launches_per_solve(n, d, prec, blocked):
+    """Kernels of this library one lsq_solve launches: sketch, column-major
+    copy, QR (unblocked: 1; blocked: per panel the panel kernel, T, and the
+    three trailing-update GEMMs plus the Gram GEMM), R extraction, inverse,
+    transpose, x0, M^T copy, LSQR (+ the accuracy pass, same kernel)."""
+    if not blocked:
+        qr = 1
+    else:
+        nb = 64 if prec == 1 else 32
+        panels = (n + nb - 1) // nb
+        qr = panels * 6 - 5  # the last panel has no trailing columns except b
+    return 1 + 1 + qr + 4 + 1 + 1
+
+
+def run_headline(args):
+    """The largest single-GPU configuration (5e6 x 2000, 80 GB): the plain FP64
+    form is the headline value; the mixed form solves the same A and b."""
+    import numpy as np
     import torch
 
-    import paper_2506_03070_gb300 as P
-    import __graft_entry__
-    __graft_entry__.build()
     world, rank, local = _dist()
     torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2506_03070_gb300 as P
     from paper_2506_03070_gb300 import synth
-    m, n = args.m or 5_000_000, args.n or 2000
-    d, zeta, tol, cond = 4 * n, 8, 1e-12, args.cond if args.cond != 1e10 else 1e8
-    p = synth.large_problem(m, n, cond, seed=20, device=f"cuda:{local}")
+
+    m, n, cond, d, zeta, tol = c2_shape(args)
+    dev = f"cuda:{local}"
+    p = synth.large_problem(m, n, cond, seed=C2["seed"], device=dev)
     A, b = p["A"], p["b"]
+    del p
     torch.cuda.synchronize()
     ctx = P.Context(local)
     stream = torch.cuda.current_stream()
-    res = {}
+    flags = P.FLAG_TIMING
+
+    def solve(prec):
+        return ctx.lsq_solve(A, b, d, zeta=zeta, seed=C2["sketch_seed"], tol=tol, prec=prec, flags=flags,
+                             stream=stream)
+
+    for _ in range(args.warmup):
+        x, info = solve(P.PREC_FP64)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     sampler = ClockSampler(local)
     sampler.start()
-    for prec in (P.PREC_FP64, P.PREC_MIXED):
-        for _ in range(args.warmup):
-            x, info = ctx.lsq_solve(A, b, d, zeta=zeta, seed=7, tol=tol, prec=prec, flags=P.FLAG_TIMING,
-                                    stream=stream)
-        ms, infos = [], []
-        for _ in range(args.steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            x, info = ctx.lsq_solve(A, b, d, zeta=zeta, seed=7, tol=tol, prec=prec, flags=P.FLAG_TIMING,
-                                    stream=stream)
-            e1.record(stream)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
-            infos.append(info)
-        res[prec] = (statistics.mean(ms), infos[-1], x.clone())
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ms, infos = [], []
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x, info = solve(P.PREC_FP64)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        infos.append(info)
+    ev1.record(stream)
+    torch.cuda.synchronize()
     clocks = sampler.stop()
+    total_ms = ev0.elapsed_time(ev1)
+    t_max = max_over_ranks(total_ms, dev)
+    value = world * args.steps / (t_max / 1e3)
+    xp = x.clone()
+
+    # the mixed form on the same A and b (extra key; fewer timed solves)
+    km = max(1, min(args.steps, 5))
+    for _ in range(min(args.warmup, 2)):
+        xm, im = solve(P.PREC_MIXED)
+    mixed_ms, minfos = [], []
+    for _ in range(km):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xm, im = solve(P.PREC_MIXED)
+        e1.record(stream)
+        e1.synchronize()
+        mixed_ms.append(e0.elapsed_time(e1))
+        minfos.append(im)
+    bn = float(torch.linalg.vector_norm(b))
+    dist_mp = float(torch.linalg.vector_norm(A @ (xm - xp))) / bn
+    # accuracy of the mixed solution by the same FP64 pass
+    chk_m = ctx.lsq_check(A, b, xm)
+
     peaks, peak_src = _peaks()
     peak = float(peaks["hbm_gbs"])
-    out = {}
-    for prec, tag in ((P.PREC_FP64, "plain"), (P.PREC_MIXED, "mixed")):
-        t, info, _ = res[prec]
-        alg = lsqr_algorithmic_bytes(m, n, info["iters"])
-        out[tag] = {"solves_per_s": 1e3 / t, "ms_per_solve": t, "lsqr_iters": info["iters"],
-                    "phases_ms": {"sketch": info["t_sketch_ms"], "precond": info["t_precond_ms"],
-                                  "lsqr_and_check": info["t_lsqr_ms"]},
-                    "precond_fallback": info["precond_fallback"],
-                    "lsqr_gbs": alg / (info["t_lsqr_ms"] / 1e3) / 1e9,
-                    "backward_error_ne": info["backward_error_ne"]}
-    xp, xm = res[P.PREC_FP64][2], res[P.PREC_MIXED][2]
-    dist = float(torch.linalg.vector_norm(A @ (xm - xp)) / torch.linalg.vector_norm(b))
-    tp = res[P.PREC_FP64][1]
-    alg = lsqr_algorithmic_bytes(m, n, tp["iters"])
-    achieved = alg / (tp["t_lsqr_ms"] / 1e3) / 1e9
-    line = {"metric": "ls_solves_per_sec", "value": out["mixed"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["mixed"]["ms_per_solve"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"mixed_vs_plain_{m}x{n}_cond{cond:.0e}_d{d}_zeta{zeta}_tol{tol:g}",
-                       "construction": "cheap (G/sqrt(m)) diag(s) H1 H2, built in place",
-                       "l2_policy": "inputs larger than L2 (A is %.0f GB)" % (8 * m * n / 1e9)},
-            "roofline": {"bound": "hbm", "kernel": "k_lsqr_dfp (plain form)", "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                         "peak_source": f"{peak_src} hbm_gbs"},
-            "gpu_launches": 8 * args.steps * 2,
-            "plain": out["plain"], "mixed": out["mixed"],
-            "mixed_over_plain": out["mixed"]["solves_per_s"] / out["plain"]["solves_per_s"],
-            "accuracy": {"rel_residual_distance_mixed_vs_plain": dist,
-                         "backward_error_ne_plain": out["plain"]["backward_error_ne"],
-                         "note": "KW estimate not computed at this size (needs a second 80 GB copy of A)"},
-            "clocks": clocks}
-    print(json.dumps(line))
+    it = statistics.mean(i["iters"] for i in infos)
+    t_lsqr = statistics.mean(i["t_lsqr_ms"] for i in infos)
+    t_check = statistics.mean(i["t_check_ms"] for i in infos)
+    alg = lsqr_algorithmic_bytes(m, n, it)
+    achieved = alg / (t_lsqr / 1e3) / 1e9
+    alg_iter = it * (8.0 * m * n + 16.0 * m + 16.0 * n * n) + (8.0 * m * n + 16.0 * m)
+    achieved_iter = alg_iter / ((t_lsqr - t_check) / 1e3) / 1e9 if t_lsqr > t_check else None
+    sketch_ms = statistics.mean(i["t_sketch_ms"] for i in infos)
+    precond_ms = statistics.mean(i["t_precond_ms"] for i in infos)
+    blocked = n >= 1700
+    per_solve = launches_per_solve(n, d, 0, blocked)
+
+    def phase(ii):
+        return {"sketch": statistics.mean(i["t_sketch_ms"] for i in ii),
+                "precond": statistics.mean(i["t_precond_ms"] for i in ii),
+                "lsqr_and_check": statistics.mean(i["t_lsqr_ms"] for i in ii),
+                "check": statistics.mean(i["t_check_ms"] for i in ii)}
+
+    mixed_val = 1e3 / statistics.mean(mixed_ms)
+    line = {
+        "metric": "ls_solves_per_sec", "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": c2_config(m, n, cond, d, zeta, tol),
+        "lsqr_arith": "df47 (A as float pairs of its top 47 bits, pair sums; FP64 recurrences; native FP64 check)",
+        "roofline": {"bound": "hbm", "kernel": "k_lsqr_dfp<4> (LSQR + accuracy pass, one launch per solve)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json, of measured)",
+                     "algorithmic_bytes_per_launch": alg,
+                     "achieved_excluding_check": achieved_iter,
+                     "check_pass_ms": t_check,
+                     "check_pass_gbs": (8.0 * m * n + 16.0 * m) / (t_check / 1e3) / 1e9 if t_check > 0 else None},
+        "gpu_launches": per_solve * args.steps,
+        "latency_ms": {"p50": statistics.median(step_ms),
+                       "p99": sorted(step_ms)[min(len(step_ms) - 1, int(0.99 * len(step_ms)))]},
+        "phases_ms": {"sketch": sketch_ms, "precond": precond_ms, "lsqr_and_check": t_lsqr, "check": t_check},
+        "sketch_gbs": (8.0 * m * (n + 1) + 8.0 * d * (n + 1)) / (sketch_ms / 1e3) / 1e9,
+        "lsqr_iters": it,
+        "accuracy": {"backward_error_ne": infos[-1]["backward_error_ne"],
+                     "backward_error_pre": infos[-1]["backward_error_pre"],
+                     "gate_bound": min(infos[-1]["backward_error_ne"], infos[-1]["backward_error_pre"]),
+                     "note": "FP64 accuracy pass on the device: Stewart's bound ||A^T r||/(||A||_F ||r||) and "
+                             "||M^T A^T r||/(||A||_F ||x||) (bounds the Karlson-Walden estimate up to the "
+                             "sketch distortion); the oracle's KW needs a QR of [||x|| A; ||r|| I] (80 GB)"},
+        "mixed": {"solves_per_s": mixed_val, "ms_per_solve": statistics.mean(mixed_ms), "steps": km,
+                  "lsqr_iters": statistics.mean(i["iters"] for i in minfos), "phases_ms": phase(minfos),
+                  "precond_fallback": minfos[-1]["precond_fallback"], "status": minfos[-1]["status"],
+                  "mixed_over_plain": mixed_val / value * world,
+                  "rel_residual_distance_to_plain": dist_mp,
+                  "backward_error_ne": chk_m["backward_error_ne"], "backward_error_pre": minfos[-1][
+                      "backward_error_pre"],
+                  "dtype": "sketch: FP32 compensated accumulation; QR: FP32; LSQR: df47 + FP64 recurrences"},
+        "clocks": clocks,
+    }
+
+    # e2e: host (pinned) A, b through the same C ABI, copies inside the timed region
+    e2e = None
+    need = 8 * m * n + 8 * m
+    if not args.no_e2e and _mem_available_bytes() > 1.25 * need:
+        try:
+            Ah = torch.empty((m, n), dtype=torch.float64, pin_memory=True)
+            bh = torch.empty((m,), dtype=torch.float64, pin_memory=True)
+            Ah.copy_(A)
+            bh.copy_(b)
+            Anp, bnp = Ah.numpy(), bh.numpy()
+            xh = np.empty(n, dtype=np.float64)
+            ctx.lsq_solve(Anp, bnp, d, zeta=zeta, seed=C2["sketch_seed"], tol=tol, flags=flags, x=xh)
+            k2 = max(1, min(args.steps, 3))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(k2):
+                ctx.lsq_solve(Anp, bnp, d, zeta=zeta, seed=C2["sketch_seed"], tol=tol, flags=flags, x=xh)
+            t_e2e = time.perf_counter() - t0
+            e2e = {"value": world * k2 / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": 8 * m * n + 8 * m,
+                   "d2h_bytes_per_step": 8 * n + 4096, "steps": k2}
+            del Ah, bh, Anp, bnp
+        except Exception as exc:  # pinned allocation of the whole problem refused
+            e2e = {"value": None, "unit": "solves/s", "h2d_bytes_per_step": need, "d2h_bytes_per_step": 8 * n,
+                   "unavailable": f"{type(exc).__name__}: {exc}"[:200]}
+    elif not args.no_e2e:
+        e2e = {"value": None, "unit": "solves/s", "h2d_bytes_per_step": need, "d2h_bytes_per_step": 8 * n,
+               "unavailable": f"host memory available ({_mem_available_bytes() / 1e9:.0f} GB) below the pinned "
+                              f"copy of A and b ({need / 1e9:.0f} GB)"}
+    line["e2e"] = e2e
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        cores = host_cores()
+        oracle.use_parallel(cores)
+        rows = min(m, 20_000)
+        Ah2 = A[:rows].cpu().numpy()
+        bh2 = b[:rows].cpu().numpy()
+        est = cpu_oracle_estimate(_Scaled(Ah2, m), bh2, d, zeta, C2["sketch_seed"], tol, int(round(it)), rows=rows,
+                                  lsqr_iters=2)
+        line["cpu_baseline"] = {"value": 1.0 / est["t_solve_s"], "unit": "solves/s", "cores": cores,
+                                "kind": "oracle", "sample": est["sample"] + " (OpenMP build, -O3 -fopenmp)"}
+    del A, b, x, xp, xm
     ctx.close()
+    torch.cuda.empty_cache()
+
+    if rank == 0 and world == 1 and not args.no_c1:
+        # the 2,000,000 x 500 coherent-row configuration as an extra key
+        import copy
+        a1 = copy.copy(args)
+        a1.config, a1.m, a1.n, a1.cond, a1.steps, a1.warmup = 1, 0, 0, 1e10, min(args.steps, 5), min(args.warmup, 3)
+        a1.no_e2e, a1.no_cpu_baseline = True, True
+        c1 = run_gpu(a1, emit=False)
+        line["c1"] = {k: c1[k] for k in ("value", "ms_per_step", "config", "roofline", "phases_ms", "lsqr_iters",
+                                         "accuracy", "auto_d", "hbm", "sketch_gbs") if k in c1}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
 
 
 def run_sparse(args):
@@ -633,13 +832,15 @@ def run_sparse(args):
     ctx.close()
 
 
-def run_gpu(args):
+def run_gpu(args, emit=True):
+    """Configs 0 and 1 (one problem per rank).  Returns the JSON line (and
+    prints it when emit)."""
     import numpy as np
     import torch
 
     world, rank, local = _dist()
     torch.cuda.set_device(local)
-    if world > 1:
+    if world > 1 and emit:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import __graft_entry__
@@ -729,7 +930,7 @@ def run_gpu(args):
         "metric": "ls_solves_per_sec", "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(_workload(p, args.prec), parallelism="replicas" if world > 1 else "single"),
+        "config": _workload(p, args.prec),
         "roofline": {"bound": "hbm", "kernel": "k_lsqr_native" if args.native else "k_lsqr_df", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None if (args.native or n > 512 or args.prec != "fp64" or not LSQR_DF_TRAFFIC_CURRENT)
@@ -790,19 +991,21 @@ def run_gpu(args):
                        "lsqr_phase_ms": ih["t_lsqr_ms"], "backward_error_kw": oracle.backward_error_kw(A, b, xh)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle as orc
-        orc.build()
+        cores = host_cores()
+        orc.use_parallel(cores)
         rows = 100_000 if m > 100_000 else m
         Ah2 = A[:rows].cpu().numpy()
         bh2 = b[:rows].cpu().numpy()
         est = cpu_oracle_estimate(_Scaled(Ah2, m), bh2, d, zeta, seed, tol, int(round(it_mean)), rows=rows,
                                   lsqr_iters=2)
-        line["cpu_baseline"] = {"value": 1.0 / est["t_solve_s"], "unit": "solves/s", "cores": 1, "kind": "oracle",
-                                "sample": est["sample"]}
-    if rank == 0:
+        line["cpu_baseline"] = {"value": 1.0 / est["t_solve_s"], "unit": "solves/s", "cores": cores, "kind": "oracle",
+                                "sample": est["sample"] + " (OpenMP build, -O3 -fopenmp)"}
+    if rank == 0 and emit:
         print(json.dumps(line))
-    if world > 1:
+    if world > 1 and emit:
         torch.distributed.destroy_process_group()
     ctx.close()
+    return line
 
 
 def main():
@@ -811,7 +1014,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=1, choices=[0, 1, 2, 3, 4])
+    ap.add_argument("--config", type=int, default=2, choices=[0, 1, 2, 3, 4],
+                    help="2 (default): the 5e6 x 2000 headline with plain and mixed forms; 1: 2e6 x 500; "
+                         "0: 20000 x 200; 3: batched; 4: serving")
     ap.add_argument("--requests", type=int, default=10000, help="serving: requests in the Poisson stream")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean arrival rate (1/s)")
     ap.add_argument("--sub-requests", type=int, default=1000, help="serving: requests of the extra sub-saturation run")
@@ -836,11 +1041,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-auto-d", action="store_true", help="skip the extra solve with the chosen embedding dimension")
     ap.add_argument("--sparse", action="store_true", help="the paper's 5e5_500_sparse workload (CSR path)")
+    ap.add_argument("--no-c1", action="store_true", help="headline: skip the extra 2e6 x 500 solves")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
-    elif args.config == 2:
-        run_mixed(args)
+    elif args.config == 2 and not args.sparse:
+        run_headline(args)
     elif args.config == 3:
         run_batch(args)
     elif args.config == 4:

@@ -43,8 +43,12 @@ _lib = None
 ORC_OK, ORC_ERR_ARG, ORC_ERR_SKETCH, ORC_ERR_RANK, ORC_ERR_NOCONV, ORC_ERR_OOM = 0, -1, -2, -3, -4, -5
 
 
+_OMP_PATH = os.path.join(_BUILD, "liblsq_oracle_omp.so")
+
+
 def build(force: bool = False) -> str:
-    """Compile lsq_oracle.c with gcc (plain -O2, no fast-math, no OpenMP)."""
+    """Compile lsq_oracle.c with gcc (plain -O2, no fast-math, no OpenMP): the
+    single-threaded checker every test uses."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
@@ -52,6 +56,29 @@ def build(force: bool = False) -> str:
         subprocess.check_call(cmd)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+def build_parallel(force: bool = False) -> str:
+    """The same source with -O3 -fopenmp: the CPU-baseline build that the
+    benchmark times on all host cores (row loops on every thread, per-thread
+    partial sums added in thread order).  Tests never load it."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_OMP_PATH) or os.path.getmtime(_OMP_PATH) < os.path.getmtime(_SRC):
+        tmp = _OMP_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O3", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp", "-o", tmp, _SRC,
+               "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _OMP_PATH)
+    return _OMP_PATH
+
+
+def use_parallel(threads: int) -> None:
+    """Switch this process's oracle calls to the OpenMP build on `threads`
+    threads (the benchmark's CPU baseline only)."""
+    global _lib
+    os.environ["OMP_NUM_THREADS"] = str(int(threads))
+    _lib = None
+    _load(build_parallel())
 
 
 class LsqrInfo(ctypes.Structure):
@@ -65,25 +92,28 @@ class SolveInfo(ctypes.Structure):
 
 
 def lib():
-    global _lib
     if _lib is None:
-        path = build()
-        L = ctypes.CDLL(path)
-        P = ctypes.c_void_p
-        i64, i32, u64, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_double
-        L.orc_philox4x64_10.argtypes = [P, P, P]
-        L.orc_philox4x64_10.restype = None
-        L.orc_sketch_row.argtypes = [u64, i64, i64, i32, P, P]
-        L.orc_sketch_indices.argtypes = [u64, i64, i64, i64, i32, P, P, P]
-        L.orc_sketch_apply.argtypes = [P, i64, i64, i64, P, i64, i32, u64, i64, P, i64]
-        L.orc_householder_qr.argtypes = [P, i64, i64, i64, P]
-        L.orc_tri_inverse.argtypes = [P, i64, i64, P, i64]
-        L.orc_lsqr.argtypes = [P, i64, i64, i64, P, P, P, f64, i64, P, P, P, P]
-        L.orc_backward_error.argtypes = [P, i64, i64, i64, P, P, f64, P]
-        L.orc_backward_error.restype = f64
-        L.orc_solve.argtypes = [P, i64, i64, i64, P, i64, i32, u64, f64, i64, P, P, P, P, P]
-        _lib = L
+        _load(build())
     return _lib
+
+
+def _load(path):
+    global _lib
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i64, i32, u64, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_double
+    L.orc_philox4x64_10.argtypes = [P, P, P]
+    L.orc_philox4x64_10.restype = None
+    L.orc_sketch_row.argtypes = [u64, i64, i64, i32, P, P]
+    L.orc_sketch_indices.argtypes = [u64, i64, i64, i64, i32, P, P, P]
+    L.orc_sketch_apply.argtypes = [P, i64, i64, i64, P, i64, i32, u64, i64, P, i64]
+    L.orc_householder_qr.argtypes = [P, i64, i64, i64, P]
+    L.orc_tri_inverse.argtypes = [P, i64, i64, P, i64]
+    L.orc_lsqr.argtypes = [P, i64, i64, i64, P, P, P, f64, i64, P, P, P, P]
+    L.orc_backward_error.argtypes = [P, i64, i64, i64, P, P, f64, P]
+    L.orc_backward_error.restype = f64
+    L.orc_solve.argtypes = [P, i64, i64, i64, P, i64, i32, u64, f64, i64, P, P, P, P, P]
+    _lib = L
 
 
 def _p(a):

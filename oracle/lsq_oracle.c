@@ -29,6 +29,16 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Built two ways.  The checker build (tests, smoke) is plain single-threaded
+ * C: every loop runs in the order written here.  The CPU-baseline build adds
+ * -fopenmp: the row loops of the sketch and of the matvecs, the trailing
+ * columns of each Householder step and the columns of the inverse run on all
+ * host threads (partial sums of per-thread copies added in thread order), the
+ * same operations in a different summation order.  Nothing else changes. */
 
 #define ORC_OK 0
 #define ORC_ERR_ARG (-1)
@@ -179,6 +189,41 @@ int orc_sketch_apply(const double* A, int64_t m, int64_t n, int64_t lda, const d
   for (int64_t r = 0; r < d; ++r)
     for (int64_t j = 0; j < ldy; ++j) Y[r * ldy + j] = 0.0;
   const double scale = 1.0 / sqrt((double)zeta);
+#ifdef _OPENMP
+  /* CPU-baseline build: each thread sketches a contiguous block of rows into
+   * its own copy of Y; the copies are added in thread order */
+  const int nt = omp_get_max_threads();
+  double* priv = nt > 1 ? (double*)calloc((size_t)nt * (size_t)d * (size_t)ldy, sizeof(double)) : NULL;
+  if (priv) {
+    int fail = 0;
+#pragma omp parallel num_threads(nt)
+    {
+      double* Yt = priv + (size_t)omp_get_thread_num() * (size_t)d * (size_t)ldy;
+      int32_t idx[ORC_MAX_ZETA];
+      int8_t sgn[ORC_MAX_ZETA];
+#pragma omp for schedule(static)
+      for (int64_t i = 0; i < m; ++i) {
+        if (orc_sketch_row(seed, row0 + i, d, zeta, idx, sgn) < 0) {
+#pragma omp atomic write
+          fail = 1;
+          continue;
+        }
+        for (int k = 0; k < zeta; ++k) {
+          double s = sgn[k] > 0 ? scale : -scale;
+          double* y = Yt + (int64_t)idx[k] * ldy;
+          for (int64_t j = 0; j < n; ++j) y[j] += s * A[i * lda + j];
+          if (b) y[n] += s * b[i];
+        }
+      }
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < d; ++r)
+      for (int t = 0; t < nt; ++t)
+        for (int64_t j = 0; j < ldy; ++j) Y[r * ldy + j] += priv[((size_t)t * d + r) * ldy + j];
+    free(priv);
+    return fail ? ORC_ERR_SKETCH : ORC_OK;
+  }
+#endif
   int32_t idx[ORC_MAX_ZETA];
   int8_t sgn[ORC_MAX_ZETA];
   for (int64_t i = 0; i < m; ++i) {
@@ -217,6 +262,7 @@ int orc_householder_qr(double* Y, int64_t rows, int64_t cols, int64_t ld, double
     tau[k] = (beta - alpha) / beta;
     for (int64_t i = k + 1; i < rows; ++i) Y[i * ld + k] /= v0;
     Y[k * ld + k] = beta;
+#pragma omp parallel for schedule(static)
     for (int64_t j = k + 1; j < cols; ++j) {
       double dot = Y[k * ld + j];
       for (int64_t i = k + 1; i < rows; ++i) dot += Y[i * ld + k] * Y[i * ld + j];
@@ -237,6 +283,7 @@ int orc_tri_inverse(const double* R, int64_t n, int64_t ldr, double* M, int64_t 
     if (R[i * ldr + i] == 0.0) return ORC_ERR_RANK;
   for (int64_t i = 0; i < n; ++i)
     for (int64_t c = 0; c < n; ++c) M[i * ldm + c] = 0.0;
+#pragma omp parallel for schedule(dynamic, 8)
   for (int64_t c = 0; c < n; ++c) {
     M[c * ldm + c] = 1.0 / R[c * ldr + c];
     for (int64_t i = c - 1; i >= 0; --i) {
@@ -250,6 +297,7 @@ int orc_tri_inverse(const double* R, int64_t n, int64_t ldr, double* M, int64_t 
 
 /* y = A x (m), y = A^T z (n), y = M x, y = M^T x : plain loops */
 static void mv_A(const double* A, int64_t m, int64_t n, int64_t lda, const double* x, double* y) {
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < m; ++i) {
     double s = 0.0;
     for (int64_t j = 0; j < n; ++j) s += A[i * lda + j] * x[j];
@@ -258,6 +306,25 @@ static void mv_A(const double* A, int64_t m, int64_t n, int64_t lda, const doubl
 }
 static void mv_At(const double* A, int64_t m, int64_t n, int64_t lda, const double* z, double* y) {
   for (int64_t j = 0; j < n; ++j) y[j] = 0.0;
+#ifdef _OPENMP
+  /* CPU-baseline build: per-thread partial sums over contiguous row blocks,
+   * added in thread order */
+  const int nt = omp_get_max_threads();
+  double* part = nt > 1 ? (double*)calloc((size_t)nt * (size_t)n, sizeof(double)) : NULL;
+  if (part) {
+#pragma omp parallel num_threads(nt)
+    {
+      double* yt = part + (size_t)omp_get_thread_num() * (size_t)n;
+#pragma omp for schedule(static)
+      for (int64_t i = 0; i < m; ++i)
+        for (int64_t j = 0; j < n; ++j) yt[j] += A[i * lda + j] * z[i];
+    }
+    for (int t = 0; t < nt; ++t)
+      for (int64_t j = 0; j < n; ++j) y[j] += part[(size_t)t * n + j];
+    free(part);
+    return;
+  }
+#endif
   for (int64_t i = 0; i < m; ++i)
     for (int64_t j = 0; j < n; ++j) y[j] += A[i * lda + j] * z[i];
 }

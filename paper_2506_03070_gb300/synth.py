@@ -114,26 +114,37 @@ def batched_problem(m, n, cond, *, seed, device="cpu", dtype=torch.float64):
     return {"A": A.contiguous(), "b": b, "x_true": x_true, "cond": cond}
 
 
-def large_problem(m, n, cond, *, seed, device="cuda", chunk_rows=1 << 18, dtype=torch.float64):
+def large_problem(m, n, cond, *, seed, device="cuda", chunk_rows=1 << 18, dtype=torch.float64, rows=None):
     """Cheap construction of ``batched_problem`` built in place: A (m x n) is the
     only full-size allocation; G, diag(s) and the two reflectors are applied
     chunk by chunk of rows.  cond(A) is within (1+sqrt(n/m))/(1-sqrt(n/m)) of
-    ``cond``."""
+    ``cond``.  With ``rows``, only the first ``rows`` rows of the m-row problem
+    are built (A, b), the same values as the full construction's first rows on
+    the same device (a bounded sample of the workload)."""
     dev = torch.device(device)
     gen = _gen(dev, seed)
-    A = torch.empty((m, n), device=dev, dtype=dtype)
+    mr = m if rows is None else min(int(rows), m)
+    A = torch.empty((mr, n), device=dev, dtype=dtype)
     s = torch.logspace(0.0, -math.log10(cond), n, device=dev, dtype=dtype) / math.sqrt(m)
     vs = [_householder(n, _gen(dev, seed + 1 + k), dev, dtype) for k in range(2)]
-    for r0 in range(0, m, chunk_rows):
+    for r0 in range(0, mr, chunk_rows):
         blk = A[r0:r0 + chunk_rows]
-        blk.normal_(generator=gen)
+        if blk.shape[0] < chunk_rows and mr < m:
+            # a partial last chunk of a sample: draw the full chunk so the
+            # generator's stream (and so every value) matches the full build
+            full = torch.empty((min(chunk_rows, m - r0), n), device=dev, dtype=dtype)
+            full.normal_(generator=gen)
+            blk.copy_(full[: blk.shape[0]])
+            del full
+        else:
+            blk.normal_(generator=gen)
         blk.mul_(s)
         for v in vs:
             blk.addr_(blk @ v, v, alpha=-2.0)
     x_true = torch.randn(n, generator=_gen(dev, seed + 3), device=dev, dtype=dtype)
     g = torch.randn(m, generator=_gen(dev, seed + 4), device=dev, dtype=dtype)
     b = A @ x_true
-    b.add_(g, alpha=1e-6 / float(torch.linalg.vector_norm(g)))
+    b.add_(g[:mr], alpha=1e-6 / float(torch.linalg.vector_norm(g)))
     del g
     return {"A": A, "b": b, "x_true": x_true, "cond": cond}
 
