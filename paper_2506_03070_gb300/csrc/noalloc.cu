@@ -12,8 +12,9 @@
 // loads the library holds for the life of the process (about 4.1 MB).  The
 // caller passes only inputs and outputs.  Host code never uses the array's
 // name as an address: the device address comes from cudaGetSymbolAddress,
-// looked up once per device, with that device current, on the first call made
-// on it (make that first call before any stream capture).  Every call on a
+// looked up once per device (and per driver context, for callers that make
+// their own context current), with that device current, on the first call
+// made there (make that first call before any stream capture).  Every call on a
 // device reuses the same array and leaves its contents behind; the barrier
 // and status words are cleared at the start of each call and every other
 // region is fully rewritten before it is read.  Two calls whose work overlaps
@@ -42,18 +43,52 @@ constexpr size_t kScratchBytes = kOffMt + (size_t)kNoallocMaxN * kNoallocMaxN * 
 static __device__ __align__(256) unsigned char g_check_scratch[kScratchBytes];
 
 std::mutex g_setup_mutex;
-void* g_scratch_addr[kNoallocMaxDevices] = {};
+// (device, CUDA context) -> device address of g_check_scratch in that context.
+// The runtime uses the device's primary context unless the caller made
+// another context current through the driver API; the array has a separate
+// copy (and address) in every context that loaded the library.
+struct ScratchEntry {
+  int dev;
+  void* cuctx;
+  void* addr;
+};
+ScratchEntry g_entries[kNoallocMaxDevices];
+int g_nentries = 0;
 
-// Device address of g_check_scratch on the current device (looked up once).
+// The current driver context (cuCtxGetCurrent through the runtime's entry
+// point query: the library links no driver library).
+void* current_cuctx() {
+  typedef int (*GetCurrent)(void**);
+  static GetCurrent fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<GetCurrent>(f);
+    looked = true;
+  }
+  void* c = nullptr;
+  if (fn && fn(&c) != 0) c = nullptr;
+  return c;
+}
+
+// Device address of g_check_scratch for the current device and context
+// (looked up once per pair, with that device current).
 cudaError_t scratch_address(int dev, void** out) {
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_check_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  void* cctx = current_cuctx();
+  for (int i = 0; i < g_nentries; ++i)
+    if (g_entries[i].dev == dev && g_entries[i].cuctx == cctx) {
+      *out = g_entries[i].addr;
+      return cudaSuccess;
+    }
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_check_scratch);
+  if (e != cudaSuccess) return e;
+  if (g_nentries < kNoallocMaxDevices) g_entries[g_nentries++] = ScratchEntry{dev, cctx, p};
+  *out = p;
   return cudaSuccess;
 }
 
@@ -107,8 +142,9 @@ extern "C" lsq_status lsq_check_noalloc(const double* A, int64_t m, int64_t n, i
   p.ldi = (n + 1) / 2 * 2;
   p.vec = vec;
   p.a_ring = false;
-  p.check_df = false;
   p.ring_k = 1;
+  p.range = nullptr;
+  p.gate = 0.0;
   p.bar = bar;
   p.status = status;
   p.out = out;

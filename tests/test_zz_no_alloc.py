@@ -54,15 +54,16 @@ def _same(a, ref):
 def test_noalloc_matches_lsq_check_twice_in_a_row(lib_and_ctx):
     P, L, ctx = lib_and_ctx
     A1, b1, x1, M1 = _problem(5003, 37, 1)   # odd n: unaligned-row path
-    A2, b2, x2, _ = _problem(20000, 200, 2)  # even n: vector path
+    A2, b2, x2, M2 = _problem(20000, 200, 2)  # even n: vector path, another M
     first = _noalloc(P, L, A1, b1, x1, M1)
-    second = _noalloc(P, L, A2, b2, x2, None)
+    second = _noalloc(P, L, A2, b2, x2, M2)
     _same(first, ctx.lsq_check(A1, b1, x1, M1))
-    ref2 = ctx.lsq_check(A2, b2, x2)
-    _same(second, ref2)
-    assert second["backward_error_pre"] == 0.0  # nothing left over from the first call
+    _same(second, ctx.lsq_check(A2, b2, x2, M2))
+    # a call after a larger one: nothing left over from the 200-column call
     third = _noalloc(P, L, A1, b1, x1, M1)
     _same(third, first)
+    no_m = _noalloc(P, L, A2, b2, x2, None)
+    _same(no_m, ctx.lsq_check(A2, b2, x2))
 
 
 def test_noalloc_rejects_n_beyond_its_scratch(lib_and_ctx):
