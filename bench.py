@@ -574,15 +574,15 @@ def _mem_available_bytes():
 
 def launches_per_solve(n, d, prec, blocked):
     """Kernels of this library one lsq_solve launches: sketch, column-major
-    copy, QR (unblocked: 1; blocked: per panel the panel kernel, T, and the
-    three trailing-update GEMMs plus the Gram GEMM), R extraction, inverse,
-    transpose, x0, M^T copy, LSQR (+ the accuracy pass, same kernel)."""
+    copy, QR (unblocked: 1 kernel; blocked, per 64-column panel: the panel
+    kernel, four slicing kernels, three tensor-core GEMMs and T; the last
+    panel only the panel kernel), R extraction, inverse, transpose, x0, M^T
+    copy, LSQR (+ the accuracy pass, same kernel)."""
     if not blocked:
         qr = 1
     else:
-        nb = 64 if prec == 1 else 32
-        panels = (n + nb - 1) // nb
-        qr = panels * 6 - 5  # the last panel has no trailing columns except b
+        panels = (n + 63) // 64
+        qr = (panels - 1) * 9 + 1
     return 1 + 1 + qr + 4 + 1 + 1
 
 

@@ -2,9 +2,10 @@
 
 Each translation unit under csrc/ compiles in parallel, then one shared object
 is linked next to this file (git-ignored).  The CUDA runtime is linked
-statically; cuBLAS (the blocked QR's trailing-update GEMMs) is linked from the
-toolkit's lib64 with that directory as the run path.  The library loads on a
-machine without a GPU (for the ABI symbol check).
+statically and no other library is: every kernel on the path is the
+library's own (driver entry points such as the TMA descriptor encoder are
+fetched through the runtime at run time).  The library loads on a machine
+without a GPU (for the ABI symbol check).
 """
 from __future__ import annotations
 
@@ -66,9 +67,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        cudalib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
-        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-L", cudalib, "-lcublas", "-Xlinker", "-rpath",
-             "-Xlinker", cudalib])
+        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
         os.replace(tmp, LIB)
     return LIB
 

@@ -8,8 +8,6 @@
 #include <cstring>
 #include <string>
 
-#include <cublas_v2.h>
-
 #include "ctx.h"
 
 using namespace lsq;
@@ -139,19 +137,6 @@ lsq_status read_small(lsq_ctx* ctx, cudaStream_t st, uint32_t* bits, int32_t* ro
   return LSQ_OK;
 }
 
-// cuBLAS handle of the context (null if it cannot be created: the QR then
-// runs unblocked).
-void* blas_handle(lsq_ctx* ctx) {
-  if (!ctx->blas && !ctx->blas_failed) {
-    cublasHandle_t h = nullptr;
-    if (cublasCreate(&h) == CUBLAS_STATUS_SUCCESS)
-      ctx->blas = h;
-    else
-      ctx->blas_failed = true;
-  }
-  return ctx->blas;
-}
-
 bool vec_ok(const double* A, int64_t lda) { return ((uintptr_t)A % 16 == 0) && (lda % 2 == 0); }
 
 int64_t default_maxit(int64_t n, int64_t d, double tol) {
@@ -203,7 +188,7 @@ void fill_info(lsq_info* info, const double* out, lsq_status st, int32_t rounds)
 lsq_status run_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int n, int64_t lda, const double* b, const double* M,
                     const double* Mt, double* x, double tol, int64_t maxit, int mode, const LsqrWork& w, int grid,
                     int npad, bool native, cudaStream_t st, double hbm_alpha = 0.0, double hbm_beta = 0.0,
-                    double gate = 0.0) {
+                    double gate = 0.0, const double* fro_in = nullptr) {
   LsqrParams p;
   p.A = A;
   p.m = m;
@@ -218,6 +203,7 @@ lsq_status run_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int n, int64_t lda
   p.ring_k = 1;
   p.range = ctx->d_range;
   p.gate = gate;
+  p.fro_in = fro_in;
   p.M = M;
   p.Mt = Mt;
   p.x = x;
@@ -295,7 +281,6 @@ lsq_status calibrate_d(lsq_ctx* ctx, int64_t n64, lsq_ctx::DCalib* out) {
   carve(cv, &A, &b, &x, &M, &lw, &Y, &pb, &R2, &M2, &x0);
   pb.bar = ctx->d_bar;
   pb.status = ctx->d_status;
-  pb.blas = blas_handle(ctx);
   pb.mode = ctx->qr_mode;
   cudaStream_t st = nullptr;
   CK(fill_hash(A, mc, n, n, 11, ctx->sms, st));
@@ -376,6 +361,7 @@ lsq_status lsq_create(lsq_ctx** out, int device, size_t hbm_budget_bytes) {
   ctx->d_bar = reinterpret_cast<GridBarrier*>(small + 128);
   ctx->d_out = reinterpret_cast<double*>(small + 256);
   ctx->d_range = reinterpret_cast<uint32_t*>(small + 1024);
+  ctx->d_fro = reinterpret_cast<double*>(small + 1040);
   if (cudaMallocHost(&ctx->h_small, kSmallBytes) != cudaSuccess) {
     cudaFree(small);
     delete ctx;
@@ -392,7 +378,6 @@ lsq_status lsq_destroy(lsq_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->server) server_destroy(ctx->server);
   ctx->server = nullptr;
-  if (ctx->blas) cublasDestroy(static_cast<cublasHandle_t>(ctx->blas));
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->h_small) cudaFreeHost(ctx->h_small);
@@ -544,18 +529,18 @@ lsq_status lsq_sketch(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64
   CK(cudaMemsetAsync(Y, 0, (size_t)d * ldy * esz, st));
   if (prec == LSQ_PREC_FP64) {
     CK(sketch_apply<double>(A, m, n, lda, b, d, zeta, seed, 0, (double*)Y, ldy, ctx->d_status, ctx->d_max_rounds,
-                            nullptr, ctx->sms, st));
+                            nullptr, nullptr, ctx->sms, st));
   } else if (ldy % 4 == 0 && (uintptr_t)Y % 16 == 0) {
     // compensated FP32 accumulation (error terms in workspace), then Y += Ylo
     if ((s = ensure_ws(ctx, align_up((size_t)d * ldy * sizeof(float)))) != LSQ_OK) return s;
     float* Ylo = reinterpret_cast<float*>(ctx->ws);
     CK(cudaMemsetAsync(Ylo, 0, (size_t)d * ldy * sizeof(float), st));
     CK(sketch_apply_f32c(A, m, n, lda, b, d, zeta, seed, 0, (float*)Y, Ylo, ldy, ctx->d_status, ctx->d_max_rounds,
-                         nullptr, ctx->sms, st));
+                         nullptr, nullptr, ctx->sms, st));
     CK(add_lo((float*)Y, Ylo, d * ldy, ctx->sms, st));
   } else {
     CK(sketch_apply<float>(A, m, n, lda, b, d, zeta, seed, 0, (float*)Y, ldy, ctx->d_status, ctx->d_max_rounds,
-                           nullptr, ctx->sms, st));
+                           nullptr, nullptr, ctx->sms, st));
   }
   uint32_t bits = 0;
   if ((s = read_small(ctx, st, &bits, nullptr, nullptr)) != LSQ_OK) return s;
@@ -587,7 +572,6 @@ lsq_status lsq_precond(lsq_ctx* ctx, const void* Y, int64_t d, int64_t n, int64_
   buf.R = cv.take<double>((size_t)n * n);
   buf.Mt = cv.take<double>((size_t)n * n);
   buf.blk = cv.take<char>(precond_blocked_bytes(d, n));
-  buf.blas = blas_handle(ctx);
   buf.mode = ctx->qr_mode;
   buf.bar = ctx->d_bar;
   buf.status = ctx->d_status;
@@ -826,7 +810,6 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
   carve(cv, &A, &b, &xd, &Y, &pb, &R, &M, &lw);
   pb.bar = ctx->d_bar;
   pb.status = ctx->d_status;
-  pb.blas = blas_handle(ctx);
   pb.mode = ctx->qr_mode;
 
   Events<6> ev;
@@ -847,13 +830,13 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
   // the double-float LSQR passes
   if (o->prec == LSQ_PREC_FP64) {
     CK(sketch_apply<double>(A, m, n, lda_dev, b, d, o->zeta, o->seed, 0, (double*)Y, ldy, ctx->d_status,
-                            ctx->d_max_rounds, ctx->d_range, ctx->sms, st));
+                            ctx->d_max_rounds, ctx->d_range, ctx->d_fro, ctx->sms, st));
   } else {
     // compensated FP32 accumulation: Y + Ylo, summed once into the QR's copy
     CK(cudaMemsetAsync(const_cast<void*>(pb.Ylo), 0, (size_t)d * ldy * sizeof(float), st));
     CK(sketch_apply_f32c(A, m, n, lda_dev, b, d, o->zeta, o->seed, 0, (float*)Y,
                          static_cast<float*>(const_cast<void*>(pb.Ylo)), ldy, ctx->d_status, ctx->d_max_rounds,
-                         ctx->d_range, ctx->sms, st));
+                         ctx->d_range, ctx->d_fro, ctx->sms, st));
   }
   if (timing) CK(cudaEventRecord(ev[2], st));
   if (o->prec == LSQ_PREC_FP64)
@@ -894,7 +877,8 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
   // heavy-ball momentum: App. C.2 parameters with the distortion estimate sqrt(n/d)
   const double e2 = (double)n / (double)d;
   if ((s = run_lsqr(ctx, A, m, ni, lda_dev, b, M, lw.Mt, xd, o->tol, maxit, mode, lw, grid, npad, native, st,
-                    hbm ? (1.0 - e2) * (1.0 - e2) : 0.0, hbm ? e2 : 0.0, solve_gate(o->tol, o->gate))) != LSQ_OK)
+                    hbm ? (1.0 - e2) * (1.0 - e2) : 0.0, hbm ? e2 : 0.0, solve_gate(o->tol, o->gate),
+                    ctx->d_fro)) != LSQ_OK)
     return s;
   if (timing) CK(cudaEventRecord(ev[4], st));
   if (host) CK(cudaMemcpyAsync(x, xd, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
@@ -1006,7 +990,6 @@ lsq_status lsq_solve_csr(lsq_ctx* ctx, const lsq_csr_problem* pr, const lsq_opts
   carve(cv, &Y, &pb, &R, &M, &lw);
   pb.bar = ctx->d_bar;
   pb.status = ctx->d_status;
-  pb.blas = blas_handle(ctx);
   pb.mode = ctx->qr_mode;
   Events<4> ev;
   if (timing) CK(ev.create());

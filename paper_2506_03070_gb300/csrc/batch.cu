@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(BatchParams bp) {
     p.a_ring = p.vec && (n % 2 == 0);
     p.range = range;
     p.gate = bp.mode == 0 ? fmax(1e-10, bp.tol) : 0.0;
+    p.fro_in = nullptr;
     p.M = M;
     p.Mt = Mt;
     p.x = it.x;

@@ -27,14 +27,12 @@ struct lsq_ctx {
   lsq::GridBarrier* d_bar = nullptr;
   double* d_out = nullptr;
   uint32_t* d_range = nullptr;  // [2] exponent maxima of A and b (pass_scale)
+  double* d_fro = nullptr;      // sum of A_ij^2 formed by the sketch of lsq_solve
   uint32_t wait_limit_us = 0;   // limit of every device wait (0: the built-in 20 s)
   // pinned host mirror of the small words
   void* h_small = nullptr;
   // batched solves: tuned LSQR pass shapes per n-range
   lsq::BatchTuning* tuning = nullptr;
-  // cublasHandle_t of the blocked QR's trailing updates (created on first use)
-  void* blas = nullptr;
-  bool blas_failed = false;
   int qr_mode = 0;  // LSQ_QR_AUTO / LSQ_QR_UNBLOCKED / LSQ_QR_BLOCKED
   // embedding-dimension calibration per width n: seconds per row of one LSQR
   // iteration, seconds per extra sketch row of the preconditioner

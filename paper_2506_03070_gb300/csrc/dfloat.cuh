@@ -93,6 +93,39 @@ __device__ __forceinline__ df df_renorm(df a) {
   return r;
 }
 
+// ---------------------------------------------------------------------------
+// The same pair arithmetic on two independent lanes at once with the packed
+// FP32x2 instructions (sm_100 and later): every operation is the one of the
+// scalar form on each half, in the same order with the same rounding, so the
+// results are bit for bit those of the scalar functions; each packed
+// instruction does two of them.  (hi, lo) accumulators are float2 pairs:
+// hi = (hi_0, hi_1), lo = (lo_0, lo_1).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// acc += a * w for two entries: a = (hi, mid), w = (w1, w2), as df_fma_acc.
+__device__ __forceinline__ void df2_fma_acc(float2& acc_hi, float2& acc_lo, float2 hi, float2 mid, float2 w1,
+                                            float2 w2) {
+  const float2 p = __fmul2_rn(hi, w1);
+  float2 e = __ffma2_rn(hi, w1, neg2(p));
+  e = __ffma2_rn(hi, w2, e);
+  e = __ffma2_rn(mid, w1, e);
+  // two_sum(acc_hi, p)
+  const float2 s = __fadd2_rn(acc_hi, p);
+  const float2 bp = __fadd2_rn(s, neg2(acc_hi));
+  const float2 ap = __fadd2_rn(s, neg2(bp));
+  const float2 err = __fadd2_rn(__fadd2_rn(acc_hi, neg2(ap)), __fadd2_rn(p, neg2(bp)));
+  acc_hi = s;
+  acc_lo = __fadd2_rn(acc_lo, __fadd2_rn(err, e));
+}
+
+// df_renorm on two pairs.
+__device__ __forceinline__ void df2_renorm(float2& hi, float2& lo) {
+  const float2 s = __fadd2_rn(hi, lo);
+  lo = __fadd2_rn(lo, neg2(__fadd2_rn(s, neg2(hi))));
+  hi = s;
+}
+
 // Exact integer split of an FP64 value into (hi, mid) floats; see above.
 __device__ __forceinline__ void split2(double a, float& hi, float& mid) {
   const uint32_t hw = (uint32_t)__double2hiint(a), lw = (uint32_t)__double2loint(a);

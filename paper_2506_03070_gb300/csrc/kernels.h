@@ -14,16 +14,18 @@ cudaError_t sketch_indices(uint64_t seed, int64_t row0, int64_t rows, int64_t d,
                            int32_t* rounds, uint32_t* status, int32_t* max_rounds, int sms, cudaStream_t st);
 // range (nullable, [2] words, zeroed by the caller): atomic max of the
 // exponent field (high word & 0x7FF00000) over A's and over b's finite entries.
+// fro (nullable, zeroed by the caller): FP64 sum of A_ij^2 (atomic adds of warp partials).
 template <typename TY>
 cudaError_t sketch_apply(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d, int zeta,
                          uint64_t seed, int64_t row0, TY* Y, int64_t ldy, uint32_t* status, int32_t* max_rounds,
-                         uint32_t* range, int sms, cudaStream_t st);
+                         uint32_t* range, double* fro, int sms, cudaStream_t st);
 // Mixed form: FP32 accumulation into Y (ldy % 4 == 0, 16-byte aligned); with
 // Ylo (same shape, zeroed) non-null, compensated: the exact rounding error of
 // every add goes into Ylo, and Y + Ylo is the sketch to about u^2 sqrt(N).
 cudaError_t sketch_apply_f32c(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d,
                               int zeta, uint64_t seed, int64_t row0, float* Y, float* Ylo, int64_t ldy,
-                              uint32_t* status, int32_t* max_rounds, uint32_t* range, int sms, cudaStream_t st);
+                              uint32_t* status, int32_t* max_rounds, uint32_t* range, double* fro, int sms,
+                              cudaStream_t st);
 // Y[e] = fl32(Y[e] + Ylo[e]) for e < count.
 cudaError_t add_lo(float* Y, const float* Ylo, int64_t count, int sms, cudaStream_t st);
 // The same range words (and DS_NONFINITE) from one read of A and b, for LSQR
@@ -40,7 +42,6 @@ struct PrecondBuffers {
   GridBarrier* bar;
   uint32_t* status;
   void* blk;       // precond_blocked_bytes(d, n) of scratch for the blocked QR, or null (unblocked)
-  void* blas;      // cublasHandle_t for the blocked QR's trailing updates
   int mode;        // 0: choose by size, 1: unblocked, 2: blocked (LSQ_QR_*)
   const void* Ylo = nullptr;  // compensated FP32 sketch: error terms added to Y (same type and layout), or null
 };
@@ -60,6 +61,7 @@ struct OzGemm {
   const void* a;  // __nv_bfloat16 slices of A's M rows
   const void* b;  // __nv_bfloat16 slices of B's N rows
   int M, N, K, Kpad;
+  int a_rows, b_rows;  // rows per slice in the slice arrays (>= M resp. N, >= the 128 / 64 row boxes)
   const int* ea;
   const int* eb;
   int mode;       // 0: out[a * ldo + b] += D (FP64 atomics, out zeroed by the caller); 1: out[b * ldo + a] -= D
@@ -72,10 +74,11 @@ struct OzGemm {
 };
 int oz_kpad(int K);
 // Slices of R rows of length K (row r at X + r ldx), or with T (b x b, K = b)
-// of the rows of U T^T for column-major U (X, ld ldx).
+// of the rows of U T^T for column-major U (X, ld ldx); out is [S][Rpad][Kpad]
+// with zero rows past R and zero columns past K.
 template <typename TX>
 cudaError_t oz_slice(const TX* X, int R, int K, int64_t ldx, const double* T, int S, void* out, int Kpad, int* ex,
-                     int sms, cudaStream_t st);
+                     int Rpad, int sms, cudaStream_t st);
 cudaError_t oz_gemm(const OzGemm& g, cudaStream_t st);
 
 // LSQR and the accuracy pass (lsqr.cu).
@@ -86,7 +89,7 @@ struct LsqrParams {
   int npad;
   int64_t lda;
   const double* b;
-  float2* asplit;    // m x ldi (hi, mid) float-pair image of A written by the first pass, or null
+  float2* asplit;    // m x ldi float-pair image of A (pair-major per column pair) written by the first pass, or null
   int64_t ldi;       // image row length: n rounded up to even
   bool a_ring;       // A rows can come through bulk copies (n even, lda even, A 16-byte aligned)
   bool vec;          // A rows allow 16-byte vector loads (lda even, A aligned)
@@ -111,6 +114,7 @@ struct LsqrParams {
                      // 3 = heavy-ball momentum then check, 4 = heavy-ball momentum only
   double hbm_alpha, hbm_beta;  // step and momentum of modes 3 and 4
   double gate;       // > 0: the accuracy pass raises DS_ACCURACY when min(eta_ne, eta_pre) > gate
+  const double* fro_in;  // sum of A_ij^2 formed by the sketch (FP64), or null: the accuracy pass forms it
   int gidx, gcount;  // this block's index among the blocks sharing the problem (set in-kernel)
   GridBarrier* bar;
   uint32_t* status;

@@ -170,9 +170,12 @@ struct NativePass {
     p.gparts = p.gcount;
     pass_native<T, VEC, false, false>(p, p.wv, 1.0, p.u, gamma, p.u, s_g, s_scal);
   }
-  __device__ void check(LsqrParams& p) {  // y = b - A x; sum y^2, b^2, A_ij^2
+  __device__ void check(LsqrParams& p) {  // y = b - A x; sum y^2, b^2 (and A_ij^2 unless known)
     p.gparts = p.gcount;
-    pass_native<T, VEC, true, true>(p, p.x, -1.0, p.b, -1.0, nullptr, s_g, s_scal);
+    if (p.fro_in)
+      pass_native<T, VEC, false, true>(p, p.x, -1.0, p.b, -1.0, nullptr, s_g, s_scal);
+    else
+      pass_native<T, VEC, true, true>(p, p.x, -1.0, p.b, -1.0, nullptr, s_g, s_scal);
   }
   __device__ void residual(LsqrParams& p, bool) {  // y = b - A x; sum y^2, b^2
     p.gparts = p.gcount;
@@ -386,8 +389,11 @@ __device__ void pass_native_panel(const LsqrParams& p, double* s_scal) {
 // The first pass reads A (through the ring when n and lda are even and A is
 // aligned, by direct loads otherwise) and, when p.asplit is set, stores every
 // split row as a (hi, mid) float-pair image of A (ldi entries per row, 8 bytes
-// each, as FP64); later passes stream the image: identical values, and the
-// per-entry integer split leaves the hot loop.
+// each, as FP64), pair-major per column pair: hi_c, hi_c+1, mid_c, mid_c+1;
+// later passes stream the image: identical values, and the per-entry integer
+// split leaves the hot loop.  The pass vector sits in shared memory the same
+// way (w1_c, w1_c+1, w2_c, w2_c+1), so the packed FP32x2 instructions take two
+// columns' operands straight from one 16-byte load.
 // --------------------------------------------------------------------------
 template <int L, int PPL, bool CHUNKED = false, int PW = 1>
 struct DfPass {
@@ -433,11 +439,17 @@ struct DfPass {
   }
 
   // column pairs summed over the R segments, then added to the warp's FP64 row
-  __device__ void flush(df (&Gc)[2 * PPL], double* gw, int cl, int seg, int n, bool& first, double gmul) {
+  __device__ void flush(float2 (&Gh)[PPL], float2 (&Gl)[PPL], double* gw, int cl, int seg, int n, bool& first,
+                        double gmul) {
 #pragma unroll
-    for (int q = 0; q < 2 * PPL; ++q) {
+    for (int t = 0; t < PPL; ++t) {
 #pragma unroll
-      for (int o = L; o < 32; o <<= 1) Gc[q] = df_add(Gc[q], shfl_xor_df(Gc[q], o));
+      for (int o = L; o < 32; o <<= 1) {
+        const df a = df_add(df{Gh[t].x, Gl[t].x}, shfl_xor_df(df{Gh[t].x, Gl[t].x}, o));
+        const df b = df_add(df{Gh[t].y, Gl[t].y}, shfl_xor_df(df{Gh[t].y, Gl[t].y}, o));
+        Gh[t] = make_float2(a.hi, b.hi);
+        Gl[t] = make_float2(a.lo, b.lo);
+      }
     }
     if (seg == 0) {
 #pragma unroll
@@ -445,14 +457,14 @@ struct DfPass {
         const int c = 2 * cl + 2 * L * t;
         if (c < n) {
           double2 g = first ? make_double2(0.0, 0.0) : *reinterpret_cast<const double2*>(gw + c);
-          g.x += df_to_double(Gc[2 * t]) * gmul;
-          g.y += df_to_double(Gc[2 * t + 1]) * gmul;
+          g.x += df_to_double(df{Gh[t].x, Gl[t].x}) * gmul;
+          g.y += df_to_double(df{Gh[t].y, Gl[t].y}) * gmul;
           *reinterpret_cast<double2*>(gw + c) = g;
         }
       }
     }
 #pragma unroll
-    for (int q = 0; q < 2 * PPL; ++q) Gc[q] = df{0.f, 0.f};
+    for (int t = 0; t < PPL; ++t) Gh[t] = Gl[t] = make_float2(0.f, 0.f);
     first = false;
   }
 
@@ -480,15 +492,18 @@ struct DfPass {
     const unsigned long long lim = wait_limit_ns(p.bar);
 
     // the pass vector (scaled by 2^(sa-sb)) as float pairs in shared memory (read per entry)
-    for (int c = threadIdx.x; c < p.ldi; c += kThreads) {
-      const double v = c < n ? wsign * wvec[c] * sc.w : 0.0;
-      const float v1 = __double2float_rn(v);
-      s_w[c] = make_float2(v1, __double2float_rn(v - (double)v1));
+    for (int c = 2 * threadIdx.x; c < p.ldi; c += 2 * kThreads) {
+      const double v0 = c < n ? wsign * wvec[c] * sc.w : 0.0;
+      const double v1 = c + 1 < n ? wsign * wvec[c + 1] * sc.w : 0.0;
+      const float a0 = __double2float_rn(v0), a1 = __double2float_rn(v1);
+      *reinterpret_cast<float4*>(s_w + c) =
+          make_float4(a0, a1, __double2float_rn(v0 - (double)a0), __double2float_rn(v1 - (double)a1));
     }
     __syncthreads();
-    df Gc[2 * PPL];
+    // column accumulators of the lane's column pairs (entries 2t, 2t+1 packed)
+    float2 Gh[PPL], Gl[PPL];
 #pragma unroll
-    for (int q = 0; q < 2 * PPL; ++q) Gc[q] = df{0.f, 0.f};
+    for (int t = 0; t < PPL; ++t) Gh[t] = Gl[t] = make_float2(0.f, 0.f);
     const float g1 = __double2float_rn(gamma);
     const df gdf{g1, __double2float_rn(gamma - (double)g1)};
     df ss{0.f, 0.f}, bb{0.f, 0.f}, fro{0.f, 0.f};
@@ -524,7 +539,8 @@ struct DfPass {
           else
             uu = ubuf[row];
         }
-        float h[2 * PPL], mm[2 * PPL];
+        // the lane's column pairs, pair-major: H[t] = (hi_c, hi_c+1), Mm[t] = (mid_c, mid_c+1)
+        float2 H[PPL], Mm[PPL];
 #pragma unroll
         for (int t = 0; t < PPL; ++t) {
           const int c = 2 * cl + 2 * L * t;
@@ -532,10 +548,8 @@ struct DfPass {
           if (FROM_IMAGE) {
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (in) v = *reinterpret_cast<const float4*>(buf + c);
-            h[2 * t] = v.x;
-            mm[2 * t] = v.y;
-            h[2 * t + 1] = v.z;
-            mm[2 * t + 1] = v.w;
+            H[t] = make_float2(v.x, v.y);
+            Mm[t] = make_float2(v.z, v.w);
           } else {
             double2 v = make_double2(0.0, 0.0);
             if (p.a_ring) {
@@ -545,29 +559,23 @@ struct DfPass {
               v.x = __ldcs(Ar + c);
               if (c + 1 < n) v.y = __ldcs(Ar + c + 1);
             }
-            split2s(v.x, h[2 * t], mm[2 * t], sc.a);
-            split2s(v.y, h[2 * t + 1], mm[2 * t + 1], sc.a);
+            split2s(v.x, H[t].x, Mm[t].x, sc.a);
+            split2s(v.y, H[t].y, Mm[t].y, sc.a);
             if (WRITE_IMAGE && in)
-              *reinterpret_cast<float4*>(p.asplit + row * p.ldi + c) =
-                  make_float4(h[2 * t], mm[2 * t], h[2 * t + 1], mm[2 * t + 1]);
+              *reinterpret_cast<float4*>(p.asplit + row * p.ldi + c) = make_float4(H[t].x, H[t].y, Mm[t].x, Mm[t].y);
           }
         }
-        // row dot: two independent pair accumulators (short chains)
-        constexpr int kAcc = (2 * PPL) >= 2 ? 2 : 1;
-        df av[kAcc];
-#pragma unroll
-        for (int k = 0; k < kAcc; ++k) av[k] = df{0.f, 0.f};
+        // row dot: two independent pair accumulators (even and odd columns),
+        // advanced together by the packed FP32x2 instructions
+        float2 avh = make_float2(0.f, 0.f), avl = make_float2(0.f, 0.f);
 #pragma unroll
         for (int t = 0; t < PPL; ++t) {
           const int c = 2 * cl + 2 * L * t;
           float4 ww = make_float4(0.f, 0.f, 0.f, 0.f);
           if (c < n) ww = *reinterpret_cast<const float4*>(s_w + c);
-          df_fma_acc(av[(2 * t) % kAcc], h[2 * t], mm[2 * t], ww.x, ww.y);
-          df_fma_acc(av[(2 * t + 1) % kAcc], h[2 * t + 1], mm[2 * t + 1], ww.z, ww.w);
+          df2_fma_acc(avh, avl, H[t], Mm[t], make_float2(ww.x, ww.y), make_float2(ww.z, ww.w));
         }
-        df dot = av[0];
-#pragma unroll
-        for (int k = 1; k < kAcc; ++k) dot = df_add(dot, av[k]);
+        df dot = df_add(df{avh.x, avl.x}, df{avh.y, avl.y});
 #pragma unroll
         for (int o = L / 2; o > 0; o >>= 1) dot = df_add_unnorm(dot, shfl_xor_df(dot, o));
         dot = df_renorm(dot);
@@ -579,14 +587,18 @@ struct DfPass {
           ss = df_add(ss, df_mul(y, y));
           if (UIN2) bb = df_add(bb, df_mul(ui, ui));
         }
+        const float2 y1 = make_float2(y.hi, y.hi), y2 = make_float2(y.lo, y.lo);
 #pragma unroll
-        for (int q = 0; q < 2 * PPL; ++q) {
-          df_fma_acc(Gc[q], h[q], mm[q], y.hi, y.lo);
-          if (steps & 1u) Gc[q] = df_renorm(Gc[q]);
-          if (FRO) df_fma_acc(fro, h[q], mm[q], h[q], mm[q]);
+        for (int t = 0; t < PPL; ++t) {
+          df2_fma_acc(Gh[t], Gl[t], H[t], Mm[t], y1, y2);
+          if (steps & 1u) df2_renorm(Gh[t], Gl[t]);
+          if (FRO) {
+            df_fma_acc(fro, H[t].x, Mm[t].x, H[t].x, Mm[t].x);
+            df_fma_acc(fro, H[t].y, Mm[t].y, H[t].y, Mm[t].y);
+          }
         }
         if (FRO) fro = df_renorm(fro);
-        if ((steps & 31u) == 31u) flush(Gc, gw, cl, seg, n, first_flush, sc.g);
+        if ((steps & 31u) == 31u) flush(Gh, Gl, gw, cl, seg, n, first_flush, sc.g);
       }
       __syncwarp();
       if (lane == 0 && use_ring && jc + kNbuf < count) {
@@ -603,7 +615,7 @@ struct DfPass {
       for (uint32_t k = jc; k < count && k < jc + kNbuf; ++k) wait(k, mybars, lim);
     }
     if (use_ring) seq += count;  // ring phases advance only when rows went through it
-    flush(Gc, gw, cl, seg, n, first_flush, sc.g);
+    flush(Gh, Gl, gw, cl, seg, n, first_flush, sc.g);
     // ss and bb: one copy per segment (lanes of a segment agree); fro per lane
 #pragma unroll
     for (int o = L; o < 32; o <<= 1) {
@@ -678,15 +690,17 @@ struct DfPass {
     const PassScale sc = pass_scale(p, e_out);
     const unsigned long long lim = wait_limit_ns(p.bar);
 
-    for (int c = threadIdx.x; c < p.ldi; c += kThreads) {
-      const double v = c < n ? wsign * wvec[c] * sc.w : 0.0;
-      const float v1 = __double2float_rn(v);
-      s_w[c] = make_float2(v1, __double2float_rn(v - (double)v1));
+    for (int c = 2 * threadIdx.x; c < p.ldi; c += 2 * kThreads) {
+      const double v0 = c < n ? wsign * wvec[c] * sc.w : 0.0;
+      const double v1 = c + 1 < n ? wsign * wvec[c + 1] * sc.w : 0.0;
+      const float a0 = __double2float_rn(v0), a1 = __double2float_rn(v1);
+      *reinterpret_cast<float4*>(s_w + c) =
+          make_float4(a0, a1, __double2float_rn(v0 - (double)a0), __double2float_rn(v1 - (double)a1));
     }
     __syncthreads();
-    df Gc[2 * PPL];
+    float2 Gh[PPL], Gl[PPL];
 #pragma unroll
-    for (int q = 0; q < 2 * PPL; ++q) Gc[q] = df{0.f, 0.f};
+    for (int t = 0; t < PPL; ++t) Gh[t] = Gl[t] = make_float2(0.f, 0.f);
     const float g1 = __double2float_rn(gamma);
     const df gdf{g1, __double2float_rn(gamma - (double)g1)};
     df ss{0.f, 0.f}, bb{0.f, 0.f}, fro{0.f, 0.f};
@@ -716,7 +730,7 @@ struct DfPass {
         bi = p.b[row];
       else
         uu = ubuf[row];
-      float h[2 * PPL], mm[2 * PPL];
+      float2 H[PPL], Mm[PPL];  // pair-major, as in run()
 #pragma unroll
       for (int t = 0; t < PPL; ++t) {
         const int c = c0 + 2 * lane + 64 * t;
@@ -724,10 +738,8 @@ struct DfPass {
         if (FROM_IMAGE) {
           float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
           if (in) v = *reinterpret_cast<const float4*>(buf + (c - c0));
-          h[2 * t] = v.x;
-          mm[2 * t] = v.y;
-          h[2 * t + 1] = v.z;
-          mm[2 * t + 1] = v.w;
+          H[t] = make_float2(v.x, v.y);
+          Mm[t] = make_float2(v.z, v.w);
         } else {
           double2 v = make_double2(0.0, 0.0);
           if (p.a_ring) {
@@ -737,23 +749,21 @@ struct DfPass {
             v.x = __ldcs(Ar + c);
             if (c + 1 < n) v.y = __ldcs(Ar + c + 1);
           }
-          split2s(v.x, h[2 * t], mm[2 * t], sc.a);
-          split2s(v.y, h[2 * t + 1], mm[2 * t + 1], sc.a);
+          split2s(v.x, H[t].x, Mm[t].x, sc.a);
+          split2s(v.y, H[t].y, Mm[t].y, sc.a);
           if (WRITE_IMAGE && in)
-            *reinterpret_cast<float4*>(p.asplit + row * p.ldi + c) =
-                make_float4(h[2 * t], mm[2 * t], h[2 * t + 1], mm[2 * t + 1]);
+            *reinterpret_cast<float4*>(p.asplit + row * p.ldi + c) = make_float4(H[t].x, H[t].y, Mm[t].x, Mm[t].y);
         }
       }
-      df av[2] = {df{0.f, 0.f}, df{0.f, 0.f}};
+      float2 avh = make_float2(0.f, 0.f), avl = make_float2(0.f, 0.f);
 #pragma unroll
       for (int t = 0; t < PPL; ++t) {
         const int c = c0 + 2 * lane + 64 * t;
         float4 ww = make_float4(0.f, 0.f, 0.f, 0.f);
         if (c < cend) ww = *reinterpret_cast<const float4*>(s_w + c);
-        df_fma_acc(av[0], h[2 * t], mm[2 * t], ww.x, ww.y);
-        df_fma_acc(av[1], h[2 * t + 1], mm[2 * t + 1], ww.z, ww.w);
+        df2_fma_acc(avh, avl, H[t], Mm[t], make_float2(ww.x, ww.y), make_float2(ww.z, ww.w));
       }
-      df dot = df_add(av[0], av[1]);
+      df dot = df_add(df{avh.x, avl.x}, df{avh.y, avl.y});
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) dot = df_add_unnorm(dot, shfl_xor_df(dot, o));
       dot = df_renorm(dot);
@@ -770,14 +780,18 @@ struct DfPass {
         ss = df_add(ss, df_mul(y, y));
         if (UIN2) bb = df_add(bb, df_mul(ui, ui));
       }
+      const float2 y1 = make_float2(y.hi, y.hi), y2 = make_float2(y.lo, y.lo);
 #pragma unroll
-      for (int q = 0; q < 2 * PPL; ++q) {
-        df_fma_acc(Gc[q], h[q], mm[q], y.hi, y.lo);
-        if (jc & 1u) Gc[q] = df_renorm(Gc[q]);
-        if (FRO) df_fma_acc(fro, h[q], mm[q], h[q], mm[q]);
+      for (int t = 0; t < PPL; ++t) {
+        df2_fma_acc(Gh[t], Gl[t], H[t], Mm[t], y1, y2);
+        if (jc & 1u) df2_renorm(Gh[t], Gl[t]);
+        if (FRO) {
+          df_fma_acc(fro, H[t].x, Mm[t].x, H[t].x, Mm[t].x);
+          df_fma_acc(fro, H[t].y, Mm[t].y, H[t].y, Mm[t].y);
+        }
       }
       if (FRO) fro = df_renorm(fro);
-      if ((jc & 31u) == 31u) flush_panel(Gc, gw, c0, cend, first_flush, sc.g);
+      if ((jc & 31u) == 31u) flush_panel(Gh, Gl, gw, c0, cend, first_flush, sc.g);
       __syncwarp();
       if (lane == 0 && use_ring && ok && jc + kNbuf < count) {
         fence_proxy_async_smem();
@@ -789,7 +803,7 @@ struct DfPass {
       for (uint32_t k = failed_at; k < count && k < failed_at + kNbuf; ++k) wait(k, mybars, lim);
     }
     if (use_ring) seq += count;
-    flush_panel(Gc, gw, c0, cend, first_flush, sc.g);
+    flush_panel(Gh, Gl, gw, c0, cend, first_flush, sc.g);
     double frow = 0.0;
     if (FRO) frow = warp_allreduce_sum(df_to_double(fro)) * sc.a2;
     if (lane == 0) {
@@ -806,18 +820,19 @@ struct DfPass {
     __syncthreads();
   }
 
-  __device__ void flush_panel(df (&Gc)[2 * PPL], double* gw, int c0, int cend, bool& first, double gmul) {
+  __device__ void flush_panel(float2 (&Gh)[PPL], float2 (&Gl)[PPL], double* gw, int c0, int cend, bool& first,
+                              double gmul) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int t = 0; t < PPL; ++t) {
       const int c = c0 + 2 * lane + 64 * t;
       if (c < cend) {
         double2 g = first ? make_double2(0.0, 0.0) : *reinterpret_cast<const double2*>(gw + c);
-        g.x += df_to_double(Gc[2 * t]) * gmul;
-        g.y += df_to_double(Gc[2 * t + 1]) * gmul;
+        g.x += df_to_double(df{Gh[t].x, Gl[t].x}) * gmul;
+        g.y += df_to_double(df{Gh[t].y, Gl[t].y}) * gmul;
         *reinterpret_cast<double2*>(gw + c) = g;
       }
-      Gc[2 * t] = Gc[2 * t + 1] = df{0.f, 0.f};
+      Gh[t] = Gl[t] = make_float2(0.f, 0.f);
     }
     first = false;
   }
@@ -896,17 +911,29 @@ struct DfPass {
   // on the original A -- one warp per row for n <= 512, the panel layout of
   // the wide-row pass above.
   __device__ void check(LsqrParams& p) {
+    // sum A_ij^2 is skipped when the sketch already formed it (p.fro_in):
+    // the pass is bound by the FP64 pipe, two FMA per entry instead of three
     if (PW > 1) {
       p.gparts = p.gcount * (kWarps / PW);
-      pass_native_panel<PW, true>(p, s_scal);
+      if (p.fro_in)
+        pass_native_panel<PW, false>(p, s_scal);
+      else
+        pass_native_panel<PW, true>(p, s_scal);
       return;
     }
     p.gparts = p.gcount;
     constexpr int TN = (2 * L * PPL + 63) / 64;
-    if (p.vec)
-      pass_native<TN, true, true, true>(p, p.x, -1.0, p.b, -1.0, nullptr, ring, s_scal);
-    else
-      pass_native<TN, false, true, true>(p, p.x, -1.0, p.b, -1.0, nullptr, ring, s_scal);
+    if (p.vec) {
+      if (p.fro_in)
+        pass_native<TN, true, false, true>(p, p.x, -1.0, p.b, -1.0, nullptr, ring, s_scal);
+      else
+        pass_native<TN, true, true, true>(p, p.x, -1.0, p.b, -1.0, nullptr, ring, s_scal);
+    } else {
+      if (p.fro_in)
+        pass_native<TN, false, false, true>(p, p.x, -1.0, p.b, -1.0, nullptr, ring, s_scal);
+      else
+        pass_native<TN, false, true, true>(p, p.x, -1.0, p.b, -1.0, nullptr, ring, s_scal);
+    }
   }
 };
 
@@ -1021,7 +1048,7 @@ __device__ void finish_body(LsqrParams& p, Pass& pass, double* s_scal, int64_t i
     xx = block_sum(xx, scratch);
     const double rnorm = sqrt(sum_part(p, 0));
     const double bn = sqrt(sum_part(p, 1));
-    const double fro = sqrt(sum_part(p, 2));
+    const double fro = p.fro_in ? sqrt(__ldcg(p.fro_in)) : sqrt(sum_part(p, 2));
     const double marn = p.M ? sqrt(sum_part(p, 3)) : 0.0;
     if (threadIdx.x == 0) {
       const double arn = sqrt(gx), xn = sqrt(xx);

@@ -145,6 +145,7 @@ extern "C" lsq_status lsq_check_noalloc(const double* A, int64_t m, int64_t n, i
   p.ring_k = 1;
   p.range = nullptr;
   p.gate = 0.0;
+  p.fro_in = nullptr;
   p.bar = bar;
   p.status = status;
   p.out = out;

@@ -11,16 +11,17 @@
 // of the trailing columns j > k, two or three at a time.  Column k itself is never
 // written, so one grid barrier per column suffices.
 //
-// Blocked (compact WY, as LAPACK's geqrf/larft/larfb): panels of nb columns.
+// Blocked (compact WY, as LAPACK's geqrf/larft/larfb): panels of 64 columns.
 // A panel kernel factors the panel with the reflectors of the unblocked
 // kernel, touching only the panel's columns (two barriers per column over its
 // G blocks, ~256 panel rows each); T of
-// Q = H_0 ... H_{b-1} = I - U T U^T comes from the Gram U^T U; the trailing
-// columns (and the sketched b column) then take Q^T in three GEMMs,
-// C <- C - U (T^T (U^T C)), on the tensor cores through cuBLAS (DGEMM in the
-// plain form, FP32 emulated with three BF16 terms in the mixed form).
-#include <cublas_v2.h>
-
+// Q = H_0 ... H_{b-1} = I - U T U^T comes from the Gram U^T U (larft); the
+// trailing columns (and the sketched b column) then take Q^T as
+// C <- C - V Z with Z = U^T C and V = U T^T.  The Gram and both large
+// products run on the tensor cores (tc_gemm.cu: tcgen05 with TMEM
+// accumulators, exact bf16 slicing, FP32 accumulation in TMEM, FP64
+// combination): 7 slices per row keep FP64 accuracy in the plain form, 4 keep
+// FP32 accuracy in the mixed form.
 #include <algorithm>
 
 #include "kernels.h"
@@ -287,22 +288,128 @@ __global__ void __launch_bounds__(256) k_panel(TW* __restrict__ W, int64_t ld, i
   }
 }
 
+// The same factorisation with the block's rows of the panel held in shared
+// memory (column-major, nr rows per column) for the whole panel: the data
+// never leaves the SM between the two barriers of a column, only the
+// partial sums (norms, dots) and the published row j go through L2.  Block g
+// of G owns panel rows [L g / G, L (g+1) / G) (at most kPanelSmemRows); the
+// arithmetic is k_panel's, in the same order.  Writes U (column-major, ld)
+// and, at the end, the block's rows of the panel back to W.
+constexpr int kPanelSmemRows = 224;  // 224 rows x 64 columns x 8 bytes = 112 KB (FP64)
+
+template <typename TW>
+__global__ void __launch_bounds__(256) k_panel_smem(TW* __restrict__ W, int64_t ld, int64_t k0, int64_t L, int b,
+                                                    TW* __restrict__ U, double* __restrict__ rdiag,
+                                                    TW* __restrict__ tau, TW* __restrict__ part,
+                                                    TW* __restrict__ rowv, GridBarrier* bar, uint32_t* status) {
+  extern __shared__ __align__(16) unsigned char s_panel_raw[];
+  TW* Ps = reinterpret_cast<TW*>(s_panel_raw);  // [b][nrp]
+  __shared__ TW scratch[32];
+  __shared__ TW s_sc[kPanelMax + 4];  // per-column f * inv_v0, then (tau, inv_v0, beta) of the step
+  const int G = gridDim.x, g = blockIdx.x;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int64_t r0 = L * g / G, r1 = L * (g + 1) / G;
+  const int nr = (int)(r1 - r0), nrp = nr | 1;  // odd stride: no bank conflicts along a row
+  TW* P = W + k0 * ld + k0;
+  const int PS = kPanelMax + 2;
+  auto sync = [&]() -> bool {
+    if (G == 1) {
+      __syncthreads();
+      return true;
+    }
+    return grid_sync(bar, status, (unsigned int)G);
+  };
+  for (int c = 0; c < b; ++c)
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) Ps[c * nrp + i] = __ldcg(P + (int64_t)c * ld + r0 + i);
+  __syncthreads();
+  for (int j = 0; j < b; ++j) {
+    const int par = j & 1;
+    const TW* pj = Ps + j * nrp;
+    TW* prt = part + (int64_t)par * G * PS;
+    TW* rv = rowv + par * kPanelMax;
+    // own rows strictly below panel row j
+    const int i0 = (int)(r0 > j + 1 ? 0 : (int64_t)j + 1 - r0);
+    TW sq = 0;
+    for (int i = i0 + threadIdx.x; i < nr; i += blockDim.x) sq = fma(pj[i], pj[i], sq);
+    sq = block_sum_t<TW>(sq, scratch);
+    if (threadIdx.x == 0) prt[(int64_t)g * PS] = sq;
+    if (j >= r0 && j < r1)
+      for (int jj = j + threadIdx.x; jj < b; jj += blockDim.x) rv[jj] = Ps[jj * nrp + (j - r0)];
+    if (!sync()) return;
+    if (threadIdx.x == 0) {
+      TW sigma = 0;
+      for (int q = 0; q < G; ++q) sigma += __ldcg(prt + (int64_t)q * PS);
+      const TW alpha = __ldcg(rv + j);
+      TW beta = alpha, t = 0, inv_v0 = 0;
+      if (sigma != (TW)0) {
+        const TW nrm = sqrt(fma(alpha, alpha, sigma));
+        beta = alpha >= (TW)0 ? -nrm : nrm;
+        t = (beta - alpha) / beta;
+        inv_v0 = (TW)1 / (alpha - beta);
+      }
+      if (g == 0) {
+        rdiag[k0 + j] = (double)beta;
+        tau[j] = t;
+      }
+      s_sc[kPanelMax] = t;
+      s_sc[kPanelMax + 1] = inv_v0;
+    }
+    __syncthreads();
+    const TW t = s_sc[kPanelMax], inv_v0 = s_sc[kPanelMax + 1];
+    TW* uj = U + (int64_t)j * ld + r0;
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+      const int64_t gi = r0 + i;
+      uj[i] = gi < j ? (TW)0 : (gi == j ? (TW)1 : pj[i] * inv_v0);
+    }
+    if (t == (TW)0) {
+      __syncthreads();
+      continue;  // same in every block: same barrier count
+    }
+    for (int jj = j + 1 + wib; jj < b; jj += nwarps) {
+      const TW* pjj = Ps + jj * nrp;
+      TW acc = 0;
+      for (int i = i0 + lane; i < nr; i += 32) acc = fma(pj[i], pjj[i], acc);
+      acc = warp_sum_t<TW>(acc);
+      if (lane == 0) prt[(int64_t)g * PS + 1 + jj] = acc;
+    }
+    if (!sync()) return;
+    // column scalars, one thread per later column (sums in block order)
+    for (int jj = j + 1 + threadIdx.x; jj < b; jj += blockDim.x) {
+      TW S = 0;
+      for (int q = 0; q < G; ++q) S += __ldcg(prt + (int64_t)q * PS + 1 + jj);
+      const TW wj = __ldcg(rv + jj);
+      const TW f = t * fma(inv_v0, S, wj);
+      s_sc[jj] = f * inv_v0;
+      if (j >= r0 && j < r1) Ps[jj * nrp + (j - r0)] = wj - f;
+    }
+    __syncthreads();
+    for (int jj = j + 1 + wib; jj < b; jj += nwarps) {
+      const TW fv = s_sc[jj];
+      TW* pjj = Ps + jj * nrp;
+      for (int i = i0 + lane; i < nr; i += 32) pjj[i] = fma(-fv, pj[i], pjj[i]);
+    }
+    __syncthreads();
+  }
+  for (int c = 0; c < b; ++c)
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) P[(int64_t)c * ld + r0 + i] = Ps[c * nrp + i];
+}
+
 // T (b x b, column-major, upper) of Q = I - U T U^T from the Gram U^T U and
 // tau (LAPACK larft, forward, columnwise): T[j][j] = tau_j,
-// T[0:j, j] = -tau_j T[0:j, 0:j] (U[:, 0:j]^T u_j).  One block.
+// T[0:j, j] = -tau_j T[0:j, 0:j] (U[:, 0:j]^T u_j).  One block, FP64.
 template <typename TW>
-__global__ void __launch_bounds__(256) k_tform(const TW* __restrict__ gram, const TW* __restrict__ tau, int b,
-                                               TW* __restrict__ T) {
-  __shared__ TW sT[kPanelMax * kPanelMax];
-  __shared__ TW w[kPanelMax];
+__global__ void __launch_bounds__(256) k_tform(const double* __restrict__ gram, const TW* __restrict__ tau, int b,
+                                               double* __restrict__ T) {
+  __shared__ double sT[kPanelMax * kPanelMax];
+  __shared__ double w[kPanelMax];
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) sT[e] = 0;
   __syncthreads();
   for (int j = 0; j < b; ++j) {
-    const TW tj = tau[j];
+    const double tj = (double)tau[j];
     if (threadIdx.x < j) w[threadIdx.x] = gram[threadIdx.x + (int64_t)j * b];
     __syncthreads();
     if (threadIdx.x < j) {
-      TW s = 0;
+      double s = 0;
       for (int l = threadIdx.x; l < j; ++l) s = fma(sT[threadIdx.x + l * b], w[l], s);
       sT[threadIdx.x + j * b] = -tj * s;
     }
@@ -312,40 +419,58 @@ __global__ void __launch_bounds__(256) k_tform(const TW* __restrict__ gram, cons
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) T[e] = sT[e];
 }
 
-cublasStatus_t gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, double alpha,
-                    const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc) {
-  return cublasDgemm(h, ta, tb, m, n, k, &alpha, A, lda, B, ldb, &beta, C, ldc);
-}
-cublasStatus_t gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, float alpha,
-                    const float* A, int lda, const float* B, int ldb, float beta, float* C, int ldc) {
-  return cublasGemmEx(h, ta, tb, m, n, k, &alpha, A, CUDA_R_32F, lda, B, CUDA_R_32F, ldb, &beta, C, CUDA_R_32F, ldc,
-                      CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUBLAS_GEMM_DEFAULT);
-}
+constexpr int kPanelBlocksMax = 64;    // blocks of the global-memory panel kernel
+constexpr int kPanelBlocksCap = 320;   // partial-sum slots (the shared-memory kernel may use more blocks)
+constexpr int kSlicesMax = 7;  // bf16 slices per row for FP64 data (3 for FP32)
 
+// bf16 slices per row: 7 (56 bits) for FP64 data; 4 (32 bits) for FP32 data,
+// so that entries down to 2^-8 of their row's largest keep FP32's 24 bits
 template <typename TW>
-constexpr int panel_width() {
-  return sizeof(TW) == 4 ? 64 : 32;
+constexpr int oz_slices() {
+  return sizeof(TW) == 4 ? 4 : 7;
 }
 
+// Scratch of the blocked QR for a d x (n+1) sketch (sized for 7 slices).
 struct BlockedScratch {
-  size_t oU, oGram, oT, oZ, oZ2, oTau, oPart, oRow, bytes;
+  size_t oU, oGram, oT, oZt, oTau, oPart, oRow, oUs, oCs, oVs, oZs, oEu, oEc, oEv, oEz, bytes;
 };
-constexpr int kPanelBlocksMax = 64;
+int rows_a(int r) { return r > 128 ? r : 128; }  // slice rows of an A operand (tiles of 128)
+int rows_b(int r) { return r > 64 ? r : 64; }    // of a B operand (tiles of 64)
 BlockedScratch blocked_layout(int64_t d, int64_t n) {
   auto al = [](size_t v) { return (v + 255) / 256 * 256; };
   BlockedScratch s;
   size_t o = 0;
   const size_t ncol = (size_t)n + 1;
+  const size_t kpd = (size_t)oz_kpad((int)d), kpb = (size_t)oz_kpad(kPanelMax);
+  const size_t dr = (size_t)rows_a((int)d), cr = (size_t)rows_a((int)ncol);
   s.oU = o; o += al((size_t)d * kPanelMax * 8);
   s.oGram = o; o += al((size_t)kPanelMax * kPanelMax * 8);
   s.oT = o; o += al((size_t)kPanelMax * kPanelMax * 8);
-  s.oZ = o; o += al((size_t)kPanelMax * ncol * 8);
-  s.oZ2 = o; o += al((size_t)kPanelMax * ncol * 8);
+  s.oZt = o; o += al((size_t)kPanelMax * ncol * 8);
   s.oTau = o; o += al((size_t)kPanelMax * 8);
-  s.oPart = o; o += al((size_t)2 * kPanelBlocksMax * (kPanelMax + 2) * 8);
+  s.oPart = o; o += al((size_t)2 * kPanelBlocksCap * (kPanelMax + 2) * 8);
   s.oRow = o; o += al((size_t)2 * kPanelMax * 8);
+  s.oUs = o; o += al((size_t)kSlicesMax * 128 * kpd * 2);
+  s.oCs = o; o += al((size_t)kSlicesMax * cr * kpd * 2);
+  s.oVs = o; o += al((size_t)kSlicesMax * dr * kpb * 2);
+  s.oZs = o; o += al((size_t)kSlicesMax * cr * kpb * 2);
+  s.oEu = o; o += al((size_t)128 * 4);
+  s.oEc = o; o += al(cr * 4);
+  s.oEv = o; o += al(dr * 4);
+  s.oEz = o; o += al(cr * 4);
   s.bytes = o;
   return s;
+}
+
+// K per CTA of a mode-0 GEMM: about two CTAs per SM over the output tiles,
+// a multiple of the 128-deep exact accumulation chunk.
+int k_split_for(int M, int N, int K, int sms) {
+  const int tiles = ((M + 127) / 128) * ((N + 63) / 64);
+  int splits = (2 * sms + tiles - 1) / tiles;
+  if (splits < 1) splits = 1;
+  int ks = (K + splits - 1) / splits;
+  ks = (ks + 127) / 128 * 128;
+  return ks < 128 ? 128 : ks;
 }
 
 // The blocked factorisation of the d x ncol column-major W (first kmax = n
@@ -356,21 +481,34 @@ cudaError_t householder_blocked(TW* W, int64_t d, int n, int ncol, double* rdiag
   const BlockedScratch L0 = blocked_layout(d, n);
   char* s = static_cast<char*>(buf.blk);
   TW* U = reinterpret_cast<TW*>(s + L0.oU);
-  TW* gram = reinterpret_cast<TW*>(s + L0.oGram);
-  TW* T = reinterpret_cast<TW*>(s + L0.oT);
-  TW* Z = reinterpret_cast<TW*>(s + L0.oZ);
-  TW* Z2 = reinterpret_cast<TW*>(s + L0.oZ2);
+  double* gram = reinterpret_cast<double*>(s + L0.oGram);
+  double* T = reinterpret_cast<double*>(s + L0.oT);
+  double* Zt = reinterpret_cast<double*>(s + L0.oZt);
   TW* tau = reinterpret_cast<TW*>(s + L0.oTau);
   TW* part = reinterpret_cast<TW*>(s + L0.oPart);
   TW* rowv = reinterpret_cast<TW*>(s + L0.oRow);
-  cublasHandle_t h = static_cast<cublasHandle_t>(buf.blas);
-  if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
-  constexpr int nb = panel_width<TW>();
+  void* Us = s + L0.oUs;
+  void* Cs = s + L0.oCs;
+  void* Vs = s + L0.oVs;
+  void* Zs = s + L0.oZs;
+  int* eU = reinterpret_cast<int*>(s + L0.oEu);
+  int* eC = reinterpret_cast<int*>(s + L0.oEc);
+  int* eV = reinterpret_cast<int*>(s + L0.oEv);
+  int* eZ = reinterpret_cast<int*>(s + L0.oEz);
+  constexpr int nb = kPanelMax;
+  constexpr int S = oz_slices<TW>();
   const int kmax = n < d ? n : (int)d;
-  const int ld = (int)d;
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_panel<TW>, 256, 0);
   if (e != cudaSuccess) return e;
+  // the shared-memory panel kernel: one block per SM at most, rows <= kPanelSmemRows each
+  const int smem_panel = (kPanelSmemRows | 1) * kPanelMax * (int)sizeof(TW);
+  int per_sm_s = 0;
+  if ((e = cudaFuncSetAttribute(k_panel_smem<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_panel)) !=
+          cudaSuccess ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, k_panel_smem<TW>, 256, smem_panel)) !=
+          cudaSuccess)
+    return e;
   for (int k0 = 0; k0 < kmax; k0 += nb) {
     const int b = kmax - k0 < nb ? kmax - k0 : nb;
     const int64_t L = d - k0;
@@ -379,6 +517,10 @@ cudaError_t householder_blocked(TW* W, int64_t d, int n, int ncol, double* rdiag
     int G = (int)std::min<int64_t>((L + 255) / 256, kPanelBlocksMax);
     G = std::min(G, std::max(1, per_sm * sms));
     if (G < 1) G = 1;
+    // rows held in shared memory when every block's share fits
+    int Gs = (int)std::max<int64_t>((L + 191) / 192, 1);
+    const bool smem_ok = per_sm_s >= 1 && Gs <= per_sm_s * sms && Gs <= kPanelBlocksCap &&
+                         (L + Gs - 1) / Gs <= kPanelSmemRows;
     TW* Wp = W;
     int64_t ld64 = d, k064 = k0, L64 = L;
     int bb = b;
@@ -387,24 +529,82 @@ cudaError_t householder_blocked(TW* W, int64_t d, int n, int ncol, double* rdiag
     uint32_t* status = buf.status;
     void* args[] = {&Wp, &ld64, &k064, &L64, &bb, &U, &rd, &tau, &part, &rowv, &bar, &status};
     // the ticket barrier's counter restarts for each launch (G changes with L)
-    if (G > 1 && (e = cudaMemsetAsync(&buf.bar->count, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
-    if (G == 1)
+    const int GL = smem_ok ? Gs : G;
+    if (GL > 1 && (e = cudaMemsetAsync(&buf.bar->count, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
+    if (smem_ok)
+      e = GL == 1 ? cudaLaunchKernel((const void*)k_panel_smem<TW>, 1, 256, args, smem_panel, st)
+                  : cudaLaunchCooperativeKernel((const void*)k_panel_smem<TW>, GL, 256, args, smem_panel, st);
+    else if (G == 1)
       e = cudaLaunchKernel((const void*)k_panel<TW>, 1, 256, args, 0, st);
     else
       e = cudaLaunchCooperativeKernel((const void*)k_panel<TW>, G, 256, args, 0, st);
     if (e != cudaSuccess) return e;
     const int c = ncol - k0 - b;
     if (c <= 0) continue;
-    TW* C = W + (int64_t)(k0 + b) * d + k0;
     const int Li = (int)L;
-    if (gemm(h, CUBLAS_OP_T, CUBLAS_OP_N, b, b, Li, (TW)1, U, ld, U, ld, (TW)0, gram, b) != CUBLAS_STATUS_SUCCESS)
-      return cudaErrorUnknown;
+    const int kpl = oz_kpad(Li), kpb = oz_kpad(b);
+    // slices of U's b columns (rows of U^T, length L): B operand of Z^T = C^T U
+    // and both operands of the Gram U^T U
+    if ((e = oz_slice<TW>(U, b, Li, d, nullptr, S, Us, kpl, eU, 128, sms, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(gram, 0, sizeof(double) * b * b, st)) != cudaSuccess) return e;
+    OzGemm g;
+    g.S = S;
+    g.status = buf.status;
+    g.bar = buf.bar;
+    g.a = Us;
+    g.b = Us;
+    g.M = b;
+    g.N = b;
+    g.K = Li;
+    g.Kpad = kpl;
+    g.a_rows = 128;
+    g.b_rows = 128;
+    g.ea = eU;
+    g.eb = eU;
+    g.mode = 0;
+    g.out_f32 = 0;
+    g.out = gram;
+    g.ldo = b;
+    g.k_split = k_split_for(b, b, Li, sms);
+    if ((e = oz_gemm(g, st)) != cudaSuccess) return e;
     k_tform<TW><<<1, 256, 0, st>>>(gram, tau, b, T);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (gemm(h, CUBLAS_OP_T, CUBLAS_OP_N, b, c, Li, (TW)1, U, ld, C, ld, (TW)0, Z, b) != CUBLAS_STATUS_SUCCESS ||
-        gemm(h, CUBLAS_OP_T, CUBLAS_OP_N, b, c, b, (TW)1, T, b, Z, b, (TW)0, Z2, b) != CUBLAS_STATUS_SUCCESS ||
-        gemm(h, CUBLAS_OP_N, CUBLAS_OP_N, Li, c, b, (TW)-1, U, ld, Z2, b, (TW)1, C, ld) != CUBLAS_STATUS_SUCCESS)
-      return cudaErrorUnknown;
+    // Z^T = C^T U (c x b): A operand = C's columns (length L)
+    TW* C = W + (int64_t)(k0 + b) * d + k0;
+    const int cr = rows_a(c);
+    if ((e = oz_slice<TW>(C, c, Li, d, nullptr, S, Cs, kpl, eC, cr, sms, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(Zt, 0, sizeof(double) * (size_t)c * b, st)) != cudaSuccess) return e;
+    g.a = Cs;
+    g.b = Us;
+    g.M = c;
+    g.N = b;
+    g.a_rows = cr;
+    g.b_rows = 128;
+    g.ea = eC;
+    g.eb = eU;
+    g.out = Zt;
+    g.ldo = b;
+    g.k_split = k_split_for(c, b, Li, sms);
+    if ((e = oz_gemm(g, st)) != cudaSuccess) return e;
+    // C <- C - V Z, V = U T^T (L x b), Z = (Z^T)^T: A operand = rows of V, B = rows of Z^T
+    const int lr = rows_a(Li), zr = rows_b(c);
+    if ((e = oz_slice<TW>(U, Li, b, d, T, S, Vs, kpb, eV, lr, sms, st)) != cudaSuccess) return e;
+    if ((e = oz_slice<double>(Zt, c, b, b, nullptr, S, Zs, kpb, eZ, zr, sms, st)) != cudaSuccess) return e;
+    g.a = Vs;
+    g.b = Zs;
+    g.M = Li;
+    g.N = c;
+    g.K = b;
+    g.Kpad = kpb;
+    g.a_rows = lr;
+    g.b_rows = zr;
+    g.ea = eV;
+    g.eb = eZ;
+    g.mode = 1;
+    g.out_f32 = sizeof(TW) == 4;
+    g.out = C;
+    g.ldo = d;
+    if ((e = oz_gemm(g, st)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -525,7 +725,7 @@ cudaError_t precond(const TY* Y, int64_t d, int64_t n64, int64_t ldy, int has_b,
   if ((e = cudaMemsetAsync(&buf.bar->count, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
   const bool big = n >= kBlockedMinN && (size_t)d * ncol * sizeof(TY) >= kBlockedMinBytes;
   const bool blocked = buf.mode == 2 || (buf.mode == 0 && big);
-  if (buf.blk && buf.blas && blocked && (size_t)kPanelMax * ncol <= ((size_t)1 << 31)) {
+  if (buf.blk && blocked && (size_t)kPanelMax * ncol <= ((size_t)1 << 31)) {
     if ((e = householder_blocked<TY>(W, d, n, ncol, buf.rdiag, buf, sms, st)) != cudaSuccess) return e;
   } else {
     // one block per SM (at most one per trailing column); three columns per

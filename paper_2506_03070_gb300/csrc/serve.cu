@@ -229,6 +229,7 @@ __device__ void serve_solve(const ServeItem& it, int gidx, double* s_ring, uint6
   p.ring_k = 1;
   p.range = ctl->range;
   p.gate = it.gate;
+  p.fro_in = nullptr;
   p.M = M;
   p.Mt = Mt;
   p.x = it.x;

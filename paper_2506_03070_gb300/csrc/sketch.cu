@@ -41,6 +41,14 @@ __device__ __forceinline__ void track_exp(double a, uint32_t& emax) {
   const uint32_t e = (uint32_t)__double2hiint(a) & 0x7FF00000u;
   if (e != 0x7FF00000u) emax = max(emax, e);
 }
+// Warp sum of A_ij^2 into *fro.
+__device__ __forceinline__ void flush_fro(double fa, double* fro) {
+  if (!fro) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) fa += __shfl_xor_sync(0xffffffffu, fa, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(fro, fa);
+}
+
 // Warp maxima of the A and b exponent fields into range[0], range[1].
 __device__ __forceinline__ void flush_range(uint32_t ea, uint32_t eb, uint32_t* range) {
   if (!range) return;
@@ -68,7 +76,7 @@ __global__ void __launch_bounds__(256) k_sketch_apply(const double* __restrict__
                                                       const double* __restrict__ b, uint64_t d, int zeta,
                                                       uint64_t seed, int64_t row0, TY* __restrict__ Y, int64_t ldy,
                                                       double scale, uint32_t* status, int32_t* max_rounds,
-                                                      uint32_t* range) {
+                                                      uint32_t* range, double* fro) {
   extern __shared__ int32_t s_idx[];  // [8 warps][32 rows][N]
   __shared__ uint64_t s_sgn[8][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -76,6 +84,7 @@ __global__ void __launch_bounds__(256) k_sketch_apply(const double* __restrict__
   const int ncol = n + (b ? 1 : 0);
   bool bad = false;
   uint32_t ea = 0, eb = 0;
+  double fa = 0.0;
   for (int64_t base = ((int64_t)blockIdx.x * 8 + wib) * 32; base < m; base += (int64_t)gridDim.x * 8 * 32) {
     const int64_t row = base + lane;
     if (row < m) {
@@ -99,6 +108,7 @@ __global__ void __launch_bounds__(256) k_sketch_apply(const double* __restrict__
         const double a = j < n ? __ldcs(Ai + j) : b[i];
         bad |= !isfinite(a);
         track_exp(a, j < n ? ea : eb);
+        if (j < n) fa = fma(a, a, fa);
         const double sa = a * scale;
         for (int k = 0; k < zeta; ++k) {
           const double v = flip_sign(sa, ((sg >> k) & 1ull) == 0ull);
@@ -110,6 +120,7 @@ __global__ void __launch_bounds__(256) k_sketch_apply(const double* __restrict__
   }
   if (bad) atomicOr(status, DS_NONFINITE);
   flush_range(ea, eb, range);
+  flush_fro(fa, fro);
 }
 
 __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
@@ -162,7 +173,8 @@ __global__ void __launch_bounds__(256) k_sketch_apply_f32v(const double* __restr
                                                            const double* __restrict__ b, uint64_t d, int zeta,
                                                            uint64_t seed, int64_t row0, float* __restrict__ Y,
                                                            float* __restrict__ Ylo, int64_t ldy, float scale,
-                                                           uint32_t* status, int32_t* max_rounds, uint32_t* range) {
+                                                           uint32_t* status, int32_t* max_rounds, uint32_t* range,
+                                                           double* fro) {
   extern __shared__ int32_t s_idx[];  // [8 warps][32 rows][N]
   __shared__ uint64_t s_sgn[8][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -171,6 +183,7 @@ __global__ void __launch_bounds__(256) k_sketch_apply_f32v(const double* __restr
   const int ngroups = (ncol + 3) / 4;
   bool bad = false;
   uint32_t ea = 0, eb = 0;
+  double fa = 0.0;
   for (int64_t base = ((int64_t)blockIdx.x * 8 + wib) * 32; base < m; base += (int64_t)gridDim.x * 8 * 32) {
     const int64_t row = base + lane;
     if (row < m) {
@@ -198,6 +211,7 @@ __global__ void __launch_bounds__(256) k_sketch_apply_f32v(const double* __restr
           const double a = j < n ? __ldcs(Ai + j) : (j == n && b ? b[i] : 0.0);
           bad |= !isfinite(a);
           track_exp(a, j < n ? ea : eb);
+          if (j < n) fa = fma(a, a, fa);
           v[q] = __fmul_rn(to_float_int(a), scale);
         }
         if (COMP) {
@@ -236,6 +250,7 @@ __global__ void __launch_bounds__(256) k_sketch_apply_f32v(const double* __restr
   }
   if (bad) atomicOr(status, DS_NONFINITE);
   flush_range(ea, eb, range);
+  flush_fro(fa, fro);
 }
 
 // range_scan: one warp per row (grid-stride), lanes over the columns and b_i.
@@ -264,7 +279,7 @@ __global__ void __launch_bounds__(256) k_range_scan(const double* __restrict__ A
 template <int N>
 cudaError_t launch_apply_f32v(const double* A, int64_t m, int n, int64_t lda, const double* b, int64_t d, int zeta,
                               uint64_t seed, int64_t row0, float* Y, float* Ylo, int64_t ldy, uint32_t* status,
-                              int32_t* max_rounds, uint32_t* range, int sms, cudaStream_t st) {
+                              int32_t* max_rounds, uint32_t* range, double* fro, int sms, cudaStream_t st) {
   const size_t smem = (size_t)8 * 32 * N * sizeof(int32_t);
   const void* fn = Ylo ? (const void*)k_sketch_apply_f32v<N, true> : (const void*)k_sketch_apply_f32v<N, false>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -276,11 +291,11 @@ cudaError_t launch_apply_f32v(const double* A, int64_t m, int n, int64_t lda, co
     if (Ylo)
       k_sketch_apply_f32v<N, true><<<(unsigned)blocks, 256, smem, st>>>(A, m, n, lda, b, (uint64_t)d, zeta, seed,
                                                                         row0, Y, Ylo, ldy, scale, status, max_rounds,
-                                                                        range);
+                                                                        range, fro);
     else
       k_sketch_apply_f32v<N, false><<<(unsigned)blocks, 256, smem, st>>>(A, m, n, lda, b, (uint64_t)d, zeta, seed,
                                                                          row0, Y, nullptr, ldy, scale, status,
-                                                                         max_rounds, range);
+                                                                         max_rounds, range, fro);
   }
   return cudaGetLastError();
 }
@@ -303,7 +318,7 @@ cudaError_t launch_indices(uint64_t seed, int64_t row0, int64_t rows, int64_t d,
 template <int N, typename TY>
 cudaError_t launch_apply(const double* A, int64_t m, int n, int64_t lda, const double* b, int64_t d, int zeta,
                          uint64_t seed, int64_t row0, TY* Y, int64_t ldy, uint32_t* status, int32_t* max_rounds,
-                         uint32_t* range, int sms, cudaStream_t st) {
+                         uint32_t* range, double* fro, int sms, cudaStream_t st) {
   const size_t smem = (size_t)8 * 32 * N * sizeof(int32_t);
   cudaError_t e = cudaFuncSetAttribute(k_sketch_apply<N, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -311,7 +326,8 @@ cudaError_t launch_apply(const double* A, int64_t m, int n, int64_t lda, const d
   const int64_t blocks = std::min<int64_t>(groups, (int64_t)sms * 8);
   if (blocks > 0)
     k_sketch_apply<N, TY><<<(unsigned)blocks, 256, smem, st>>>(A, m, n, lda, b, (uint64_t)d, zeta, seed, row0, Y, ldy,
-                                                               1.0 / sqrt((double)zeta), status, max_rounds, range);
+                                                               1.0 / sqrt((double)zeta), status, max_rounds, range,
+                                                               fro);
   return cudaGetLastError();
 }
 
@@ -328,34 +344,39 @@ cudaError_t sketch_indices(uint64_t seed, int64_t row0, int64_t rows, int64_t d,
 template <typename TY>
 cudaError_t sketch_apply(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d, int zeta,
                          uint64_t seed, int64_t row0, TY* Y, int64_t ldy, uint32_t* status, int32_t* max_rounds,
-                         uint32_t* range, int sms, cudaStream_t st) {
+                         uint32_t* range, double* fro, int sms, cudaStream_t st) {
   const int ni = (int)n;
   if (sizeof(TY) == 4 && ldy % 4 == 0 && (uintptr_t)Y % 16 == 0)
     return sketch_apply_f32c(A, m, n, lda, b, d, zeta, seed, row0, reinterpret_cast<float*>(Y), nullptr, ldy, status,
-                             max_rounds, range, sms, st);
+                             max_rounds, range, fro, sms, st);
   if (zeta <= 8)
-    return launch_apply<8, TY>(A, m, ni, lda, b, d, zeta, seed, row0, Y, ldy, status, max_rounds, range, sms, st);
+    return launch_apply<8, TY>(A, m, ni, lda, b, d, zeta, seed, row0, Y, ldy, status, max_rounds, range, fro, sms,
+                               st);
   if (zeta <= 16)
-    return launch_apply<16, TY>(A, m, ni, lda, b, d, zeta, seed, row0, Y, ldy, status, max_rounds, range, sms, st);
+    return launch_apply<16, TY>(A, m, ni, lda, b, d, zeta, seed, row0, Y, ldy, status, max_rounds, range, fro, sms,
+                               st);
   if (zeta <= 32)
-    return launch_apply<32, TY>(A, m, ni, lda, b, d, zeta, seed, row0, Y, ldy, status, max_rounds, range, sms, st);
-  return launch_apply<64, TY>(A, m, ni, lda, b, d, zeta, seed, row0, Y, ldy, status, max_rounds, range, sms, st);
+    return launch_apply<32, TY>(A, m, ni, lda, b, d, zeta, seed, row0, Y, ldy, status, max_rounds, range, fro, sms,
+                               st);
+  return launch_apply<64, TY>(A, m, ni, lda, b, d, zeta, seed, row0, Y, ldy, status, max_rounds, range, fro, sms,
+                               st);
 }
 
 cudaError_t sketch_apply_f32c(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d,
                               int zeta, uint64_t seed, int64_t row0, float* Y, float* Ylo, int64_t ldy,
-                              uint32_t* status, int32_t* max_rounds, uint32_t* range, int sms, cudaStream_t st) {
+                              uint32_t* status, int32_t* max_rounds, uint32_t* range, double* fro, int sms,
+                              cudaStream_t st) {
   const int ni = (int)n;
   if (ldy % 4 != 0 || (uintptr_t)Y % 16 != 0 || (uintptr_t)Ylo % 16 != 0) return cudaErrorInvalidValue;
   if (zeta <= 8)
-    return launch_apply_f32v<8>(A, m, ni, lda, b, d, zeta, seed, row0, Y, Ylo, ldy, status, max_rounds, range, sms, st);
+    return launch_apply_f32v<8>(A, m, ni, lda, b, d, zeta, seed, row0, Y, Ylo, ldy, status, max_rounds, range, fro, sms, st);
   if (zeta <= 16)
-    return launch_apply_f32v<16>(A, m, ni, lda, b, d, zeta, seed, row0, Y, Ylo, ldy, status, max_rounds, range, sms,
+    return launch_apply_f32v<16>(A, m, ni, lda, b, d, zeta, seed, row0, Y, Ylo, ldy, status, max_rounds, range, fro, sms,
                                  st);
   if (zeta <= 32)
-    return launch_apply_f32v<32>(A, m, ni, lda, b, d, zeta, seed, row0, Y, Ylo, ldy, status, max_rounds, range, sms,
+    return launch_apply_f32v<32>(A, m, ni, lda, b, d, zeta, seed, row0, Y, Ylo, ldy, status, max_rounds, range, fro, sms,
                                  st);
-  return launch_apply_f32v<64>(A, m, ni, lda, b, d, zeta, seed, row0, Y, Ylo, ldy, status, max_rounds, range, sms, st);
+  return launch_apply_f32v<64>(A, m, ni, lda, b, d, zeta, seed, row0, Y, Ylo, ldy, status, max_rounds, range, fro, sms, st);
 }
 
 cudaError_t add_lo(float* Y, const float* Ylo, int64_t count, int sms, cudaStream_t st) {
@@ -372,10 +393,10 @@ cudaError_t range_scan(const double* A, int64_t m, int64_t n, int64_t lda, const
 }
 
 template cudaError_t sketch_apply<double>(const double*, int64_t, int64_t, int64_t, const double*, int64_t, int,
-                                          uint64_t, int64_t, double*, int64_t, uint32_t*, int32_t*, uint32_t*, int,
-                                          cudaStream_t);
+                                          uint64_t, int64_t, double*, int64_t, uint32_t*, int32_t*, uint32_t*, double*,
+                                          int, cudaStream_t);
 template cudaError_t sketch_apply<float>(const double*, int64_t, int64_t, int64_t, const double*, int64_t, int,
-                                         uint64_t, int64_t, float*, int64_t, uint32_t*, int32_t*, uint32_t*, int,
-                                         cudaStream_t);
+                                         uint64_t, int64_t, float*, int64_t, uint32_t*, int32_t*, uint32_t*, double*,
+                                         int, cudaStream_t);
 
 }  // namespace lsq
