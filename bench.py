@@ -673,7 +673,7 @@ def run_headline(args):
     achieved_iter = alg_iter / ((t_lsqr - t_check) / 1e3) / 1e9 if t_lsqr > t_check else None
     sketch_ms = statistics.mean(i["t_sketch_ms"] for i in infos)
     precond_ms = statistics.mean(i["t_precond_ms"] for i in infos)
-    blocked = n >= 1700
+    blocked = 8 * d * (n + 1) >= (32 << 20)
     per_solve = launches_per_solve(n, d, 0, blocked)
 
     def phase(ii):
@@ -853,12 +853,11 @@ def run_gpu(args, emit=True):
     m, n = A.shape
     d, zeta, tol, seed = p["d"], p["zeta"], p["tol"], p["seed_sketch"]
     prec = 0 if args.prec == "fp64" else 1
-    flags = P.FLAG_TIMING | (P.FLAG_NATIVE_FP64 if args.native else 0) | (P.FLAG_NO_CHECK if args.no_check else 0)
+    flags = P.FLAG_TIMING | (P.FLAG_NATIVE_FP64 if args.native else 0)
     stream = torch.cuda.current_stream()
 
     def solve():
-        return ctx.lsq_solve(A, b, d, zeta=zeta, seed=seed, tol=tol, prec=prec, flags=flags, stream=stream,
-                             maxit=args.maxit, allow_noconv=args.maxit > 0)
+        return ctx.lsq_solve(A, b, d, zeta=zeta, seed=seed, tol=tol, prec=prec, flags=flags, stream=stream)
 
     for _ in range(args.warmup):
         x, info = solve()
@@ -906,14 +905,12 @@ def run_gpu(args, emit=True):
         bh.copy_(b)
         Anp, bnp = Ah.numpy(), bh.numpy()
         xh = np.empty(n, dtype=np.float64)
-        ctx.lsq_solve(Anp, bnp, d, zeta=zeta, seed=seed, tol=tol, prec=prec, flags=flags, x=xh, maxit=args.maxit,
-                      allow_noconv=args.maxit > 0)
+        ctx.lsq_solve(Anp, bnp, d, zeta=zeta, seed=seed, tol=tol, prec=prec, flags=flags, x=xh)
         k2 = max(1, min(args.steps, 3))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(k2):
-            ctx.lsq_solve(Anp, bnp, d, zeta=zeta, seed=seed, tol=tol, prec=prec, flags=flags, x=xh,
-                          maxit=args.maxit, allow_noconv=args.maxit > 0)
+            ctx.lsq_solve(Anp, bnp, d, zeta=zeta, seed=seed, tol=tol, prec=prec, flags=flags, x=xh)
         t_e2e = time.perf_counter() - t0
         e2e = {"value": world * k2 / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": 8 * m * n + 8 * m,
                "d2h_bytes_per_step": 8 * n + 4096, "steps": k2}
@@ -1036,8 +1033,6 @@ def main():
     ap.add_argument("--cond", type=float, default=1e10, help="condition number of a custom problem")
     ap.add_argument("--coherent", type=float, default=0.01, help="fraction of rows scaled x1e4 (custom problem)")
     ap.add_argument("--n", type=int, default=0, help="custom problem columns (profiling runs)")
-    ap.add_argument("--maxit", type=int, default=0, help="cap LSQR iterations (profiling runs)")
-    ap.add_argument("--no-check", action="store_true", help="skip the accuracy pass (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-auto-d", action="store_true", help="skip the extra solve with the chosen embedding dimension")
     ap.add_argument("--sparse", action="store_true", help="the paper's 5e5_500_sparse workload (CSR path)")

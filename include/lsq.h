@@ -191,7 +191,7 @@ lsq_status lsq_precond(lsq_ctx* ctx, const void* Y, int64_t d, int64_t n, int64_
  * cooperative kernel; the Gram matrix and the trailing updates as the
  * library's own tcgen05 tensor-core GEMMs on exact bf16 slices -- 7 slices
  * per row keep FP64 accuracy, 4 keep FP32 accuracy for the mixed form) once
- * the d x (n+1) working copy reaches 32 MiB and n >= 1700, the unblocked one
+ * the d x (n+1) working copy reaches 32 MiB in its precision, the unblocked one
  * (one grid barrier per column) below.  Both compute the same reflectors. */
 /* ---- Embedding dimension (Sec. 4.3 "Selecting the embedding dimension") ----
  * The solve time is modelled as T(d) = T_qr(d) + (t(d) + 2) T_iter(m): the

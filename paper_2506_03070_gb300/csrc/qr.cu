@@ -5,7 +5,7 @@
 // Two factorisations of the column-major copy W of Y, same reflectors and
 // same storage (R's diagonal in a separate array, R[k][j] left in W[j][k]):
 //
-// Unblocked (all but wide sketches, see kBlockedMinN): one cooperative kernel, one
+// Unblocked (sketches whose working copy is below kBlockedMinBytes): one cooperative kernel, one
 // block per SM.  Step k: every block recomputes ||Y[k+1:,k]|| (same order, same
 // result in all blocks), builds the reflector scalars, and updates its share
 // of the trailing columns j > k, two or three at a time.  Column k itself is never
@@ -609,13 +609,13 @@ cudaError_t householder_blocked(TW* W, int64_t d, int n, int ncol, double* rdiag
   return cudaSuccess;
 }
 
-// Automatic choice: the blocked path for wide sketches whose working copy W
-// no longer sits comfortably in L2; below that the unblocked kernel's single
-// barrier per column is cheaper than the panel's two plus the GEMM launches.
-// Measured precond times, unblocked vs blocked (ms): FP64 d x n = 2000 x 500
-// 6.8 vs 16.9, 9600 x 500 21.6 vs 26.2, 6000 x 1500 73.6 vs 84.1, 8000 x 2000
-// 191 vs 142; FP32 4000 x 1000 17.3 vs 37.7, 8000 x 2000 102 vs 81.
-constexpr int kBlockedMinN = 1700;
+// Automatic choice: the blocked path once the working copy W reaches 32 MiB
+// (in its own precision), the unblocked kernel's single barrier per column
+// below.  Measured precond times, unblocked vs blocked (ms, FP64 / FP32):
+// 800 x 201 1.7 vs 4.1 / 1.1 vs 3.0; 2000 x 501 6.6 vs 11.0 / 4.2 vs 8.2;
+// 4000 x 1001 26.2 vs 26.5 / 17.4 vs 19.8; 9450 x 501 21.9 vs 17.3 / 12.0 vs 13.4;
+// 6000 x 1501 74 vs 52 / 49 vs 38; 8000 x 2001 191 vs 83 / 102 vs 62;
+// 16000 x 2001 477 vs 129 / 331 vs 95.
 constexpr size_t kBlockedMinBytes = (size_t)32 << 20;
 
 // R (row-major n x n, upper), z = W[n][0:n] (x0 slot), and the rank test
@@ -723,7 +723,7 @@ cudaError_t precond(const TY* Y, int64_t d, int64_t n64, int64_t ldy, int has_b,
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if ((e = cudaMemsetAsync(&buf.bar->count, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
-  const bool big = n >= kBlockedMinN && (size_t)d * ncol * sizeof(TY) >= kBlockedMinBytes;
+  const bool big = (size_t)d * ncol * sizeof(TY) >= kBlockedMinBytes;
   const bool blocked = buf.mode == 2 || (buf.mode == 0 && big);
   if (buf.blk && blocked && (size_t)kPanelMax * ncol <= ((size_t)1 << 31)) {
     if ((e = householder_blocked<TY>(W, d, n, ncol, buf.rdiag, buf, sms, st)) != cudaSuccess) return e;
