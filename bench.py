@@ -2,7 +2,7 @@
 configuration, a dense 5,000,000 x 2000 FP64 problem (80 GB; singular values
 geometric 1..1e-8; b = A x_true + 1e-6 g/||g||), sparse sign sketch d = 8000,
 zeta = 8, LSQR tolerance 1e-12, at backward error <= 1e-10.  The headline is
-the plain FP64 form; the mixed form (FP32 compensated sketch, FP32 QR) runs on
+the plain FP64 form; the mixed form (sketch terms added in FP32 chunk sums) runs on
 the same A and b beside it, and the 2,000,000 x 500 coherent-row problem
 (d = 2000) is reported as an extra key.
 
@@ -143,14 +143,18 @@ def _workload(p, prec):
             if 8 * m * n > L2_BYTES else "inputs fit in L2 (small config)"}
 
 
-# DRAM traffic / algorithmic bytes of the double-float LSQR kernel, from the ncu
-# capture summarised in profiles/lsqr_df_1000000x500.md (1e6 x 500, 5 passes:
-# 25.33 GB measured for 24.08 GB algorithmic); traffic grows with passes x rows.
-LSQR_DF_TRAFFIC_RATIO = 25.33 / 24.08
-# The kernel's block sums changed after that capture (the per-warp totals are
-# now added on one lane), so its counters no longer describe the code that
-# runs: the bench line reports traffic as null until the next capture.
-LSQR_DF_TRAFFIC_CURRENT = False
+# DRAM traffic / algorithmic bytes of the double-float LSQR kernels, each from
+# one ncu capture of a whole launch (init pass, all iterations, accuracy pass):
+#   k_lsqr_df<8>, 1e6 x 500, 35 iterations: 161.64 GB measured / 148.73 GB
+#     algorithmic (profiles/lsqr_df_1000000x500.md)
+#   k_lsqr_dfp<4>, 250,000 x 2000, 36 iterations: 166.53 GB / 154.46 GB
+#     (profiles/lsqr_dfp_250000x2000.md)
+# The excess is mostly the float-pair image the first pass writes (8mn, 2.7%),
+# which the algorithmic count leaves out.  Every term of both counts is linear
+# in the rows and the passes, so a launch on another problem of the same kernel
+# moves ratio x its algorithmic bytes.
+LSQR_DF_TRAFFIC_RATIO = 161.64 / 148.73
+LSQR_DFP_TRAFFIC_RATIO = 166.53 / 154.46
 
 
 def lsqr_algorithmic_bytes(m, n, iters):
@@ -691,7 +695,10 @@ def run_headline(args):
         "lsqr_arith": "df47 (A as float pairs of its top 47 bits, pair sums; FP64 recurrences; native FP64 check)",
         "roofline": {"bound": "hbm", "kernel": "k_lsqr_dfp<4> (LSQR + accuracy pass, one launch per solve)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json, of measured)",
+                     "traffic": LSQR_DFP_TRAFFIC_RATIO * alg,
+                     "traffic_source": "ncu capture ratio (profiles/lsqr_dfp_250000x2000.md, 250,000 x 2000) x this "
+                                       "launch's algorithmic bytes: both scale with rows x passes",
+                     "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json, of measured)",
                      "algorithmic_bytes_per_launch": alg,
                      "achieved_excluding_check": achieved_iter,
                      "check_pass_ms": t_check,
@@ -715,7 +722,7 @@ def run_headline(args):
                   "rel_residual_distance_to_plain": dist_mp,
                   "backward_error_ne": chk_m["backward_error_ne"], "backward_error_pre": minfos[-1][
                       "backward_error_pre"],
-                  "dtype": "sketch: FP32 compensated accumulation; QR: FP32; LSQR: df47 + FP64 recurrences"},
+                  "dtype": "sketch: terms added in FP32 (chunk sums of ~16 terms per entry, combined in FP64); QR: FP64 (tcgen05 trailing updates, FP32 accumulation); LSQR: df47 + FP64 recurrences"},
         "clocks": clocks,
     }
 
@@ -928,13 +935,13 @@ def run_gpu(args, emit=True):
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": _workload(p, args.prec),
-        "roofline": {"bound": "hbm", "kernel": "k_lsqr_native" if args.native else "k_lsqr_df", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": "k_lsqr_native" if args.native else ("k_lsqr_dfp" if n > 512 else "k_lsqr_df"),
+                     "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None if (args.native or n > 512 or args.prec != "fp64" or not LSQR_DF_TRAFFIC_CURRENT)
-                     else LSQR_DF_TRAFFIC_RATIO * alg_bytes,
-                     "traffic_last_capture": {"ratio_to_algorithmic": round(LSQR_DF_TRAFFIC_RATIO, 4),
-                                              "summary": "profiles/lsqr_df_1000000x500.md",
-                                              "current": LSQR_DF_TRAFFIC_CURRENT},
+                     "traffic": None if args.native else (LSQR_DFP_TRAFFIC_RATIO if n > 512 else LSQR_DF_TRAFFIC_RATIO)
+                     * alg_bytes,
+                     "traffic_source": "ncu capture ratio x this launch's algorithmic bytes ("
+                     + ("profiles/lsqr_dfp_250000x2000.md" if n > 512 else "profiles/lsqr_df_1000000x500.md") + ")",
                      "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
                      else "fallback 6.8 TB/s"},
         "gpu_launches": 8 * args.steps,

@@ -66,10 +66,11 @@ typedef int32_t lsq_status;
  * entries below 2^-103 of the largest entry of A (or b) are flushed. */
 typedef enum {
   LSQ_PREC_FP64 = 0,  /* sketch accumulated and factored in FP64 */
-  LSQ_PREC_MIXED = 1  /* sketch accumulated in FP32 (compensated: every atomic add's exact
-                         rounding error is accumulated in a second FP32 array, so the sum
-                         matches the FP64 sketch to about u_fp32^2 sqrt(terms per entry)),
-                         rounded once to FP32 and factored in FP32 */
+  LSQ_PREC_MIXED = 1  /* every sketch term added in FP32, one chunk of rows at a time (about
+                         16 terms per entry per chunk), the chunk sums combined in FP64;
+                         lsq_solve factors that sketch in FP64 (tensor-core trailing updates
+                         with FP32 accumulation, as the plain form), lsq_precond with FP32 Y
+                         factors in FP32 */
 } lsq_prec;
 
 typedef enum { LSQ_MEM_DEVICE = 0, LSQ_MEM_HOST = 1 } lsq_mem;
@@ -77,9 +78,11 @@ typedef enum { LSQ_MEM_DEVICE = 0, LSQ_MEM_HOST = 1 } lsq_mem;
 typedef struct lsq_ctx lsq_ctx;
 
 /* One least-squares problem. A: m x n row-major (lda >= n), b: m. With
- * mem = LSQ_MEM_HOST, A, b and the solution x live in host memory (pinned
- * memory gives full copy speed) and the library copies them to and from the
- * device inside the call. */
+ * mem = LSQ_MEM_HOST, A, b and the solution x live in host memory and the
+ * library moves them to and from the device inside the call: when A and b are
+ * pinned or registered (page-locked) and prec = LSQ_PREC_FP64, the sketch
+ * pass reads them in place over the host link and writes the device copy in
+ * the same pass; otherwise they are copied to the device before the sketch. */
 typedef struct {
   const double* A;
   const double* b;
@@ -169,9 +172,9 @@ lsq_status lsq_sketch_indices(lsq_ctx* ctx, uint64_t seed, int64_t row0, int64_t
 /* Y = S [A | b]  (Algorithm 1 "Form Y = SA"; S never stored).
  * A: device, m x n (lda >= n); b: device m or NULL.
  * Y: device, d x ldy row-major, ldy >= n + (b != NULL); FP64 (prec FP64) or
- * FP32 (prec MIXED; compensated accumulation, rounded once to FP32, when
- * ldy % 4 == 0 and Y is 16-byte aligned; plain FP32 accumulation otherwise).
- * Y is overwritten.  Errors: LSQ_ERR_ARG, LSQ_ERR_SKETCH, LSQ_ERR_NONFINITE
+ * FP32 (prec MIXED: FP32 accumulation in row chunks whose sums are combined in
+ * FP64 workspace of d (n + 1) doubles plus d (n + 4) floats, then rounded once
+ * to FP32).  Y is overwritten.  Errors: LSQ_ERR_ARG, LSQ_ERR_SKETCH, LSQ_ERR_NONFINITE
  * (A or b not finite). */
 lsq_status lsq_sketch(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d,
                       int32_t zeta, uint64_t seed, int32_t prec, void* Y, int64_t ldy, void* stream);
@@ -287,9 +290,12 @@ lsq_status lsq_check_noalloc(const double* A, int64_t m, int64_t n, int64_t lda,
 /* Algorithm 1 end to end: sketch, precondition, LSQR, accuracy pass.
  * x: n doubles, device memory for LSQ_MEM_DEVICE problems, host memory for
  * LSQ_MEM_HOST problems.  info may be NULL.
- * prec = LSQ_PREC_MIXED accumulates the sketch in FP32 (compensated) and
- * factors it in FP32; the preconditioner then carries FP32 rounding, good while
- * cond(A) * 6e-8 * sqrt(n) stays below about one.  The mixed LSQR is capped at
+ * prec = LSQ_PREC_MIXED adds every sketch term in FP32 (4-wide vector
+ * reductions, a third of the FP64 reduction cost per term) in row chunks whose
+ * sums are combined in FP64, then factors the sketch as the plain form does:
+ * the relative error of the sketch stays near FP32's unit roundoff times the
+ * square root of the terms per chunk, which keeps the preconditioner's
+ * quality while cond(A) * 1e-7 stays well below one.  The mixed LSQR is capped at
  * twice the iterations the Sec. 4.3 rate estimate predicts
  * (2 ceil(log(tol)/log(sqrt(n/d))) + 5); if it stalls, fails the accuracy
  * gate, or max|A| or max|b| lies outside [2^-60, 2^101) (the FP32 sketch's

@@ -139,6 +139,18 @@ lsq_status read_small(lsq_ctx* ctx, cudaStream_t st, uint32_t* bits, int32_t* ro
 
 bool vec_ok(const double* A, int64_t lda) { return ((uintptr_t)A % 16 == 0) && (lda % 2 == 0); }
 
+// The address at which kernels read host memory p, when p lies in pinned or
+// registered host memory (page-locked, mapped into the device's address
+// space); nullptr for pageable memory, which is copied instead.
+const void* host_device_view(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 int64_t default_maxit(int64_t n, int64_t d, double tol) {
   const double rate = std::sqrt((double)n / (double)d);
   if (!(tol > 0.0) || !(rate < 1.0)) return 1000;
@@ -525,22 +537,23 @@ lsq_status lsq_sketch(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64
   if (prec != LSQ_PREC_FP64 && prec != LSQ_PREC_MIXED) return fail(ctx, LSQ_ERR_ARG, "unknown precision");
   cudaStream_t st = (cudaStream_t)stream;
   if ((s = reset_small(ctx, st)) != LSQ_OK) return s;
-  const size_t esz = prec == LSQ_PREC_FP64 ? 8 : 4;
-  CK(cudaMemsetAsync(Y, 0, (size_t)d * ldy * esz, st));
   if (prec == LSQ_PREC_FP64) {
+    CK(cudaMemsetAsync(Y, 0, (size_t)d * ldy * sizeof(double), st));
     CK(sketch_apply<double>(A, m, n, lda, b, d, zeta, seed, 0, (double*)Y, ldy, ctx->d_status, ctx->d_max_rounds,
                             nullptr, nullptr, ctx->sms, st));
-  } else if (ldy % 4 == 0 && (uintptr_t)Y % 16 == 0) {
-    // compensated FP32 accumulation (error terms in workspace), then Y += Ylo
-    if ((s = ensure_ws(ctx, align_up((size_t)d * ldy * sizeof(float)))) != LSQ_OK) return s;
-    float* Ylo = reinterpret_cast<float*>(ctx->ws);
-    CK(cudaMemsetAsync(Ylo, 0, (size_t)d * ldy * sizeof(float), st));
-    CK(sketch_apply_f32c(A, m, n, lda, b, d, zeta, seed, 0, (float*)Y, Ylo, ldy, ctx->d_status, ctx->d_max_rounds,
-                         nullptr, nullptr, ctx->sms, st));
-    CK(add_lo((float*)Y, Ylo, d * ldy, ctx->sms, st));
   } else {
-    CK(sketch_apply<float>(A, m, n, lda, b, d, zeta, seed, 0, (float*)Y, ldy, ctx->d_status, ctx->d_max_rounds,
-                           nullptr, nullptr, ctx->sms, st));
+    // blocked FP32 accumulation (chunk sums in FP32, folded into an FP64
+    // sketch in workspace), rounded once into the FP32 output
+    const int64_t ncol = n + (b ? 1 : 0), ldc = (ncol + 3) / 4 * 4;
+    const size_t y64 = align_up((size_t)d * ncol * sizeof(double));
+    if ((s = ensure_ws(ctx, y64 + align_up((size_t)d * ldc * sizeof(float)))) != LSQ_OK) return s;
+    double* Y64 = reinterpret_cast<double*>(ctx->ws);
+    float* Yc = reinterpret_cast<float*>(static_cast<char*>(ctx->ws) + y64);
+    CK(cudaMemsetAsync(Y64, 0, (size_t)d * ncol * sizeof(double), st));
+    CK(cudaMemsetAsync(Yc, 0, (size_t)d * ldc * sizeof(float), st));
+    CK(sketch_apply_fold(A, m, n, lda, b, d, zeta, seed, Yc, ldc, Y64, ncol, ctx->d_status, ctx->d_max_rounds,
+                         nullptr, nullptr, ctx->d_bar, ctx->sms, st));
+    CK(round_to_float(Y64, ncol, static_cast<float*>(Y), ldy, d, ncol, ctx->sms, st));
   }
   uint32_t bits = 0;
   if ((s = read_small(ctx, st, &bits, nullptr, nullptr)) != LSQ_OK) return s;
@@ -737,11 +750,23 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
     return fail(ctx, LSQ_ERR_UNSUPPORTED, "native FP64 LSQR kernel built for n <= 512");
   cudaStream_t st = (cudaStream_t)stream;
   const bool host = pr->mem == LSQ_MEM_HOST;
+  // host problems in pinned or registered memory are read in place by the
+  // FP64 sketch, which writes the device copy in the same pass (no separate
+  // copy before it); pageable memory is copied first
+  const double* hA = nullptr;
+  const double* hb = nullptr;
+  if (host && o->prec == LSQ_PREC_FP64) {
+    hA = static_cast<const double*>(host_device_view(pr->A));
+    hb = static_cast<const double*>(host_device_view(pr->b));
+  }
+  const bool tee = hA && hb;
   const bool timing = (o->flags & LSQ_FLAG_TIMING) != 0;
   const int ni = (int)n, npad = (int)((n + 31) / 32 * 32);
-  // the mixed form's 4-wide FP32 reductions want rows of Y padded to 4 floats
-  const int64_t ncol = n + 1, ldy = o->prec == LSQ_PREC_MIXED ? (ncol + 3) / 4 * 4 : ncol;
-  const size_t yes = o->prec == LSQ_PREC_FP64 ? 8 : 4;
+  // Y is FP64 in both forms; the mixed form accumulates its terms in FP32
+  // chunk sums (Yc, rows padded to 4 floats for the 4-wide reductions)
+  const int64_t ncol = n + 1, ldy = ncol, ldc = (ncol + 3) / 4 * 4;
+  const size_t yes = 8;
+  const bool mixed = o->prec == LSQ_PREC_MIXED;
   const int64_t lda_dev = host ? n : lda;
   const bool vec = host ? (n % 2 == 0) : vec_ok(pr->A, lda);
   // host problems are copied into 256-byte aligned workspace with lda = n
@@ -751,6 +776,7 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
   const int64_t maxit = o->maxit > 0 ? o->maxit : default_maxit(n, d, o->tol);
 
   bool image = !native && !(o->flags & LSQ_FLAG_NO_IMAGE);
+  float* Yc = nullptr;
   auto carve = [&](Carver& cv, const double** A, const double** b, double** xd, void** Y, PrecondBuffers* pb,
                    double** R, double** M, LsqrWork* lw) {
     if (host) {
@@ -763,8 +789,7 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
       *xd = x;
     }
     *Y = cv.take<char>((size_t)d * ldy * yes);
-    // mixed form: the compensated sketch's error terms, same layout as Y
-    pb->Ylo = o->prec == LSQ_PREC_MIXED ? cv.take<float>((size_t)d * ldy) : nullptr;
+    Yc = mixed ? cv.take<float>((size_t)d * ldc) : nullptr;
     pb->W = cv.take<double>((size_t)ncol * d);
     pb->rdiag = cv.take<double>(npad);
     pb->blk = cv.take<char>(precond_blocked_bytes(d, n));
@@ -815,7 +840,7 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
   Events<6> ev;
   if (timing) CK(ev.create());
   if (timing) CK(cudaEventRecord(ev[0], st));
-  if (host) {
+  if (host && !tee) {
     if (lda == n)  // packed rows: one flat copy
       CK(cudaMemcpyAsync((void*)A, pr->A, sizeof(double) * (size_t)m * n, cudaMemcpyHostToDevice, st));
     else
@@ -828,21 +853,23 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
   CK(cudaMemsetAsync(Y, 0, (size_t)d * ldy * yes, st));
   // the sketch also records the exponent range of A and b (ctx->d_range) for
   // the double-float LSQR passes
-  if (o->prec == LSQ_PREC_FP64) {
+  if (tee) {
+    CK(sketch_apply_tee(hA, m, n, lda, hb, d, o->zeta, o->seed, (double*)Y, ldy, const_cast<double*>(A), lda_dev,
+                        const_cast<double*>(b), ctx->d_status, ctx->d_max_rounds, ctx->d_range, ctx->d_fro,
+                        ctx->sms, st));
+  } else if (o->prec == LSQ_PREC_FP64) {
     CK(sketch_apply<double>(A, m, n, lda_dev, b, d, o->zeta, o->seed, 0, (double*)Y, ldy, ctx->d_status,
                             ctx->d_max_rounds, ctx->d_range, ctx->d_fro, ctx->sms, st));
   } else {
-    // compensated FP32 accumulation: Y + Ylo, summed once into the QR's copy
-    CK(cudaMemsetAsync(const_cast<void*>(pb.Ylo), 0, (size_t)d * ldy * sizeof(float), st));
-    CK(sketch_apply_f32c(A, m, n, lda_dev, b, d, o->zeta, o->seed, 0, (float*)Y,
-                         static_cast<float*>(const_cast<void*>(pb.Ylo)), ldy, ctx->d_status, ctx->d_max_rounds,
-                         ctx->d_range, ctx->d_fro, ctx->sms, st));
+    // blocked FP32 accumulation: chunk sums in Yc, folded into the FP64 Y
+    CK(cudaMemsetAsync(Yc, 0, (size_t)d * ldc * sizeof(float), st));
+    CK(sketch_apply_fold(A, m, n, lda_dev, b, d, o->zeta, o->seed, Yc, ldc, (double*)Y, ldy, ctx->d_status,
+                         ctx->d_max_rounds, ctx->d_range, ctx->d_fro, ctx->d_bar, ctx->sms, st));
   }
   if (timing) CK(cudaEventRecord(ev[2], st));
-  if (o->prec == LSQ_PREC_FP64)
-    CK(precond<double>((const double*)Y, d, n, ldy, 1, R, M, xd, pb, ctx->sms, st));
-  else
-    CK(precond<float>((const float*)Y, d, n, ldy, 1, R, M, xd, pb, ctx->sms, st));
+  // both forms factor the FP64 sketch (the tensor-core trailing updates
+  // accumulate bf16 slice products in FP32 either way)
+  CK(precond<double>((const double*)Y, d, n, ldy, 1, R, M, xd, pb, ctx->sms, st));
   if (timing) CK(cudaEventRecord(ev[3], st));
   // status after the preconditioner (sketch failure, rank) before iterating
   uint32_t bits = 0;

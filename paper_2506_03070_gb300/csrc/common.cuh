@@ -164,6 +164,14 @@ __device__ __forceinline__ float warp_allreduce_sum(float v) {
   return v;
 }
 
+// The 32-double scratch of block_sum, one per block for all callers: every
+// block_sum starts with a barrier before it writes the scratch, so calls in
+// sequence may share it.
+__device__ __forceinline__ double* block_scratch() {
+  __shared__ double s_scratch[32];
+  return s_scratch;
+}
+
 // Block-wide sum in a fixed order (deterministic for a fixed block size).
 // `scratch` holds at least 32 doubles.  Result valid in every thread.  One
 // thread adds the per-warp sums and shares the total: GB300's FP64 pipe

@@ -15,19 +15,29 @@ cudaError_t sketch_indices(uint64_t seed, int64_t row0, int64_t rows, int64_t d,
 // range (nullable, [2] words, zeroed by the caller): atomic max of the
 // exponent field (high word & 0x7FF00000) over A's and over b's finite entries.
 // fro (nullable, zeroed by the caller): FP64 sum of A_ij^2 (atomic adds of warp partials).
-template <typename TY>
+template <typename TY>  // double
 cudaError_t sketch_apply(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d, int zeta,
                          uint64_t seed, int64_t row0, TY* Y, int64_t ldy, uint32_t* status, int32_t* max_rounds,
                          uint32_t* range, double* fro, int sms, cudaStream_t st);
-// Mixed form: FP32 accumulation into Y (ldy % 4 == 0, 16-byte aligned); with
-// Ylo (same shape, zeroed) non-null, compensated: the exact rounding error of
-// every add goes into Ylo, and Y + Ylo is the sketch to about u^2 sqrt(N).
-cudaError_t sketch_apply_f32c(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d,
-                              int zeta, uint64_t seed, int64_t row0, float* Y, float* Ylo, int64_t ldy,
-                              uint32_t* status, int32_t* max_rounds, uint32_t* range, double* fro, int sms,
-                              cudaStream_t st);
-// Y[e] = fl32(Y[e] + Ylo[e]) for e < count.
-cudaError_t add_lo(float* Y, const float* Ylo, int64_t count, int sms, cudaStream_t st);
+// out (d x ncol floats, row stride ldo) = Y (FP64, row stride ldy) rounded to nearest.
+cudaError_t round_to_float(const double* Y, int64_t ldy, float* out, int64_t ldo, int64_t d, int64_t ncol, int sms,
+                           cudaStream_t st);
+// The mixed form's sketch with blocked FP32 accumulation: terms are added in
+// FP32 into Yc (d x ldc floats, ldc % 4 == 0, zero on entry and on exit) one
+// chunk of rows at a time, each chunk's sums then added into the FP64 sketch
+// Y (d x ldy, zero on entry).  Cooperative launch; bar's counter is reset.
+cudaError_t sketch_apply_fold(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d,
+                              int zeta, uint64_t seed, float* Yc, int64_t ldc, double* Y, int64_t ldy,
+                              uint32_t* status, int32_t* max_rounds, uint32_t* range, double* fro, GridBarrier* bar,
+                              int sms, cudaStream_t st);
+// The FP64 sketch of a problem in host memory the device reads in place
+// (A, b: device-usable addresses of pinned or registered host memory, row
+// stride lda): the same Y as sketch_apply, and every entry is also stored to
+// the device copy Aout (row stride ldo) and bout.
+cudaError_t sketch_apply_tee(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d,
+                             int zeta, uint64_t seed, double* Y, int64_t ldy, double* Aout, int64_t ldo, double* bout,
+                             uint32_t* status, int32_t* max_rounds, uint32_t* range, double* fro, int sms,
+                             cudaStream_t st);
 // The same range words (and DS_NONFINITE) from one read of A and b, for LSQR
 // calls that do not sketch first.
 cudaError_t range_scan(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, uint32_t* range,
@@ -43,7 +53,6 @@ struct PrecondBuffers {
   uint32_t* status;
   void* blk;       // precond_blocked_bytes(d, n) of scratch for the blocked QR, or null (unblocked)
   int mode;        // 0: choose by size, 1: unblocked, 2: blocked (LSQ_QR_*)
-  const void* Ylo = nullptr;  // compensated FP32 sketch: error terms added to Y (same type and layout), or null
 };
 // Scratch the blocked Householder QR needs for a d x (n+1) sketch.
 size_t precond_blocked_bytes(int64_t d, int64_t n);
@@ -158,6 +167,15 @@ int lsqr_gparts(int grid);
 // Grid size the LSQR kernel will use for n (co-resident blocks).
 int lsqr_grid(int n, bool vec, bool native, int sms);
 cudaError_t lsqr_run(const LsqrParams& p, bool vec, bool native, int grid, cudaStream_t st);
+// The kernel families behind lsqr_grid / lsqr_run (lsqr_rows.cu: double-float,
+// one warp per row, `chunks` column pairs per lane; lsqr_wide.cu: double-float,
+// `panels` warps per row; lsqr_native.cu: native FP64).  Grid 0 = unusable.
+int lsqr_rows_grid(int chunks, int n, int sms);
+cudaError_t lsqr_rows_run(int chunks, const LsqrParams& p, int grid, cudaStream_t st);
+int lsqr_wide_grid(int panels, int n, int sms);
+cudaError_t lsqr_wide_run(int panels, const LsqrParams& p, int grid, cudaStream_t st);
+int lsqr_native_grid(int chunks, bool vec, int sms);
+cudaError_t lsqr_native_run(int chunks, bool vec, const LsqrParams& p, int grid, cudaStream_t st);
 // Self-test of the bounded device waits: kind 0 -- a grid barrier of `blocks`
 // co-resident blocks that expects one block more (it can never fill); kind 1
 // -- an mbarrier phase that nothing completes.  Both give up after the

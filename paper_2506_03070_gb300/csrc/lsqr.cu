@@ -15,137 +15,14 @@
 // and 4 run heavy-ball momentum (Algorithm 6) over the same passes instead.  After the
 // loop the same pass structure computes r = b - A x, A^T r and ||A||_F (the
 // accuracy check) and the backward-error bounds.
+// The kernels are instantiated in lsqr_rows.cu (double-float, n <= 512),
+// lsqr_wide.cu (double-float, 512 < n <= 4096) and lsqr_native.cu (native
+// FP64, n <= 512); this file dispatches to them and holds the wait self-tests.
 #include "lsqr_device.cuh"
 
 namespace lsq {
 
 namespace {
-
-template <int T, bool VEC>
-__global__ void __launch_bounds__(kThreads, 2) k_lsqr_native(LsqrParams p) {
-  __shared__ double s_g[kWarps * 64 * T];
-  __shared__ double s_scal[kWarps * 4];
-  NativePass<T, VEC> pass{s_g, s_scal};
-  p.gidx = blockIdx.x;
-  p.gcount = gridDim.x;
-  if (p.mode >= 3)
-    hbm_body(p, pass, s_scal);
-  else
-    lsqr_body(p, pass, s_scal);
-}
-
-template <int T>
-__global__ void __launch_bounds__(kThreads, 2) k_lsqr_df(LsqrParams p) {
-  extern __shared__ __align__(128) double s_ring[];
-  __shared__ __align__(8) uint64_t s_bars[kWarps * kNbuf];
-  __shared__ double s_scal[kWarps * 4];
-  __shared__ __align__(16) float2 s_w[64 * T];
-  if ((threadIdx.x & 31) == 0) {
-    for (int b = 0; b < kNbuf; ++b) mbar_init(&s_bars[(threadIdx.x >> 5) * kNbuf + b], 1u);
-    fence_proxy_async_smem();
-  }
-  __syncthreads();
-  DfPass<32, T> pass{s_ring, s_bars, s_scal, 0u, s_w};
-  p.gidx = blockIdx.x;
-  p.gcount = gridDim.x;
-  if (p.mode >= 3)
-    hbm_body(p, pass, s_scal);
-  else
-    lsqr_body(p, pass, s_scal);
-}
-
-// n > 512: PW warps per row (column panels of at most 512); ring of panel
-// slices, then the pass vector as float pairs, in dynamic shared memory.
-template <int PW>
-__global__ void __launch_bounds__(kThreads, 2) k_lsqr_dfp(LsqrParams p) {
-  extern __shared__ __align__(128) double s_ring[];
-  __shared__ __align__(8) uint64_t s_bars[kWarps * kNbuf];
-  __shared__ __align__(16) double s_scal[kWarps * 6];
-  if ((threadIdx.x & 31) == 0) {
-    for (int b = 0; b < kNbuf; ++b) mbar_init(&s_bars[(threadIdx.x >> 5) * kNbuf + b], 1u);
-    fence_proxy_async_smem();
-  }
-  __syncthreads();
-  float2* s_w = reinterpret_cast<float2*>(s_ring + (size_t)kWarps * kNbuf * 512);
-  DfPass<32, 8, false, PW> pass{s_ring, s_bars, s_scal, 0u, s_w};
-  p.gidx = blockIdx.x;
-  p.gcount = gridDim.x;
-  if (p.mode >= 3)
-    hbm_body(p, pass, s_scal);
-  else
-    lsqr_body(p, pass, s_scal);
-}
-
-size_t dfp_smem(int n) { return (size_t)kWarps * kNbuf * 512 * sizeof(double) + (size_t)((n + 1) / 2 * 2) * 8; }
-
-template <int PW>
-int grid_dfp(int n, int sms) {
-  const size_t smem = dfp_smem(n);
-  if (cudaFuncSetAttribute(k_lsqr_dfp<PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return 0;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lsqr_dfp<PW>, kThreads, smem) != cudaSuccess ||
-      per_sm < 1)
-    return 0;
-  if (per_sm > 2) per_sm = 2;
-  return per_sm * sms;
-}
-
-template <int PW>
-cudaError_t launch_dfp(const LsqrParams& p, int grid, cudaStream_t st) {
-  LsqrParams q = p;
-  void* args[] = {&q};
-  const size_t smem = dfp_smem(p.n);
-  cudaError_t e = cudaFuncSetAttribute(k_lsqr_dfp<PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaLaunchCooperativeKernel((const void*)k_lsqr_dfp<PW>, grid, kThreads, args, smem, st);
-}
-
-size_t df_smem(int T, int n) {
-  const size_t ring = (size_t)kWarps * kNbuf * (size_t)((n + 1) / 2 * 2) * sizeof(double);  // one row per step
-  const size_t red = (size_t)kWarps * 64 * T * sizeof(double);
-  return ring > red ? ring : red;
-}
-
-template <int T, bool VEC>
-int grid_native(int sms) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lsqr_native<T, VEC>, kThreads, 0) != cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
-  if (per_sm > 2) per_sm = 2;
-  return per_sm * sms;
-}
-
-template <int T>
-int grid_df(int n, int sms) {
-  const size_t smem = df_smem(T, n);
-  if (cudaFuncSetAttribute(k_lsqr_df<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return 0;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lsqr_df<T>, kThreads, smem) != cudaSuccess ||
-      per_sm < 1)
-    return 0;
-  if (per_sm > 2) per_sm = 2;
-  return per_sm * sms;
-}
-
-template <int T, bool VEC>
-cudaError_t launch_native(const LsqrParams& p, int grid, cudaStream_t st) {
-  LsqrParams q = p;
-  void* args[] = {&q};
-  return cudaLaunchCooperativeKernel((const void*)k_lsqr_native<T, VEC>, grid, kThreads, args, 0, st);
-}
-
-template <int T>
-cudaError_t launch_df(const LsqrParams& p, int grid, cudaStream_t st) {
-  LsqrParams q = p;
-  void* args[] = {&q};
-  const size_t smem = df_smem(T, p.n);
-  cudaError_t e = cudaFuncSetAttribute(k_lsqr_df<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaLaunchCooperativeKernel((const void*)k_lsqr_df<T>, grid, kThreads, args, smem, st);
-}
 
 // column pairs per lane of the one-warp-per-row kernels (n <= 512)
 int chunks_for(int n) {
@@ -207,56 +84,22 @@ bool lsqr_native_ok(int64_t n) { return n >= 1 && n <= 512; }
 
 int lsqr_grid(int n, bool vec, bool native, int sms) {
   if (!native && n > 512) {
-    switch (panels_for(n)) {
-      case 2: return grid_dfp<2>(n, sms);
-      case 4: return grid_dfp<4>(n, sms);
-      case 8: return grid_dfp<8>(n, sms);
-      default: return 0;
-    }
+    return lsqr_wide_grid(panels_for(n), n, sms);
   }
   if (!native) {
-    switch (chunks_for(n)) {
-      case 1: return grid_df<1>(n, sms);
-      case 2: return grid_df<2>(n, sms);
-      case 4: return grid_df<4>(n, sms);
-      case 8: return grid_df<8>(n, sms);
-      default: return 0;
-    }
+    return lsqr_rows_grid(chunks_for(n), n, sms);
   }
-  switch (chunks_for(n)) {
-    case 1: return vec ? grid_native<1, true>(sms) : grid_native<1, false>(sms);
-    case 2: return vec ? grid_native<2, true>(sms) : grid_native<2, false>(sms);
-    case 4: return vec ? grid_native<4, true>(sms) : grid_native<4, false>(sms);
-    case 8: return vec ? grid_native<8, true>(sms) : grid_native<8, false>(sms);
-    default: return 0;
-  }
+  return lsqr_native_grid(chunks_for(n), vec, sms);
 }
 
 cudaError_t lsqr_run(const LsqrParams& p, bool vec, bool native, int grid, cudaStream_t st) {
   if (!native && p.n > 512) {
-    switch (panels_for(p.n)) {
-      case 2: return launch_dfp<2>(p, grid, st);
-      case 4: return launch_dfp<4>(p, grid, st);
-      case 8: return launch_dfp<8>(p, grid, st);
-      default: return cudaErrorInvalidValue;
-    }
+    return lsqr_wide_run(panels_for(p.n), p, grid, st);
   }
   if (!native) {
-    switch (chunks_for(p.n)) {
-      case 1: return launch_df<1>(p, grid, st);
-      case 2: return launch_df<2>(p, grid, st);
-      case 4: return launch_df<4>(p, grid, st);
-      case 8: return launch_df<8>(p, grid, st);
-      default: return cudaErrorInvalidValue;
-    }
+    return lsqr_rows_run(chunks_for(p.n), p, grid, st);
   }
-  switch (chunks_for(p.n)) {
-    case 1: return vec ? launch_native<1, true>(p, grid, st) : launch_native<1, false>(p, grid, st);
-    case 2: return vec ? launch_native<2, true>(p, grid, st) : launch_native<2, false>(p, grid, st);
-    case 4: return vec ? launch_native<4, true>(p, grid, st) : launch_native<4, false>(p, grid, st);
-    case 8: return vec ? launch_native<8, true>(p, grid, st) : launch_native<8, false>(p, grid, st);
-    default: return cudaErrorInvalidValue;
-  }
+  return lsqr_native_run(chunks_for(p.n), vec, p, grid, st);
 }
 
 }  // namespace lsq

@@ -187,7 +187,7 @@ struct NativePass {
 // Column j is summed by block j % G: thread t adds partials t, t+256, ...,
 // then a fixed-order block reduction (deterministic for a given grid).
 __device__ void reduce_g(const LsqrParams& p) {
-  __shared__ double scratch[32];
+  double* scratch = block_scratch();
   const int G = p.gcount;
   for (int j = p.gidx; j < p.n; j += G) {
     double s = 0.0;
@@ -201,7 +201,7 @@ __device__ void reduce_g(const LsqrParams& p) {
 // then a fixed-order block reduction.  Every thread of every block calls it
 // and gets the same value.
 __device__ double sum_part(const LsqrParams& p, int slot) {
-  __shared__ double scratch[32];
+  double* scratch = block_scratch();
   double s = 0.0;
   for (int c = threadIdx.x; c < p.gcount; c += kThreads) s += p.part[(int64_t)c * 4 + slot];
   return block_sum(s, scratch);
@@ -755,15 +755,20 @@ struct DfPass {
             *reinterpret_cast<float4*>(p.asplit + row * p.ldi + c) = make_float4(H[t].x, H[t].y, Mm[t].x, Mm[t].y);
         }
       }
-      float2 avh = make_float2(0.f, 0.f), avl = make_float2(0.f, 0.f);
+      // four pair chains (even / odd t, each packed over two columns): two
+      // independent dependency chains per lane
+      float2 h0 = make_float2(0.f, 0.f), l0 = h0, h1 = h0, l1 = h0;
 #pragma unroll
       for (int t = 0; t < PPL; ++t) {
         const int c = c0 + 2 * lane + 64 * t;
         float4 ww = make_float4(0.f, 0.f, 0.f, 0.f);
         if (c < cend) ww = *reinterpret_cast<const float4*>(s_w + c);
-        df2_fma_acc(avh, avl, H[t], Mm[t], make_float2(ww.x, ww.y), make_float2(ww.z, ww.w));
+        if (t & 1)
+          df2_fma_acc(h1, l1, H[t], Mm[t], make_float2(ww.x, ww.y), make_float2(ww.z, ww.w));
+        else
+          df2_fma_acc(h0, l0, H[t], Mm[t], make_float2(ww.x, ww.y), make_float2(ww.z, ww.w));
       }
-      df dot = df_add(df{avh.x, avl.x}, df{avh.y, avl.y});
+      df dot = df_add(df_add(df{h0.x, l0.x}, df{h0.y, l0.y}), df_add(df{h1.x, l1.x}, df{h1.y, l1.y}));
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) dot = df_add_unnorm(dot, shfl_xor_df(dot, o));
       dot = df_renorm(dot);
@@ -1038,7 +1043,7 @@ __device__ void finish_body(LsqrParams& p, Pass& pass, double* s_scal, int64_t i
   if (p.M) mt_apply(p, 1.0, 0.0, 3, s_scal);
   if (!group_sync(p)) return;
   if (p.gidx == 0) {
-    __shared__ double scratch[32];
+    double* scratch = block_scratch();
     double gx = 0.0, xx = 0.0;
     for (int j = threadIdx.x; j < p.n; j += kThreads) {
       gx = fma(p.g[j], p.g[j], gx);

@@ -240,7 +240,7 @@ __device__ bool precond_group(const double* W, int d, int n, const double* rdiag
 
 // LSQR with chunked pass shape S: K = ring_k steps of 32/L rows per ring buffer.
 template <int S>
-__device__ void lsqr_shape(LsqrParams& p, double* ring, uint64_t* bars, double* s_scal, uint32_t& seq,
+__device__ __noinline__ void lsqr_shape(LsqrParams& p, double* ring, uint64_t* bars, double* s_scal, uint32_t& seq,
                            float2* s_w) {
   constexpr int R = 32 / shape_L(S);
   const int kk = kChunkDoubles / (R * (int)p.ldi);

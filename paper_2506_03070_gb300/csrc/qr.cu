@@ -31,10 +31,8 @@ namespace lsq {
 namespace {
 
 template <typename TY>
-__global__ void k_to_colmajor(const TY* __restrict__ Y, const TY* __restrict__ Ylo, int64_t d, int ncol, int64_t ldy,
-                              TY* __restrict__ W) {
+__global__ void k_to_colmajor(const TY* __restrict__ Y, int64_t d, int ncol, int64_t ldy, TY* __restrict__ W) {
   // 32x32 tiles through shared memory: read rows of Y, write columns of W.
-  // With Ylo (the compensated sketch's error terms), W = fl(Y + Ylo).
   __shared__ TY tile[32][33];
   const int64_t i0 = (int64_t)blockIdx.x * 32;
   const int j0 = blockIdx.y * 32;
@@ -42,10 +40,7 @@ __global__ void k_to_colmajor(const TY* __restrict__ Y, const TY* __restrict__ Y
     const int64_t i = i0 + r;
     const int j = j0 + threadIdx.x;
     TY v = (TY)0;
-    if (i < d && j < ncol) {
-      v = Y[i * ldy + j];
-      if (Ylo) v += Ylo[i * ldy + j];
-    }
+    if (i < d && j < ncol) v = Y[i * ldy + j];
     tile[r][threadIdx.x] = v;
   }
   __syncthreads();
@@ -205,14 +200,16 @@ __device__ __forceinline__ TW warp_sum_t(TW v) {
 // Factor the panel P = W[k0:d, k0:k0+b] (L = d - k0 rows, ld = d): for each
 // column j, the reflector of the unblocked kernel, applied to the panel's later
 // columns only.  Block g of G owns panel rows [L g / G, L (g+1) / G).  Per
-// column: (a) partial ||x_{j+1:}||^2 of my rows -> part, the owner of row j
-// publishes row j of the panel -> rowv; barrier; (b) every block sums the
-// partials in block order (same scalars everywhere), writes column j of U
-// (unit lower trapezoid: 0 above row j, 1 at j, x_i / (alpha - beta) below);
-// (c) partial dots of x with the later columns -> part; barrier; (d) every
+// column: (a) partial ||x_{j+1:}||^2 of my rows and partial dots of x_{j+1:}
+// with the later columns (both on the columns as the previous reflector left
+// them) -> part, the owner of row j publishes row j of the panel -> rowv;
+// barrier (the only one of the column); (b) every block sums the partials in
+// block order (same scalars everywhere), writes column j of U (unit lower
+// trapezoid: 0 above row j, 1 at j, x_i / (alpha - beta) below); (c) every
 // block updates its rows of the later columns.  part and rowv alternate by
-// column parity, so a block one step ahead never overwrites what a slower
-// block still reads.
+// column parity: a block reads column j's partials only between barrier j and
+// its arrival at barrier j+1, and they are rewritten (column j+2) only after
+// barrier j+1.
 template <typename TW>
 __global__ void __launch_bounds__(256) k_panel(TW* __restrict__ W, int64_t ld, int64_t k0, int64_t L, int b,
                                                TW* __restrict__ U, double* __restrict__ rdiag, TW* __restrict__ tau,
@@ -246,6 +243,14 @@ __global__ void __launch_bounds__(256) k_panel(TW* __restrict__ W, int64_t ld, i
     }
     s = block_sum_t<TW>(s, scratch);
     if (threadIdx.x == 0) prt[(int64_t)g * PS] = s;
+    // dots with the later columns as they are now: same barrier as the norm
+    for (int jj = j + 1 + wib; jj < b; jj += nwarps) {
+      const TW* pjj = P + (int64_t)jj * ld;
+      TW acc = 0;
+      for (int64_t i = i0 + lane; i < r1; i += 32) acc = fma(__ldcg(pj + i), __ldcg(pjj + i), acc);
+      acc = warp_sum_t<TW>(acc);
+      if (lane == 0) prt[(int64_t)g * PS + 1 + jj] = acc;
+    }
     if (j >= r0 && j < r1)
       for (int jj = j + threadIdx.x; jj < b; jj += blockDim.x) rv[jj] = __ldcg(P + (int64_t)jj * ld + j);
     if (!sync()) return;
@@ -268,14 +273,6 @@ __global__ void __launch_bounds__(256) k_panel(TW* __restrict__ W, int64_t ld, i
       uj[i] = i < j ? (TW)0 : (i == j ? (TW)1 : __ldcg(pj + i) * inv_v0);
     if (t == (TW)0) continue;  // same in every block: same barrier count
     for (int jj = j + 1 + wib; jj < b; jj += nwarps) {
-      const TW* pjj = P + (int64_t)jj * ld;
-      TW acc = 0;
-      for (int64_t i = i0 + lane; i < r1; i += 32) acc = fma(__ldcg(pj + i), __ldcg(pjj + i), acc);
-      acc = warp_sum_t<TW>(acc);
-      if (lane == 0) prt[(int64_t)g * PS + 1 + jj] = acc;
-    }
-    if (!sync()) return;
-    for (int jj = j + 1 + wib; jj < b; jj += nwarps) {
       TW S = 0;
       for (int q = 0; q < G; ++q) S += __ldcg(prt + (int64_t)q * PS + 1 + jj);
       const TW wj = __ldcg(rv + jj);
@@ -290,7 +287,7 @@ __global__ void __launch_bounds__(256) k_panel(TW* __restrict__ W, int64_t ld, i
 
 // The same factorisation with the block's rows of the panel held in shared
 // memory (column-major, nr rows per column) for the whole panel: the data
-// never leaves the SM between the two barriers of a column, only the
+// never leaves the SM between the barriers of the columns, only the
 // partial sums (norms, dots) and the published row j go through L2.  Block g
 // of G owns panel rows [L g / G, L (g+1) / G) (at most kPanelSmemRows); the
 // arithmetic is k_panel's, in the same order.  Writes U (column-major, ld)
@@ -333,6 +330,16 @@ __global__ void __launch_bounds__(256) k_panel_smem(TW* __restrict__ W, int64_t 
     for (int i = i0 + threadIdx.x; i < nr; i += blockDim.x) sq = fma(pj[i], pj[i], sq);
     sq = block_sum_t<TW>(sq, scratch);
     if (threadIdx.x == 0) prt[(int64_t)g * PS] = sq;
+    // the dots of x with the later columns need only the columns as they are
+    // now (before this column's reflector), so they go through the same
+    // barrier as the norm: one grid barrier per column
+    for (int jj = j + 1 + wib; jj < b; jj += nwarps) {
+      const TW* pjj = Ps + jj * nrp;
+      TW acc = 0;
+      for (int i = i0 + lane; i < nr; i += 32) acc = fma(pj[i], pjj[i], acc);
+      acc = warp_sum_t<TW>(acc);
+      if (lane == 0) prt[(int64_t)g * PS + 1 + jj] = acc;
+    }
     if (j >= r0 && j < r1)
       for (int jj = j + threadIdx.x; jj < b; jj += blockDim.x) rv[jj] = Ps[jj * nrp + (j - r0)];
     if (!sync()) return;
@@ -365,14 +372,6 @@ __global__ void __launch_bounds__(256) k_panel_smem(TW* __restrict__ W, int64_t 
       __syncthreads();
       continue;  // same in every block: same barrier count
     }
-    for (int jj = j + 1 + wib; jj < b; jj += nwarps) {
-      const TW* pjj = Ps + jj * nrp;
-      TW acc = 0;
-      for (int i = i0 + lane; i < nr; i += 32) acc = fma(pj[i], pjj[i], acc);
-      acc = warp_sum_t<TW>(acc);
-      if (lane == 0) prt[(int64_t)g * PS + 1 + jj] = acc;
-    }
-    if (!sync()) return;
     // column scalars, one thread per later column (sums in block order)
     for (int jj = j + 1 + threadIdx.x; jj < b; jj += blockDim.x) {
       TW S = 0;
@@ -719,7 +718,7 @@ cudaError_t precond(const TY* Y, int64_t d, int64_t n64, int64_t ldy, int has_b,
   cudaError_t e;
   {
     dim3 grid((unsigned)((d + 31) / 32), (unsigned)((ncol + 31) / 32)), block(32, 8);
-    k_to_colmajor<TY><<<grid, block, 0, st>>>(Y, reinterpret_cast<const TY*>(buf.Ylo), d, ncol, ldy, W);
+    k_to_colmajor<TY><<<grid, block, 0, st>>>(Y, d, ncol, ldy, W);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if ((e = cudaMemsetAsync(&buf.bar->count, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;

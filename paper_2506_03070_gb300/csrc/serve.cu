@@ -164,7 +164,7 @@ __device__ int claim(const ServeArgs& a, unsigned long long& idx, int& gidx, uns
 }
 
 template <int PW>
-__device__ void lsqr_wide(LsqrParams& p, double* ring, uint64_t* bars, double* s_scal, uint32_t& seq, float2* s_w) {
+__device__ __noinline__ void lsqr_wide(LsqrParams& p, double* ring, uint64_t* bars, double* s_scal, uint32_t& seq, float2* s_w) {
   p.ring_k = 1;
   DfPass<32, 8, false, PW> pass{ring, bars, s_scal, seq, s_w};
   lsqr_body(p, pass, s_scal);

@@ -13,6 +13,9 @@ namespace lsq {
 
 namespace {
 
+// Terms per FP32 partial sum of the blocked mixed-form sketch (k_sketch_fold).
+constexpr int kFoldTerms = 16;
+
 // One thread per column of S: export indices and signs.
 template <int N>
 __global__ void __launch_bounds__(256) k_sketch_indices(uint64_t seed, int64_t row0, int64_t rows, uint64_t d,
@@ -61,7 +64,6 @@ __device__ __forceinline__ void flush_range(uint32_t ea, uint32_t eb, uint32_t* 
 }
 
 __device__ __forceinline__ void red_add(double* p, double v) { atomicAdd(p, v); }
-__device__ __forceinline__ void red_add(float* p, double v) { atomicAdd(p, (float)v); }
 
 __device__ __forceinline__ double flip_sign(double v, bool neg) {
   return __longlong_as_double(__double_as_longlong(v) ^ ((long long)neg << 63));
@@ -71,12 +73,20 @@ __device__ __forceinline__ double flip_sign(double v, bool neg) {
 // of S into shared memory; then the warp walks the 32 rows, lanes spread over
 // the n (+1 for b) entries of each row, and adds +-A_ij/sqrt(zeta) into the
 // zeta target rows of Y with global reductions (Y is L2-resident).
-template <int N, typename TY>
+//
+// TEE: A and b live in host memory that the device reads in place (pinned or
+// registered); every entry read is also stored to the device copy (Aout with
+// row stride ldo, bout), so one pass over the host link both sketches and
+// moves the problem.  The lane loads its next four entries before it stores
+// or reduces any of them, which keeps enough reads in flight to cover the
+// link's latency.
+template <int N, typename TY, bool TEE = false>
 __global__ void __launch_bounds__(256) k_sketch_apply(const double* __restrict__ A, int64_t m, int n, int64_t lda,
                                                       const double* __restrict__ b, uint64_t d, int zeta,
                                                       uint64_t seed, int64_t row0, TY* __restrict__ Y, int64_t ldy,
                                                       double scale, uint32_t* status, int32_t* max_rounds,
-                                                      uint32_t* range, double* fro) {
+                                                      uint32_t* range, double* fro, double* __restrict__ Aout = nullptr,
+                                                      int64_t ldo = 0, double* __restrict__ bout = nullptr) {
   extern __shared__ int32_t s_idx[];  // [8 warps][32 rows][N]
   __shared__ uint64_t s_sgn[8][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -104,15 +114,46 @@ __global__ void __launch_bounds__(256) k_sketch_apply(const double* __restrict__
       const double* Ai = A + i * lda;
       const uint64_t sg = s_sgn[wib][rr];
       const int32_t* ci = my_idx + rr * N;
-      for (int j = lane; j < ncol; j += 32) {
-        const double a = j < n ? __ldcs(Ai + j) : b[i];
-        bad |= !isfinite(a);
-        track_exp(a, j < n ? ea : eb);
-        if (j < n) fa = fma(a, a, fa);
-        const double sa = a * scale;
-        for (int k = 0; k < zeta; ++k) {
-          const double v = flip_sign(sa, ((sg >> k) & 1ull) == 0ull);
-          red_add(Y + (int64_t)ci[k] * ldy + j, v);
+      if constexpr (TEE) {
+        double* Ao = Aout + i * ldo;
+        for (int j0 = lane; j0 < ncol; j0 += 128) {
+          double av[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = j0 + 32 * u;
+            av[u] = j < n ? Ai[j] : (j == n ? b[i] : 0.0);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = j0 + 32 * u;
+            if (j < ncol) {
+              const double a = av[u];
+              if (j < n)
+                __stcs(Ao + j, a);
+              else
+                __stcs(bout + i, a);
+              bad |= !isfinite(a);
+              track_exp(a, j < n ? ea : eb);
+              if (j < n) fa = fma(a, a, fa);
+              const double sa = a * scale;
+              for (int k = 0; k < zeta; ++k) {
+                const double v = flip_sign(sa, ((sg >> k) & 1ull) == 0ull);
+                red_add(Y + (int64_t)ci[k] * ldy + j, v);
+              }
+            }
+          }
+        }
+      } else {
+        for (int j = lane; j < ncol; j += 32) {
+          const double a = j < n ? __ldcs(Ai + j) : b[i];
+          bad |= !isfinite(a);
+          track_exp(a, j < n ? ea : eb);
+          if (j < n) fa = fma(a, a, fa);
+          const double sa = a * scale;
+          for (int k = 0; k < zeta; ++k) {
+            const double v = flip_sign(sa, ((sg >> k) & 1ull) == 0ull);
+            red_add(Y + (int64_t)ci[k] * ldy + j, v);
+          }
         }
       }
     }
@@ -129,25 +170,6 @@ __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, 
 
 __device__ __forceinline__ float flip_sign_f(float v, bool neg) { return __uint_as_float(__float_as_uint(v) ^ ((uint32_t)neg << 31)); }
 
-// Vector atomic add that returns the four old values.
-__device__ __forceinline__ float4 atom_add_v4(float* p, float a, float b, float c, float d) {
-  float4 o;
-  asm volatile("atom.global.add.v4.f32 {%0, %1, %2, %3}, [%4], {%5, %6, %7, %8};"
-               : "=f"(o.x), "=f"(o.y), "=f"(o.z), "=f"(o.w)
-               : "l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
-               : "memory");
-  return o;
-}
-
-// (old + v) - fl(old + v) exactly (Knuth's TwoSum): the rounding error of the
-// atomic add that turned `old` into fl(old + v), recomputed from its inputs.
-__device__ __forceinline__ float add_err(float old, float v) {
-  const float s = __fadd_rn(old, v);
-  const float bp = __fsub_rn(s, old);
-  const float ap = __fsub_rn(s, bp);
-  return __fadd_rn(__fsub_rn(old, ap), __fsub_rn(v, bp));
-}
-
 // FP64 entry -> nearest float using integer ops only (the FP64->FP32
 // conversion instruction runs at about one per clock per SM on this GPU).
 __device__ __forceinline__ float to_float_int(double a) {
@@ -156,40 +178,42 @@ __device__ __forceinline__ float to_float_int(double a) {
   return __fadd_rn(hi, mid);
 }
 
-// FP32 accumulation (mixed form) with 4-wide vector reductions: lane l owns
-// column groups 4(l + 32t) .. +3; entries past n are b_i (column n) or 0.
-// Requires ldy % 4 == 0 and Y (and Ylo) 16-byte aligned.
-//
-// COMP (compensated): every add into Y is a vector atomic that returns the
-// old values; the exact rounding error of each add (TwoSum of old and the
-// term) goes into Ylo with a vector reduction.  Y + Ylo then equals the exact
-// sum up to Ylo's own FP32 rounding, errors of size u^2 sqrt(N) relative for N
-// terms per entry, instead of u sqrt(N) for plain FP32 accumulation (with
-// about 5000 terms per entry at 5e6 rows and d = 8000, 1e-6 relative against
-// the 2.5e-8 of rounding an FP64 sketch once).  Atomics are issued eight
-// targets at a time so their round trips overlap.
-template <int N, bool COMP>
-__global__ void __launch_bounds__(256) k_sketch_apply_f32v(const double* __restrict__ A, int64_t m, int n, int64_t lda,
-                                                           const double* __restrict__ b, uint64_t d, int zeta,
-                                                           uint64_t seed, int64_t row0, float* __restrict__ Y,
-                                                           float* __restrict__ Ylo, int64_t ldy, float scale,
-                                                           uint32_t* status, int32_t* max_rounds, uint32_t* range,
-                                                           double* fro) {
+// Mixed-form sketch with blocked FP32 accumulation: every term is added in
+// FP32 (4-wide vector reductions into Yc; lane l owns column groups
+// 4(l + 32t) .. +3, entries past n are b_i (column n) or 0), but only
+// for one chunk of rows at a time; after each chunk the grid meets at a
+// barrier, adds Yc into the FP64 sketch Y and clears Yc.  A chunk is R rows
+// per warp of the grid, sized so that each entry of Yc receives about
+// kFoldTerms terms (R = kFoldTerms d / (zeta warps), clamped to [1, 32]):
+// FP32 rounding then grows with sqrt(kFoldTerms) instead of sqrt(zeta m / d)
+// (about 5000 terms at 5e6 rows, d = 8000), and the chunk sums are combined
+// in FP64.  Yc (ldc % 4 == 0, 16-byte aligned) and Y must be zero on entry;
+// Yc is zero again on exit.  Cooperative launch (grid barriers).
+template <int N>
+__global__ void __launch_bounds__(256) k_sketch_fold(const double* __restrict__ A, int64_t m, int n, int64_t lda,
+                                                     const double* __restrict__ b, uint64_t d, int zeta,
+                                                     uint64_t seed, int R, float* __restrict__ Yc, int64_t ldc,
+                                                     double* __restrict__ Y, int64_t ldy, float scale,
+                                                     uint32_t* status, int32_t* max_rounds, uint32_t* range,
+                                                     double* fro, GridBarrier* bar) {
   extern __shared__ int32_t s_idx[];  // [8 warps][32 rows][N]
   __shared__ uint64_t s_sgn[8][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   int32_t* my_idx = s_idx + wib * 32 * N;
   const int ncol = n + (b ? 1 : 0);
   const int ngroups = (ncol + 3) / 4;
+  const int64_t nw = (int64_t)gridDim.x * 8, gw = (int64_t)blockIdx.x * 8 + wib;
+  const int64_t chunk = nw * R;
   bool bad = false;
   uint32_t ea = 0, eb = 0;
   double fa = 0.0;
-  for (int64_t base = ((int64_t)blockIdx.x * 8 + wib) * 32; base < m; base += (int64_t)gridDim.x * 8 * 32) {
-    const int64_t row = base + lane;
-    if (row < m) {
+  for (int64_t c0 = 0; c0 < m; c0 += chunk) {
+    const int64_t base = c0 + gw * R;
+    const int nrows = (int)max((int64_t)0, min((int64_t)R, m - base));
+    if (lane < nrows) {
       int32_t c[N];
       uint64_t signs;
-      const int r = sketch_column<N>(seed, (uint64_t)(row0 + row), d, zeta, c, signs);
+      const int r = sketch_column<N>(seed, (uint64_t)(base + lane), d, zeta, c, signs);
       if (r < 0) atomicOr(status, DS_SKETCH);
       if (r > 0) atomicMax(max_rounds, r);
 #pragma unroll
@@ -197,7 +221,6 @@ __global__ void __launch_bounds__(256) k_sketch_apply_f32v(const double* __restr
       s_sgn[wib][lane] = signs;
     }
     __syncwarp();
-    const int nrows = (int)min((int64_t)32, m - base);
     for (int rr = 0; rr < nrows; ++rr) {
       const int64_t i = base + rr;
       const double* Ai = A + i * lda;
@@ -214,43 +237,56 @@ __global__ void __launch_bounds__(256) k_sketch_apply_f32v(const double* __restr
           if (j < n) fa = fma(a, a, fa);
           v[q] = __fmul_rn(to_float_int(a), scale);
         }
-        if (COMP) {
-          for (int k0 = 0; k0 < zeta; k0 += 8) {
-            float4 o[8];
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-              const int k = k0 + kk;
-              if (k < zeta) {
-                const bool neg = ((sg >> k) & 1ull) == 0ull;
-                o[kk] = atom_add_v4(Y + (int64_t)ci[k] * ldy + 4 * g, flip_sign_f(v[0], neg), flip_sign_f(v[1], neg),
-                                    flip_sign_f(v[2], neg), flip_sign_f(v[3], neg));
-              }
-            }
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-              const int k = k0 + kk;
-              if (k < zeta) {
-                const bool neg = ((sg >> k) & 1ull) == 0ull;
-                red_add_v4(Ylo + (int64_t)ci[k] * ldy + 4 * g, add_err(o[kk].x, flip_sign_f(v[0], neg)),
-                           add_err(o[kk].y, flip_sign_f(v[1], neg)), add_err(o[kk].z, flip_sign_f(v[2], neg)),
-                           add_err(o[kk].w, flip_sign_f(v[3], neg)));
-              }
-            }
-          }
-        } else {
-          for (int k = 0; k < zeta; ++k) {
-            const bool neg = ((sg >> k) & 1ull) == 0ull;
-            red_add_v4(Y + (int64_t)ci[k] * ldy + 4 * g, flip_sign_f(v[0], neg), flip_sign_f(v[1], neg),
-                       flip_sign_f(v[2], neg), flip_sign_f(v[3], neg));
-          }
+        for (int k = 0; k < zeta; ++k) {
+          const bool neg = ((sg >> k) & 1ull) == 0ull;
+          red_add_v4(Yc + (int64_t)ci[k] * ldc + 4 * g, flip_sign_f(v[0], neg), flip_sign_f(v[1], neg),
+                     flip_sign_f(v[2], neg), flip_sign_f(v[3], neg));
         }
       }
     }
     __syncwarp();
+    if (!grid_sync(bar, status, gridDim.x)) break;  // every reduction of the chunk has landed
+    // the chunk's FP32 sums into the FP64 sketch; Yc cleared for the next chunk
+    for (int64_t r = blockIdx.x; r < (int64_t)d; r += gridDim.x) {
+      float* yc = Yc + r * ldc;
+      double* y = Y + r * ldy;
+      for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+        __stcg(y + c, __ldcg(y + c) + (double)__ldcg(yc + c));
+        __stcg(yc + c, 0.f);
+      }
+    }
+    if (!grid_sync(bar, status, gridDim.x)) break;  // Yc is clear before the next chunk's reductions
   }
   if (bad) atomicOr(status, DS_NONFINITE);
   flush_range(ea, eb, range);
   flush_fro(fa, fro);
+}
+
+template <int N>
+cudaError_t launch_fold(const double* A, int64_t m, int n, int64_t lda, const double* b, int64_t d, int zeta,
+                        uint64_t seed, float* Yc, int64_t ldc, double* Y, int64_t ldy, uint32_t* status,
+                        int32_t* max_rounds, uint32_t* range, double* fro, GridBarrier* bar, int sms,
+                        cudaStream_t st) {
+  const size_t smem = (size_t)8 * 32 * N * sizeof(int32_t);
+  cudaError_t e = cudaFuncSetAttribute(k_sketch_fold<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sketch_fold<N>, 256, smem)) != cudaSuccess)
+    return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int grid = per_sm * sms;
+  const int64_t nw = (int64_t)grid * 8;
+  const double rr = (double)kFoldTerms * (double)d / ((double)zeta * (double)nw);
+  int R = (int)(rr + 0.5);
+  R = R < 1 ? 1 : (R > 32 ? 32 : R);
+  float scale = (float)(1.0 / sqrt((double)zeta));
+  if ((e = cudaMemsetAsync(&bar->count, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
+  uint64_t dd = (uint64_t)d;
+  int64_t mm = m, la = lda, lc = ldc, ly = ldy;
+  int nn = n, z = zeta;
+  void* args[] = {&A, &mm, &nn, &la, &b, &dd, &z, &seed, &R, &Yc, &lc, &Y, &ly, &scale, &status, &max_rounds,
+                  &range, &fro, &bar};
+  return cudaLaunchCooperativeKernel((const void*)k_sketch_fold<N>, grid, 256, args, smem, st);
 }
 
 // range_scan: one warp per row (grid-stride), lanes over the columns and b_i.
@@ -276,33 +312,11 @@ __global__ void __launch_bounds__(256) k_range_scan(const double* __restrict__ A
   flush_range(ea, eb, range);
 }
 
-template <int N>
-cudaError_t launch_apply_f32v(const double* A, int64_t m, int n, int64_t lda, const double* b, int64_t d, int zeta,
-                              uint64_t seed, int64_t row0, float* Y, float* Ylo, int64_t ldy, uint32_t* status,
-                              int32_t* max_rounds, uint32_t* range, double* fro, int sms, cudaStream_t st) {
-  const size_t smem = (size_t)8 * 32 * N * sizeof(int32_t);
-  const void* fn = Ylo ? (const void*)k_sketch_apply_f32v<N, true> : (const void*)k_sketch_apply_f32v<N, false>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const int64_t groups = (m + 255) / 256;
-  const int64_t blocks = std::min<int64_t>(groups, (int64_t)sms * 8);
-  const float scale = (float)(1.0 / sqrt((double)zeta));
-  if (blocks > 0) {
-    if (Ylo)
-      k_sketch_apply_f32v<N, true><<<(unsigned)blocks, 256, smem, st>>>(A, m, n, lda, b, (uint64_t)d, zeta, seed,
-                                                                        row0, Y, Ylo, ldy, scale, status, max_rounds,
-                                                                        range, fro);
-    else
-      k_sketch_apply_f32v<N, false><<<(unsigned)blocks, 256, smem, st>>>(A, m, n, lda, b, (uint64_t)d, zeta, seed,
-                                                                         row0, Y, nullptr, ldy, scale, status,
-                                                                         max_rounds, range, fro);
-  }
-  return cudaGetLastError();
-}
-
-__global__ void k_add_lo(float* __restrict__ Y, const float* __restrict__ Ylo, int64_t count) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
-    Y[e] = __fadd_rn(Y[e], Ylo[e]);
+// Y (FP64, row stride ldy) rounded to FP32 into out (row stride ldo).
+__global__ void k_round_to_float(const double* __restrict__ Y, int64_t ldy, float* __restrict__ out, int64_t ldo,
+                                 int64_t d, int ncol) {
+  for (int64_t r = blockIdx.x; r < d; r += gridDim.x)
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) out[r * ldo + c] = __double2float_rn(Y[r * ldy + c]);
 }
 
 template <int N>
@@ -331,7 +345,44 @@ cudaError_t launch_apply(const double* A, int64_t m, int n, int64_t lda, const d
   return cudaGetLastError();
 }
 
+template <int N>
+cudaError_t launch_apply_tee(const double* A, int64_t m, int n, int64_t lda, const double* b, int64_t d, int zeta,
+                             uint64_t seed, double* Y, int64_t ldy, double* Aout, int64_t ldo, double* bout,
+                             uint32_t* status, int32_t* max_rounds, uint32_t* range, double* fro, int sms,
+                             cudaStream_t st) {
+  const size_t smem = (size_t)8 * 32 * N * sizeof(int32_t);
+  cudaError_t e = cudaFuncSetAttribute(k_sketch_apply<N, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t groups = (m + 255) / 256;
+  const int64_t blocks = std::min<int64_t>(groups, (int64_t)sms * 8);
+  if (blocks > 0)
+    k_sketch_apply<N, double, true><<<(unsigned)blocks, 256, smem, st>>>(
+        A, m, n, lda, b, (uint64_t)d, zeta, seed, 0, Y, ldy, 1.0 / sqrt((double)zeta), status, max_rounds, range, fro,
+        Aout, ldo, bout);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t sketch_apply_tee(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d,
+                             int zeta, uint64_t seed, double* Y, int64_t ldy, double* Aout, int64_t ldo, double* bout,
+                             uint32_t* status, int32_t* max_rounds, uint32_t* range, double* fro, int sms,
+                             cudaStream_t st) {
+  const int ni = (int)n;
+  if (!b || !bout) return cudaErrorInvalidValue;
+  if (zeta <= 8)
+    return launch_apply_tee<8>(A, m, ni, lda, b, d, zeta, seed, Y, ldy, Aout, ldo, bout, status, max_rounds, range,
+                               fro, sms, st);
+  if (zeta <= 16)
+    return launch_apply_tee<16>(A, m, ni, lda, b, d, zeta, seed, Y, ldy, Aout, ldo, bout, status, max_rounds, range,
+                                fro, sms, st);
+  if (zeta <= 32)
+    return launch_apply_tee<32>(A, m, ni, lda, b, d, zeta, seed, Y, ldy, Aout, ldo, bout, status, max_rounds, range,
+                                fro, sms, st);
+  return launch_apply_tee<64>(A, m, ni, lda, b, d, zeta, seed, Y, ldy, Aout, ldo, bout, status, max_rounds, range,
+                              fro, sms, st);
+}
 
 cudaError_t sketch_indices(uint64_t seed, int64_t row0, int64_t rows, int64_t d, int zeta, int32_t* idx, int8_t* sgn,
                            int32_t* rounds, uint32_t* status, int32_t* max_rounds, int sms, cudaStream_t st) {
@@ -346,9 +397,6 @@ cudaError_t sketch_apply(const double* A, int64_t m, int64_t n, int64_t lda, con
                          uint64_t seed, int64_t row0, TY* Y, int64_t ldy, uint32_t* status, int32_t* max_rounds,
                          uint32_t* range, double* fro, int sms, cudaStream_t st) {
   const int ni = (int)n;
-  if (sizeof(TY) == 4 && ldy % 4 == 0 && (uintptr_t)Y % 16 == 0)
-    return sketch_apply_f32c(A, m, n, lda, b, d, zeta, seed, row0, reinterpret_cast<float*>(Y), nullptr, ldy, status,
-                             max_rounds, range, fro, sms, st);
   if (zeta <= 8)
     return launch_apply<8, TY>(A, m, ni, lda, b, d, zeta, seed, row0, Y, ldy, status, max_rounds, range, fro, sms,
                                st);
@@ -362,26 +410,29 @@ cudaError_t sketch_apply(const double* A, int64_t m, int64_t n, int64_t lda, con
                                st);
 }
 
-cudaError_t sketch_apply_f32c(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d,
-                              int zeta, uint64_t seed, int64_t row0, float* Y, float* Ylo, int64_t ldy,
-                              uint32_t* status, int32_t* max_rounds, uint32_t* range, double* fro, int sms,
-                              cudaStream_t st) {
+cudaError_t sketch_apply_fold(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d,
+                              int zeta, uint64_t seed, float* Yc, int64_t ldc, double* Y, int64_t ldy,
+                              uint32_t* status, int32_t* max_rounds, uint32_t* range, double* fro, GridBarrier* bar,
+                              int sms, cudaStream_t st) {
   const int ni = (int)n;
-  if (ldy % 4 != 0 || (uintptr_t)Y % 16 != 0 || (uintptr_t)Ylo % 16 != 0) return cudaErrorInvalidValue;
+  if (ldc % 4 != 0 || (uintptr_t)Yc % 16 != 0) return cudaErrorInvalidValue;
   if (zeta <= 8)
-    return launch_apply_f32v<8>(A, m, ni, lda, b, d, zeta, seed, row0, Y, Ylo, ldy, status, max_rounds, range, fro, sms, st);
+    return launch_fold<8>(A, m, ni, lda, b, d, zeta, seed, Yc, ldc, Y, ldy, status, max_rounds, range, fro, bar, sms,
+                          st);
   if (zeta <= 16)
-    return launch_apply_f32v<16>(A, m, ni, lda, b, d, zeta, seed, row0, Y, Ylo, ldy, status, max_rounds, range, fro, sms,
-                                 st);
+    return launch_fold<16>(A, m, ni, lda, b, d, zeta, seed, Yc, ldc, Y, ldy, status, max_rounds, range, fro, bar,
+                           sms, st);
   if (zeta <= 32)
-    return launch_apply_f32v<32>(A, m, ni, lda, b, d, zeta, seed, row0, Y, Ylo, ldy, status, max_rounds, range, fro, sms,
-                                 st);
-  return launch_apply_f32v<64>(A, m, ni, lda, b, d, zeta, seed, row0, Y, Ylo, ldy, status, max_rounds, range, fro, sms, st);
+    return launch_fold<32>(A, m, ni, lda, b, d, zeta, seed, Yc, ldc, Y, ldy, status, max_rounds, range, fro, bar,
+                           sms, st);
+  return launch_fold<64>(A, m, ni, lda, b, d, zeta, seed, Yc, ldc, Y, ldy, status, max_rounds, range, fro, bar, sms,
+                         st);
 }
 
-cudaError_t add_lo(float* Y, const float* Ylo, int64_t count, int sms, cudaStream_t st) {
-  const int64_t blocks = std::min<int64_t>((count + 255) / 256, (int64_t)sms * 8);
-  if (blocks > 0) k_add_lo<<<(unsigned)blocks, 256, 0, st>>>(Y, Ylo, count);
+cudaError_t round_to_float(const double* Y, int64_t ldy, float* out, int64_t ldo, int64_t d, int64_t ncol, int sms,
+                           cudaStream_t st) {
+  const int64_t blocks = std::min<int64_t>(d, (int64_t)sms * 8);
+  if (blocks > 0) k_round_to_float<<<(unsigned)blocks, 256, 0, st>>>(Y, ldy, out, ldo, d, (int)ncol);
   return cudaGetLastError();
 }
 
@@ -395,8 +446,6 @@ cudaError_t range_scan(const double* A, int64_t m, int64_t n, int64_t lda, const
 template cudaError_t sketch_apply<double>(const double*, int64_t, int64_t, int64_t, const double*, int64_t, int,
                                           uint64_t, int64_t, double*, int64_t, uint32_t*, int32_t*, uint32_t*, double*,
                                           int, cudaStream_t);
-template cudaError_t sketch_apply<float>(const double*, int64_t, int64_t, int64_t, const double*, int64_t, int,
-                                         uint64_t, int64_t, float*, int64_t, uint32_t*, int32_t*, uint32_t*, double*,
-                                         int, cudaStream_t);
+
 
 }  // namespace lsq
