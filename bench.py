@@ -577,17 +577,15 @@ def _mem_available_bytes():
 
 
 def launches_per_solve(n, d, prec, blocked):
-    """Kernels of this library one lsq_solve launches: sketch, column-major
-    copy, QR (unblocked: 1 kernel; blocked, per 64-column panel: the panel
-    kernel, four slicing kernels, three tensor-core GEMMs and T; the last
-    panel only the panel kernel), R extraction, inverse, transpose, x0, M^T
-    copy, LSQR (+ the accuracy pass, same kernel)."""
-    if not blocked:
-        qr = 1
-    else:
-        panels = (n + 63) // 64
-        qr = (panels - 1) * 9 + 1
-    return 1 + 1 + qr + 4 + 1 + 1
+    """Kernels of this library one lsq_solve launches: sketch (the mixed form
+    adds the pair-to-FP64 pass), column-major copy, QR (unblocked: 1 kernel;
+    blocked, per 64-column panel of the n columns: the panel kernel, four
+    slicing kernels, three tensor-core GEMMs and T -- the b column always
+    leaves a trailing update), R extraction, inverse, transpose, x0, and the
+    LSQR kernel (with the accuracy pass).  Checked against the ncu launch list
+    of the default bench line (295 per plain solve at 5e6 x 2000)."""
+    qr = 9 * ((n + 63) // 64) if blocked else 1
+    return 1 + (1 if prec == 1 else 0) + 1 + qr + 4 + 1
 
 
 def run_headline(args):

@@ -70,7 +70,9 @@ typedef enum {
                          16 terms per entry per chunk), the chunk sums combined in FP64;
                          lsq_solve factors that sketch in FP64 (tensor-core trailing updates
                          with FP32 accumulation, as the plain form), lsq_precond with FP32 Y
-                         factors in FP32 */
+                         factors in FP32.  The solve's ||A||_F (info->anorm_fro, the
+                         backward-error bounds' scale) is then summed from the FP32 values
+                         of A's entries: relative error about 1e-7 */
 } lsq_prec;
 
 typedef enum { LSQ_MEM_DEVICE = 0, LSQ_MEM_HOST = 1 } lsq_mem;

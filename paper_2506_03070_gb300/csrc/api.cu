@@ -542,18 +542,18 @@ lsq_status lsq_sketch(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64
     CK(sketch_apply<double>(A, m, n, lda, b, d, zeta, seed, 0, (double*)Y, ldy, ctx->d_status, ctx->d_max_rounds,
                             nullptr, nullptr, ctx->sms, st));
   } else {
-    // blocked FP32 accumulation (chunk sums in FP32, folded into an FP64
-    // sketch in workspace), rounded once into the FP32 output
+    // blocked FP32 accumulation (chunk sums in FP32, folded into float
+    // pairs in workspace), rounded once into the FP32 output
     const int64_t ncol = n + (b ? 1 : 0), ldc = (ncol + 3) / 4 * 4;
     const size_t y64 = align_up((size_t)d * ncol * sizeof(double));
     if ((s = ensure_ws(ctx, y64 + align_up((size_t)d * ldc * sizeof(float)))) != LSQ_OK) return s;
-    double* Y64 = reinterpret_cast<double*>(ctx->ws);
+    float2* Yp = reinterpret_cast<float2*>(ctx->ws);
     float* Yc = reinterpret_cast<float*>(static_cast<char*>(ctx->ws) + y64);
-    CK(cudaMemsetAsync(Y64, 0, (size_t)d * ncol * sizeof(double), st));
+    CK(cudaMemsetAsync(Yp, 0, (size_t)d * ncol * sizeof(float2), st));
     CK(cudaMemsetAsync(Yc, 0, (size_t)d * ldc * sizeof(float), st));
-    CK(sketch_apply_fold(A, m, n, lda, b, d, zeta, seed, Yc, ldc, Y64, ncol, ctx->d_status, ctx->d_max_rounds,
+    CK(sketch_apply_fold(A, m, n, lda, b, d, zeta, seed, Yc, ldc, Yp, ncol, ctx->d_status, ctx->d_max_rounds,
                          nullptr, nullptr, ctx->d_bar, ctx->sms, st));
-    CK(round_to_float(Y64, ncol, static_cast<float*>(Y), ldy, d, ncol, ctx->sms, st));
+    CK(round_to_float(Yp, ncol, static_cast<float*>(Y), ldy, d, ncol, ctx->sms, st));
   }
   uint32_t bits = 0;
   if ((s = read_small(ctx, st, &bits, nullptr, nullptr)) != LSQ_OK) return s;
@@ -861,10 +861,12 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
     CK(sketch_apply<double>(A, m, n, lda_dev, b, d, o->zeta, o->seed, 0, (double*)Y, ldy, ctx->d_status,
                             ctx->d_max_rounds, ctx->d_range, ctx->d_fro, ctx->sms, st));
   } else {
-    // blocked FP32 accumulation: chunk sums in Yc, folded into the FP64 Y
+    // blocked FP32 accumulation: chunk sums in Yc, folded into float pairs in
+    // Y's memory, then turned into the FP64 sketch in place
     CK(cudaMemsetAsync(Yc, 0, (size_t)d * ldc * sizeof(float), st));
-    CK(sketch_apply_fold(A, m, n, lda_dev, b, d, o->zeta, o->seed, Yc, ldc, (double*)Y, ldy, ctx->d_status,
+    CK(sketch_apply_fold(A, m, n, lda_dev, b, d, o->zeta, o->seed, Yc, ldc, (float2*)Y, ldy, ctx->d_status,
                          ctx->d_max_rounds, ctx->d_range, ctx->d_fro, ctx->d_bar, ctx->sms, st));
+    CK(pairs_to_double((float2*)Y, d * ldy, ctx->sms, st));
   }
   if (timing) CK(cudaEventRecord(ev[2], st));
   // both forms factor the FP64 sketch (the tensor-core trailing updates

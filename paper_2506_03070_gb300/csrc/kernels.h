@@ -19,15 +19,19 @@ template <typename TY>  // double
 cudaError_t sketch_apply(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d, int zeta,
                          uint64_t seed, int64_t row0, TY* Y, int64_t ldy, uint32_t* status, int32_t* max_rounds,
                          uint32_t* range, double* fro, int sms, cudaStream_t st);
-// out (d x ncol floats, row stride ldo) = Y (FP64, row stride ldy) rounded to nearest.
-cudaError_t round_to_float(const double* Y, int64_t ldy, float* out, int64_t ldo, int64_t d, int64_t ncol, int sms,
+// out (d x ncol floats, row stride ldo) = the float pairs Y (row stride ldy),
+// each pair's sum rounded once to FP32.
+cudaError_t round_to_float(const float2* Y, int64_t ldy, float* out, int64_t ldo, int64_t d, int64_t ncol, int sms,
                            cudaStream_t st);
+// In place: each of the count float pairs becomes the double hi + lo.
+cudaError_t pairs_to_double(float2* Y, int64_t count, int sms, cudaStream_t st);
 // The mixed form's sketch with blocked FP32 accumulation: terms are added in
 // FP32 into Yc (d x ldc floats, ldc % 4 == 0, zero on entry and on exit) one
-// chunk of rows at a time, each chunk's sums then added into the FP64 sketch
-// Y (d x ldy, zero on entry).  Cooperative launch; bar's counter is reset.
+// chunk of rows at a time, each chunk's sums then added into the float-pair
+// sketch Y (d x ldy pairs, zero on entry; pairs_to_double or round_to_float
+// finish it).  Cooperative launch; bar's counter is reset.
 cudaError_t sketch_apply_fold(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d,
-                              int zeta, uint64_t seed, float* Yc, int64_t ldc, double* Y, int64_t ldy,
+                              int zeta, uint64_t seed, float* Yc, int64_t ldc, float2* Y, int64_t ldy,
                               uint32_t* status, int32_t* max_rounds, uint32_t* range, double* fro, GridBarrier* bar,
                               int sms, cudaStream_t st);
 // The FP64 sketch of a problem in host memory the device reads in place

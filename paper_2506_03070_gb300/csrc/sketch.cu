@@ -182,18 +182,22 @@ __device__ __forceinline__ float to_float_int(double a) {
 // FP32 (4-wide vector reductions into Yc; lane l owns column groups
 // 4(l + 32t) .. +3, entries past n are b_i (column n) or 0), but only
 // for one chunk of rows at a time; after each chunk the grid meets at a
-// barrier, adds Yc into the FP64 sketch Y and clears Yc.  A chunk is R rows
+// barrier, adds Yc into the running sketch Yp and clears Yc.  A chunk is R rows
 // per warp of the grid, sized so that each entry of Yc receives about
 // kFoldTerms terms (R = kFoldTerms d / (zeta warps), clamped to [1, 32]):
 // FP32 rounding then grows with sqrt(kFoldTerms) instead of sqrt(zeta m / d)
-// (about 5000 terms at 5e6 rows, d = 8000), and the chunk sums are combined
-// in FP64.  Yc (ldc % 4 == 0, 16-byte aligned) and Y must be zero on entry;
-// Yc is zero again on exit.  Cooperative launch (grid barriers).
+// (about 5000 terms at 5e6 rows, d = 8000).  The chunk sums are combined as
+// unevaluated float pairs (hi, lo) by TwoSum, ~48 significant bits, on the
+// FP32 pipe (an FP64 add per entry per chunk would tie up GB300's FP64 pipe);
+// pairs_to_double / round_to_float turn Yp into the sketch.  ||A||_F^2 is
+// summed the same way from the FP32 values of the entries (relative error
+// about 2^-22).  Yc (ldc % 4 == 0, 16-byte aligned) and Yp must be zero on
+// entry; Yc is zero again on exit.  Cooperative launch (grid barriers).
 template <int N>
 __global__ void __launch_bounds__(256) k_sketch_fold(const double* __restrict__ A, int64_t m, int n, int64_t lda,
                                                      const double* __restrict__ b, uint64_t d, int zeta,
                                                      uint64_t seed, int R, float* __restrict__ Yc, int64_t ldc,
-                                                     double* __restrict__ Y, int64_t ldy, float scale,
+                                                     float2* __restrict__ Yp, int64_t ldy, float scale,
                                                      uint32_t* status, int32_t* max_rounds, uint32_t* range,
                                                      double* fro, GridBarrier* bar) {
   extern __shared__ int32_t s_idx[];  // [8 warps][32 rows][N]
@@ -206,7 +210,7 @@ __global__ void __launch_bounds__(256) k_sketch_fold(const double* __restrict__ 
   const int64_t chunk = nw * R;
   bool bad = false;
   uint32_t ea = 0, eb = 0;
-  double fa = 0.0;
+  float fh = 0.f, fl = 0.f;  // sum of A_ij^2 as a float pair
   for (int64_t c0 = 0; c0 < m; c0 += chunk) {
     const int64_t base = c0 + gw * R;
     const int nrows = (int)max((int64_t)0, min((int64_t)R, m - base));
@@ -227,15 +231,22 @@ __global__ void __launch_bounds__(256) k_sketch_fold(const double* __restrict__ 
       const uint64_t sg = s_sgn[wib][rr];
       const int32_t* ci = my_idx + rr * N;
       for (int g = lane; g < ngroups; g += 32) {
-        float v[4];
+        float v[4], sq = 0.f;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int j = 4 * g + q;
           const double a = j < n ? __ldcs(Ai + j) : (j == n && b ? b[i] : 0.0);
           bad |= !isfinite(a);
           track_exp(a, j < n ? ea : eb);
-          if (j < n) fa = fma(a, a, fa);
-          v[q] = __fmul_rn(to_float_int(a), scale);
+          const float a32 = to_float_int(a);
+          if (j < n) sq = __fmaf_rn(a32, a32, sq);
+          v[q] = __fmul_rn(a32, scale);
+        }
+        {
+          float t, e;
+          two_sum(fh, sq, t, e);
+          fh = t;
+          fl = __fadd_rn(fl, e);
         }
         for (int k = 0; k < zeta; ++k) {
           const bool neg = ((sg >> k) & 1ull) == 0ull;
@@ -246,12 +257,15 @@ __global__ void __launch_bounds__(256) k_sketch_fold(const double* __restrict__ 
     }
     __syncwarp();
     if (!grid_sync(bar, status, gridDim.x)) break;  // every reduction of the chunk has landed
-    // the chunk's FP32 sums into the FP64 sketch; Yc cleared for the next chunk
+    // the chunk's FP32 sums into the running pairs; Yc cleared for the next chunk
     for (int64_t r = blockIdx.x; r < (int64_t)d; r += gridDim.x) {
       float* yc = Yc + r * ldc;
-      double* y = Y + r * ldy;
+      float2* y = Yp + r * ldy;
       for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
-        __stcg(y + c, __ldcg(y + c) + (double)__ldcg(yc + c));
+        const float2 p = __ldcg(y + c);
+        float t, e;
+        two_sum(p.x, __ldcg(yc + c), t, e);
+        __stcg(y + c, make_float2(t, __fadd_rn(p.y, e)));
         __stcg(yc + c, 0.f);
       }
     }
@@ -259,12 +273,21 @@ __global__ void __launch_bounds__(256) k_sketch_fold(const double* __restrict__ 
   }
   if (bad) atomicOr(status, DS_NONFINITE);
   flush_range(ea, eb, range);
-  flush_fro(fa, fro);
+  flush_fro((double)fh + (double)fl, fro);
+}
+
+// In place: the float pair (hi, lo) of each entry becomes the double hi + lo.
+__global__ void k_pairs_to_double(float2* __restrict__ Yp, int64_t count) {
+  double* Y = reinterpret_cast<double*>(Yp);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    const float2 p = Yp[e];
+    Y[e] = (double)p.x + (double)p.y;
+  }
 }
 
 template <int N>
 cudaError_t launch_fold(const double* A, int64_t m, int n, int64_t lda, const double* b, int64_t d, int zeta,
-                        uint64_t seed, float* Yc, int64_t ldc, double* Y, int64_t ldy, uint32_t* status,
+                        uint64_t seed, float* Yc, int64_t ldc, float2* Y, int64_t ldy, uint32_t* status,
                         int32_t* max_rounds, uint32_t* range, double* fro, GridBarrier* bar, int sms,
                         cudaStream_t st) {
   const size_t smem = (size_t)8 * 32 * N * sizeof(int32_t);
@@ -312,11 +335,15 @@ __global__ void __launch_bounds__(256) k_range_scan(const double* __restrict__ A
   flush_range(ea, eb, range);
 }
 
-// Y (FP64, row stride ldy) rounded to FP32 into out (row stride ldo).
-__global__ void k_round_to_float(const double* __restrict__ Y, int64_t ldy, float* __restrict__ out, int64_t ldo,
+// The pairs Yp (row stride ldy) rounded to FP32 into out (row stride ldo):
+// fl32(hi + lo), one rounding of the pair's exact sum.
+__global__ void k_round_to_float(const float2* __restrict__ Yp, int64_t ldy, float* __restrict__ out, int64_t ldo,
                                  int64_t d, int ncol) {
   for (int64_t r = blockIdx.x; r < d; r += gridDim.x)
-    for (int c = threadIdx.x; c < ncol; c += blockDim.x) out[r * ldo + c] = __double2float_rn(Y[r * ldy + c]);
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+      const float2 p = Yp[r * ldy + c];
+      out[r * ldo + c] = __fadd_rn(p.x, p.y);
+    }
 }
 
 template <int N>
@@ -411,7 +438,7 @@ cudaError_t sketch_apply(const double* A, int64_t m, int64_t n, int64_t lda, con
 }
 
 cudaError_t sketch_apply_fold(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d,
-                              int zeta, uint64_t seed, float* Yc, int64_t ldc, double* Y, int64_t ldy,
+                              int zeta, uint64_t seed, float* Yc, int64_t ldc, float2* Y, int64_t ldy,
                               uint32_t* status, int32_t* max_rounds, uint32_t* range, double* fro, GridBarrier* bar,
                               int sms, cudaStream_t st) {
   const int ni = (int)n;
@@ -429,10 +456,16 @@ cudaError_t sketch_apply_fold(const double* A, int64_t m, int64_t n, int64_t lda
                          st);
 }
 
-cudaError_t round_to_float(const double* Y, int64_t ldy, float* out, int64_t ldo, int64_t d, int64_t ncol, int sms,
+cudaError_t round_to_float(const float2* Y, int64_t ldy, float* out, int64_t ldo, int64_t d, int64_t ncol, int sms,
                            cudaStream_t st) {
   const int64_t blocks = std::min<int64_t>(d, (int64_t)sms * 8);
   if (blocks > 0) k_round_to_float<<<(unsigned)blocks, 256, 0, st>>>(Y, ldy, out, ldo, d, (int)ncol);
+  return cudaGetLastError();
+}
+
+cudaError_t pairs_to_double(float2* Y, int64_t count, int sms, cudaStream_t st) {
+  const int64_t blocks = std::min<int64_t>((count + 255) / 256, (int64_t)sms * 8);
+  if (blocks > 0) k_pairs_to_double<<<(unsigned)blocks, 256, 0, st>>>(Y, count);
   return cudaGetLastError();
 }
 

@@ -12,8 +12,12 @@
 // of magnitude <= 2^14, so the products of slice pairs (q, t) with q + t = p,
 // summed over a K chunk of 128, stay below 7 * 128 * 2^14 < 2^24: the FP32
 // accumulation in TMEM is exact whatever its order.  Group p of a chunk is
-// read back (tcgen05.ld), scaled by 2^(-14-8p) and added in FP64; after the
-// last chunk the row and column exponents 2^(e_a + e_b) are applied.  Pairs
+// read back (tcgen05.ld) and added, as the integer it is, into two 64-bit
+// integer sums per output (the last min(S, 4) groups into one, the others into
+// the second, each group shifted to its weight 2^(-8p)): the whole K
+// accumulates exactly, and FP64 arithmetic is needed only once per output at
+// the end, where the sums are scaled and the row and column exponents
+// 2^(e_a + e_b) applied.  Pairs
 // with q + t >= S are dropped: for S = 7 (FP64 data, 56 bits per row) the
 // result carries an error of about K 2^-53 max|a_row| max|b_row|, that of an
 // FP64 GEMM's normwise bound; S = 4 (FP32 data) gives FP32's for entries down
@@ -41,7 +45,7 @@ constexpr int kTN = 64;    // output columns per tile
 constexpr int kKS = 32;    // K per pipeline stage: one 64-byte swizzle row of bf16
 constexpr int kKC = 128;   // K per exact FP32 accumulation chunk
 constexpr int kStages = 2;
-constexpr int kThreadsG = 128;
+constexpr int kThreadsG = 256;  // 8 warps: warps w and w + 4 read TMEM lanes 32 (w % 4) .. +31, halves of the columns
 
 template <int S>
 __host__ __device__ constexpr int stage_bytes() {
@@ -126,6 +130,19 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// The integer value of an FP32 accumulator that holds an exact integer of
+// magnitude below 2^24 (a group sum of one chunk), from its IEEE fields:
+// mantissa with the hidden bit, shifted right by 150 - exponent (zero gives
+// exponent 0 and a shift of 31, hence 0).
+__device__ __forceinline__ int32_t exact_int(float g) {
+  const uint32_t b = __float_as_uint(g);
+  const uint32_t e = (b >> 23) & 0xFFu;
+  const uint32_t mant = (b & 0x7FFFFFu) | 0x800000u;
+  const uint32_t sh = min(150u - e, 31u);
+  const int32_t mag = (int32_t)(mant >> sh);
+  return (b >> 31) ? -mag : mag;
+}
+
 struct OzParams {
   int M, N, K;        // A rows, B rows, shared dimension
   int k_split;        // K per CTA (multiple of kKC); grid.z = ceil(K / k_split)
@@ -194,9 +211,15 @@ __global__ void __launch_bounds__(kThreadsG, 1)
     for (int t = 0; t < S; ++t) tma_load_3d(b_tile(st, t), &tma_b, k, n0, t, &bar_full[st]);
   };
 
-  double acc[kTN];
+  // exact integer sums of the groups (see the file header), this thread's
+  // row and column half: lo over the last L groups, hi over the first S - L
+  constexpr int L = S < 4 ? S : 4, H = S - L, kHalf = kTN / 2;
+  int64_t acc_lo[kHalf], acc_hi[H > 0 ? kHalf : 1];
 #pragma unroll
-  for (int c = 0; c < kTN; ++c) acc[c] = 0.0;
+  for (int c = 0; c < kHalf; ++c) acc_lo[c] = 0;
+#pragma unroll
+  for (int c = 0; c < (H > 0 ? kHalf : 1); ++c) acc_hi[c] = 0;
+  const int col_half = (warp >> 2) * kHalf;
 
   // thread 0's pipeline state: stages issued to TMA, stages whose data it
   // has waited for, and the barrier phase of the chunk's last commit
@@ -251,16 +274,21 @@ __global__ void __launch_bounds__(kThreadsG, 1)
     tc_fence_after();
     __syncthreads();
     if (s_fail) break;
-    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
 #pragma unroll
     for (int pg = 0; pg < S; ++pg) {
-      const double sc = ldexp(1.0, -14 - 8 * pg);
 #pragma unroll
-      for (int c16 = 0; c16 < kTN / 16; ++c16) {
+      for (int c16 = 0; c16 < kHalf / 16; ++c16) {
         float v[16];
-        tmem_ld16(tmem + lane_base + (uint32_t)(pg * kTN + c16 * 16), v);
+        tmem_ld16(tmem + lane_base + (uint32_t)(pg * kTN + col_half + c16 * 16), v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc[c16 * 16 + j] = fma((double)v[j], sc, acc[c16 * 16 + j]);
+        for (int j = 0; j < 16; ++j) {
+          const int64_t g = (int64_t)exact_int(v[j]);
+          if (pg < H)
+            acc_hi[c16 * 16 + j] += g * ((int64_t)1 << (8 * (H - 1 - pg)));
+          else
+            acc_lo[c16 * 16 + j] += g * ((int64_t)1 << (8 * (S - 1 - pg)));
+        }
       }
     }
     tc_fence_before();
@@ -270,21 +298,28 @@ __global__ void __launch_bounds__(kThreadsG, 1)
   if (s_fail) {
     if (threadIdx.x == 0) atomicOr(p.status, DS_TIMEOUT);
   } else if (nk > 0) {
-    const int row = m0 + threadIdx.x;
+    const int row = m0 + 32 * (warp & 3) + (threadIdx.x & 31);
+    // value = acc_hi 2^(-14 - 8 (H - 1)) + acc_lo 2^(-14 - 8 (S - 1)); the
+    // conversions round only past 2^53 (acc_lo over many chunks)
+    const double s_hi = ldexp(1.0, -14 - 8 * (H - 1)), s_lo = ldexp(1.0, -14 - 8 * (S - 1));
+    double acc[kHalf];
+#pragma unroll
+    for (int c = 0; c < kHalf; ++c)
+      acc[c] = H > 0 ? fma((double)acc_hi[H > 0 ? c : 0], s_hi, (double)acc_lo[c] * s_lo) : (double)acc_lo[c] * s_lo;
     if (row < p.M) {
       const int ea = p.ea[row];
       if (p.mode == 0) {
         double* out = static_cast<double*>(p.out) + (int64_t)row * p.ldo;
 #pragma unroll
-        for (int c = 0; c < kTN; ++c) {
-          const int col = n0 + c;
+        for (int c = 0; c < kHalf; ++c) {
+          const int col = n0 + col_half + c;
           if (col < p.N) atomicAdd(out + col, ldexp(acc[c], ea + p.eb[col]));
         }
       } else if (p.out_f32) {
         float* out = static_cast<float*>(p.out);
 #pragma unroll
-        for (int c = 0; c < kTN; ++c) {
-          const int col = n0 + c;
+        for (int c = 0; c < kHalf; ++c) {
+          const int col = n0 + col_half + c;
           if (col < p.N) {
             float* o = out + (int64_t)col * p.ldo + row;
             *o = (float)((double)*o - ldexp(acc[c], ea + p.eb[col]));
@@ -293,8 +328,8 @@ __global__ void __launch_bounds__(kThreadsG, 1)
       } else {
         double* out = static_cast<double*>(p.out);
 #pragma unroll
-        for (int c = 0; c < kTN; ++c) {
-          const int col = n0 + c;
+        for (int c = 0; c < kHalf; ++c) {
+          const int col = n0 + col_half + c;
           if (col < p.N) {
             double* o = out + (int64_t)col * p.ldo + row;
             *o -= ldexp(acc[c], ea + p.eb[col]);
