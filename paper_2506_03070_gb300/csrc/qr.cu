@@ -420,6 +420,11 @@ __global__ void __launch_bounds__(256) k_tform(const double* __restrict__ gram, 
 
 constexpr int kPanelBlocksMax = 64;    // blocks of the global-memory panel kernel
 constexpr int kPanelBlocksCap = 320;   // partial-sum slots (the shared-memory kernel may use more blocks)
+// Rows per block of the shared-memory panel kernel.  Measured on the 8000 x 2001
+// sketch (precond phase): 64 rows per block 88.9 ms, 96 rows 78.6 ms, 192 rows
+// 71.4 ms -- more blocks make each grid barrier and the per-column sums over
+// the blocks' partials slower than the smaller per-block share saves.
+constexpr int kPanelRowsTarget = 192;
 constexpr int kSlicesMax = 7;  // bf16 slices per row for FP64 data (3 for FP32)
 
 // bf16 slices per row: 7 (56 bits) for FP64 data; 4 (32 bits) for FP32 data,
@@ -516,8 +521,10 @@ cudaError_t householder_blocked(TW* W, int64_t d, int n, int ncol, double* rdiag
     int G = (int)std::min<int64_t>((L + 255) / 256, kPanelBlocksMax);
     G = std::min(G, std::max(1, per_sm * sms));
     if (G < 1) G = 1;
-    // rows held in shared memory when every block's share fits
-    int Gs = (int)std::max<int64_t>((L + 191) / 192, 1);
+    // rows held in shared memory when every block's share fits; about
+    // kPanelRowsTarget rows per block (one block per SM at most)
+    int Gs = (int)std::max<int64_t>((L + kPanelRowsTarget - 1) / kPanelRowsTarget, 1);
+    Gs = std::min(Gs, std::min(std::max(1, per_sm_s * sms), kPanelBlocksCap));
     const bool smem_ok = per_sm_s >= 1 && Gs <= per_sm_s * sms && Gs <= kPanelBlocksCap &&
                          (L + Gs - 1) / Gs <= kPanelSmemRows;
     TW* Wp = W;
