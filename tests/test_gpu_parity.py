@@ -83,6 +83,23 @@ def test_sketch_apply_mixed_fp32(ctx, orc, ldy_pad):
     assert np.linalg.norm(Y - Yo) <= (1 + np.sqrt(200)) * u32 * np.linalg.norm(Yo)
 
 
+@pytest.mark.parametrize("m,n,d,zeta,has_b", [(20011, 33, 120, 16, False), (7777, 64, 300, 32, True),
+                                              (3001, 5, 64, 64, True), (90001, 129, 2600, 8, True),
+                                              (257, 17, 40, 3, True)])
+def test_sketch_apply_mixed_variants(ctx, orc, m, n, d, zeta, has_b):
+    """The FP32 chunk-sum sketch for every zeta register width (8, 16, 32, 64),
+    without b, with ragged last chunks and rows per warp from 1 to 32: within
+    the FP32 error of one sum over all m zeta / d terms of each entry (the
+    chunk sums can only be better) plus the final rounding."""
+    rng = np.random.default_rng(m + d)
+    A = rng.standard_normal((m, n))
+    b = rng.standard_normal(m) if has_b else None
+    Y = ctx.lsq_sketch(_dev(A), _dev(b) if has_b else None, d, zeta, 17, prec=1).cpu().numpy().astype(np.float64)
+    Yo = orc.sketch_apply(A, b, d, zeta, 17)
+    u32 = 2.0 ** -24
+    assert np.linalg.norm(Y - Yo) <= (1 + np.sqrt(m * zeta / d)) * u32 * np.linalg.norm(Yo)
+
+
 def test_sketch_apply_mixed_blocked_large(ctx, orc):
     """~5000 terms per entry (m zeta / d at 2.5e6 rows, d = 4000): one FP32
     sum over all of them would be off by ~0.3 sqrt(5000) u32 = 1.3e-6
@@ -339,8 +356,9 @@ def test_solve_host_memory_equals_device(ctx, orc, prec):
     assert abs(infod["iters"] - infoh["iters"]) <= slack, (infod["iters"], infoh["iters"])
 
 
-@pytest.mark.parametrize("m,n,lda_pad", [(8000, 100, 0), (6001, 77, 5), (5000, 600, 0), (3001, 1, 3)])
-def test_solve_pinned_host_memory_read_in_place(ctx, orc, m, n, lda_pad):
+@pytest.mark.parametrize("m,n,lda_pad,zeta", [(8000, 100, 0, 8), (6001, 77, 5, 16), (5000, 600, 0, 8),
+                                              (3001, 1, 3, 5), (4001, 40, 0, 33)])
+def test_solve_pinned_host_memory_read_in_place(ctx, orc, m, n, lda_pad, zeta):
     """Pinned host A and b: the FP64 sketch reads them in place and writes the
     device copy in the same pass.  The solution equals the device-memory
     solve's up to the order of the sketch's reductions (iterations within
@@ -350,9 +368,9 @@ def test_solve_pinned_host_memory_read_in_place(ctx, orc, m, n, lda_pad):
     Ap[:, :n] = torch.from_numpy(A)
     bp = torch.from_numpy(b).pin_memory()
     Ah, bh = Ap.numpy()[:, :n], bp.numpy()
-    d = 4 * n + 4
-    xd, infod = ctx.lsq_solve(_dev(A), _dev(b), d, seed=5, tol=1e-12)
-    xh, infoh = ctx.lsq_solve(Ah, bh, d, seed=5, tol=1e-12)
+    d = max(4 * n + 4, zeta)
+    xd, infod = ctx.lsq_solve(_dev(A), _dev(b), d, zeta=zeta, seed=5, tol=1e-12)
+    xh, infoh = ctx.lsq_solve(Ah, bh, d, zeta=zeta, seed=5, tol=1e-12)
     bn = np.linalg.norm(b)
     assert infoh["status"] == 0
     assert abs(infod["iters"] - infoh["iters"]) <= 1, (infod["iters"], infoh["iters"])
