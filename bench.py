@@ -1002,6 +1002,12 @@ def run_gpu(args, emit=True):
                                   lsqr_iters=2)
         line["cpu_baseline"] = {"value": 1.0 / est["t_solve_s"], "unit": "solves/s", "cores": cores, "kind": "oracle",
                                 "sample": est["sample"] + " (OpenMP build, -O3 -fopenmp)"}
+        # the same estimate on one thread (C0 and C1)
+        orc.set_threads(1)
+        est1 = cpu_oracle_estimate(_Scaled(Ah2, m), bh2, d, zeta, seed, tol, int(round(it_mean)), rows=rows,
+                                   lsqr_iters=2)
+        orc.set_threads(cores)
+        line["cpu_baseline"]["value_1_thread"] = 1.0 / est1["t_solve_s"]
     if rank == 0 and emit:
         print(json.dumps(line))
     if world > 1 and emit:

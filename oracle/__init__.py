@@ -79,6 +79,14 @@ def use_parallel(threads: int) -> None:
     os.environ["OMP_NUM_THREADS"] = str(int(threads))
     _lib = None
     _load(build_parallel())
+    set_threads(threads)
+
+
+def set_threads(threads: int) -> None:
+    """Threads of the OpenMP build's loops from now on (the checker build
+    ignores it)."""
+    if _lib is not None and hasattr(_lib, "orc_set_threads"):
+        _lib.orc_set_threads(int(threads))
 
 
 class LsqrInfo(ctypes.Structure):
@@ -113,6 +121,8 @@ def _load(path):
     L.orc_backward_error.argtypes = [P, i64, i64, i64, P, P, f64, P]
     L.orc_backward_error.restype = f64
     L.orc_solve.argtypes = [P, i64, i64, i64, P, i64, i32, u64, f64, i64, P, P, P, P, P]
+    L.orc_set_threads.argtypes = [i32]
+    L.orc_set_threads.restype = None
     _lib = L
 
 

@@ -537,3 +537,14 @@ done:
   free(Y); free(tau); free(R); free(M); free(z); free(x0);
   return rc;
 }
+
+/* Threads of the CPU-baseline build's parallel loops (no effect on the
+ * single-threaded checker build).  Not arithmetic: the per-thread partial
+ * sums are added in thread order either way. */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  omp_set_num_threads(n > 0 ? n : 1);
+#else
+  (void)n;
+#endif
+}
