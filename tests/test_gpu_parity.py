@@ -564,9 +564,10 @@ def test_solve_double_float_repeatable(ctx):
 
 # ------------------------------------------------ wide rows (n > 512) ---
 @pytest.mark.parametrize("m,n,d,lda_pad", [(6000, 513, 1100, 0), (8000, 1000, 2400, 0), (5000, 1100, 2300, 3),
-                                           (9000, 2100, 4300, 0)])
+                                           (6000, 1025, 2100, 1), (7000, 2048, 4200, 0), (9000, 2100, 4300, 0)])
 def test_lsqr_wide_rows_match_oracle(ctx, orc, m, n, d, lda_pad):
-    """Rows shared by 2, 4 or 8 warps (column panels).  M comes from LAPACK's
+    """Rows shared by 2, 4 or 8 warps (column panels; n = 1025 and 2048 are
+    the edges of the 4-warp band).  M comes from LAPACK's
     QR of the oracle's sketch (any upper triangular M is a valid input); the
     iterates must follow the oracle's LSQR."""
     A, b, xt = _problem(m, n, 1e6, m + n)
