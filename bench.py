@@ -356,6 +356,7 @@ def run_batch(args):
             "config": {"workload": f"batched_{len(probs)}_m2000-50000_n16-128_cond1e2-1e10_d4n_zeta8_tol1e-12",
                        "problems": len(probs), "total_A_GB": elems * 8 / 1e9},
             "lsqr_iters_mean": statistics.mean(iters), "lsqr_iters_max": max(iters),
+            "pass_shapes": [ctx.lsq_batch_shape_get(k) for k in range(4)],
             "hbm_gbs_A_stream": abytes / (t / 1e3) / 1e9, "hbm_peak_gbs": float(peaks["hbm_gbs"]),
             "accuracy": {"backward_error_kw_max_sampled": worst,
                          "statuses": sorted(set(r["status"] for r in res))},
@@ -548,7 +549,7 @@ def run_serve(args):
             "saturated": sat, "sub_saturation": sub,
             "sequential_plain_solves": {"solves_per_s": seq_rate, "sample": len(seq_idx),
                                         "serving_over_sequential": sat["solves_per_s"] / seq_rate},
-            "serve_stats": stats, "clocks": clocks}
+            "serve_stats": stats, "pass_shapes": [ctx.lsq_batch_shape_get(k) for k in range(4)], "clocks": clocks}
     if not args.no_cpu_baseline:
         cm = _oracle_cost_model()
         tot = 0.0

@@ -336,10 +336,10 @@ lsq_status lsq_solve_csr(lsq_ctx* ctx, const lsq_csr_problem* problem, const lsq
  * block barriers).  A, b and x of every item are device pointers; x receives
  * the solution.  Limits per item: 1 <= n <= 256, n+1 <= d, 1 <= zeta <= 8
  * (larger problems belong to lsq_solve, which uses the whole GPU).
- * The LSQR pass processes 32/L rows per warp with L lanes per row; L is picked
- * per n-range by the context's autotuner (LSQ_FLAG_AUTOTUNE times the
- * candidate shapes on the largest problems of the batch the first time an
- * n-range is seen, and keeps the fastest).  results may be NULL. */
+ * The LSQR pass shape (lsq_batch_shape_set below) is picked per n-range by
+ * the context's autotuner (LSQ_FLAG_AUTOTUNE times the candidate shapes on the
+ * largest problems of the batch the first time an n-range is seen, and keeps
+ * the fastest).  results may be NULL. */
 typedef struct {
   const double* A;
   const double* b;
@@ -362,6 +362,19 @@ typedef struct {
 
 lsq_status lsq_solve_batch(lsq_ctx* ctx, const lsq_batch_item* items, int64_t count, double tol, int64_t maxit,
                            int32_t flags, lsq_batch_result* results, void* stream);
+
+/* Pass shape of an n-range of batched and served problems: bucket 0 (n <= 32),
+ * 1 (n <= 64), 2 (n <= 128), 3 (n <= 256).  Shape s gives each row L lanes with
+ * P column pairs a lane, a warp taking 32/L rows a step: (L, P) = (8,2), (8,4),
+ * (16,2), (16,4), (32,2), (32,4) for s = 0..5 (it takes n <= 2 L P).
+ * lsq_batch_shape_set pins the shape of a bucket (the value LSQ_FLAG_AUTOTUNE
+ * stores after timing the candidates; -1 clears it, and a bucket without a
+ * shape takes its default: 0, 1, 3, 5); a shape that cannot take the bucket's
+ * largest n, or a bucket outside 0..3, gives LSQ_ERR_ARG.
+ * lsq_batch_shape_get writes the pinned shape (-1: none) to *shape.  Neither
+ * call may run concurrently with a solve on the same context. */
+lsq_status lsq_batch_shape_set(lsq_ctx* ctx, int32_t bucket, int32_t shape);
+lsq_status lsq_batch_shape_get(lsq_ctx* ctx, int32_t bucket, int32_t* shape);
 
 /* ---- Serving: asynchronous solves of problems that arrive over time -----
  * lsq_submit queues a problem and returns at once with a ticket; lsq_poll

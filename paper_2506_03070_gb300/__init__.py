@@ -35,7 +35,8 @@ EXPORTS = ("lsq_create", "lsq_destroy", "lsq_last_error", "lsq_status_string", "
            "lsq_sketch_indices", "lsq_sketch", "lsq_precond", "lsq_lsqr", "lsq_check", "lsq_solve",
            "lsq_check_noalloc", "lsq_solve_batch", "lsq_submit", "lsq_poll", "lsq_serve_config",
            "lsq_serve_stats_get", "lsq_set_qr_mode", "lsq_choose_d", "lsq_d_from_model", "lsq_lambert_w0",
-           "lsq_hbm", "lsq_solve_csr", "lsq_set_wait_limit", "lsq_selftest_wait")
+           "lsq_hbm", "lsq_solve_csr", "lsq_set_wait_limit", "lsq_selftest_wait", "lsq_batch_shape_set",
+           "lsq_batch_shape_get")
 QR_AUTO, QR_UNBLOCKED, QR_BLOCKED = 0, 1, 2
 
 
@@ -150,7 +151,9 @@ def load(path: str = LIB_PATH):
     L.lsq_serve_stats_get.argtypes = [P, ctypes.POINTER(ServeStats)]
     L.lsq_set_wait_limit.argtypes = [P, f64]
     L.lsq_selftest_wait.argtypes = [P, i32, P]
-    for name in ("lsq_set_wait_limit", "lsq_selftest_wait", "lsq_create", "lsq_destroy", "lsq_sketch_indices", "lsq_sketch", "lsq_precond", "lsq_lsqr",
+    L.lsq_batch_shape_set.argtypes = [P, i32, i32]
+    L.lsq_batch_shape_get.argtypes = [P, i32, ctypes.POINTER(i32)]
+    for name in ("lsq_batch_shape_set", "lsq_batch_shape_get", "lsq_set_wait_limit", "lsq_selftest_wait", "lsq_create", "lsq_destroy", "lsq_sketch_indices", "lsq_sketch", "lsq_precond", "lsq_lsqr",
                  "lsq_check", "lsq_solve", "lsq_submit", "lsq_poll", "lsq_serve_config", "lsq_serve_stats_get"):
         getattr(L, name).restype = i32
     _lib = L
@@ -364,6 +367,17 @@ class Context:
         self._check(self.lib.lsq_check(self.h, _ptr(A), m, n, lda, _ptr(b), _ptr(x), _ptr(M), ctypes.byref(info),
                                        _stream(stream)))
         return info.as_dict()
+
+    def lsq_batch_shape_set(self, bucket, shape):
+        """Pin the LSQR pass shape of an n-range (bucket 0..3: n <= 32, 64,
+        128, 256) for batched and served solves; -1 clears it."""
+        self._check(self.lib.lsq_batch_shape_set(self.h, bucket, shape))
+
+    def lsq_batch_shape_get(self, bucket):
+        """The pinned pass shape of an n-range, or -1."""
+        r = ctypes.c_int32(0)
+        self._check(self.lib.lsq_batch_shape_get(self.h, bucket, ctypes.byref(r)))
+        return r.value
 
     def lsq_solve_batch(self, problems, tol=1e-12, maxit=0, flags=0, stream=None, raise_on_error=True):
         """Solve many problems in one persistent launch.  problems: list of

@@ -503,6 +503,26 @@ lsq_status lsq_selftest_wait(lsq_ctx* ctx, int32_t kind, void* stream) {
   return status_from_bits(ctx, bits);
 }
 
+lsq_status lsq_batch_shape_set(lsq_ctx* ctx, int32_t bucket, int32_t shape) {
+  lsq_status s;
+  if ((s = check_ctx(ctx)) != LSQ_OK) return s;
+  static const int kBucketMaxN[4] = {32, 64, 128, 256};
+  if (bucket < 0 || bucket > 3) return fail(ctx, LSQ_ERR_ARG, "bucket must be 0..3");
+  if (shape != -1 && batch_shape_maxn(shape) < kBucketMaxN[bucket])
+    return fail(ctx, LSQ_ERR_ARG, "shape " + std::to_string(shape) + " cannot take n <= " +
+                                      std::to_string(kBucketMaxN[bucket]));
+  batch_set_shape(ctx->tuning, bucket, shape);
+  return LSQ_OK;
+}
+
+lsq_status lsq_batch_shape_get(lsq_ctx* ctx, int32_t bucket, int32_t* shape) {
+  lsq_status s;
+  if ((s = check_ctx(ctx)) != LSQ_OK) return s;
+  if (bucket < 0 || bucket > 3 || !shape) return fail(ctx, LSQ_ERR_ARG, "bucket must be 0..3, shape non-null");
+  *shape = batch_get_shape(ctx->tuning, bucket);
+  return LSQ_OK;
+}
+
 lsq_status lsq_set_qr_mode(lsq_ctx* ctx, int32_t mode) {
   if (!ctx) return LSQ_ERR_ARG;
   if (mode != LSQ_QR_AUTO && mode != LSQ_QR_UNBLOCKED && mode != LSQ_QR_BLOCKED)

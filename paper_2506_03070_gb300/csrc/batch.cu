@@ -149,7 +149,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(BatchParams bp) {
   }
 }
 
-// shapes able to take n, fastest-first default order
+// shapes able to take n, the one measured fastest on the batched mix first
+// (the default when the n-range is not tuned)
 void shape_candidates(int n, std::vector<int>& out) {
   out.clear();
   if (n <= 32) out = {0, 2};
@@ -279,7 +280,7 @@ void batch_items_fill(void* dst, const lsq_batch_item* src, int64_t count, const
     std::vector<int> c;
     shape_candidates(b.n, c);
     const int tuned = tune ? tune->shape_for_bucket[bk] : -1;
-    b.shape = tuned >= 0 ? tuned : c.back();
+    b.shape = tuned >= 0 ? tuned : c.front();
     out[i] = b;
   }
 }
@@ -289,5 +290,6 @@ int batch_bucket_of(int n) { return bucket_of(n); }
 void batch_set_shape(BatchTuning* t, int bucket, int shape) { t->shape_for_bucket[bucket] = shape; }
 int batch_get_shape(const BatchTuning* t, int bucket) { return t->shape_for_bucket[bucket]; }
 void batch_set_item_shape(void* items, int64_t i, int shape) { static_cast<BatchItem*>(items)[i].shape = shape; }
+int batch_shape_maxn(int shape) { return shape >= 0 && shape < kShapes ? shape_maxn(shape) : 0; }
 
 }  // namespace lsq

@@ -224,5 +224,7 @@ int batch_bucket_of(int n);
 void batch_set_shape(BatchTuning* t, int bucket, int shape);
 int batch_get_shape(const BatchTuning* t, int bucket);
 void batch_set_item_shape(void* items, int64_t i, int shape);
+// Largest n a pass shape takes (0: no such shape).
+int batch_shape_maxn(int shape);
 
 }  // namespace lsq

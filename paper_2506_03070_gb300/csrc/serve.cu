@@ -336,7 +336,7 @@ int variant_for(int n, const BatchTuning* tune) {
   std::vector<int> c;
   batch_shape_candidates(n, c);
   const int tuned = tune ? batch_get_shape(tune, batch_bucket_of(n)) : -1;
-  return tuned >= 0 ? tuned : c.back();
+  return tuned >= 0 ? tuned : c.front();
 }
 
 lsq_status status_of_bits(uint32_t bits) {

@@ -91,6 +91,54 @@ def test_batch_autotune_and_reuse(ctx, orc):
         assert orc.backward_error_kw(A, b, x.cpu().numpy()) <= 1e-10
 
 
+# every pass shape of every n-range, pinned: n at the edges of the range and
+# inside it (odd n, a single column pair, rows that do not fill a buffer)
+BUCKET_NS = {0: [1, 2, 16, 17, 31, 32], 1: [33, 50, 63, 64], 2: [65, 100, 127, 128], 3: [129, 200, 255, 256]}
+SHAPE_CASES = [(0, 0), (0, 2), (0, 5), (1, 1), (1, 2), (1, 3), (2, 3), (2, 4), (2, 5), (3, 5)]
+
+
+@pytest.mark.parametrize("bucket,shape", SHAPE_CASES)
+def test_batch_every_pass_shape(ctx, orc, bucket, shape):
+    """Batched solves with the bucket's pass shape pinned (lsq_batch_shape_set):
+    each result matches the oracle's solve on the same sketch, and the first
+    of the bucket's n also at another row count."""
+    probs, host = [], []
+    for k, n in enumerate(BUCKET_NS[bucket]):
+        for m in (1500 + 37 * k, 803):
+            A, b = _problem(m, n, 10.0 ** (3 + k % 5), 900 + 10 * k + m % 7)
+            d = max(4 * n, n + 1)
+            host.append((A, b, d))
+            probs.append({"A": _dev(A), "b": _dev(b), "d": d, "zeta": min(8, d), "seed": 40 + k})
+    ctx.lsq_batch_shape_set(bucket, shape)
+    try:
+        assert ctx.lsq_batch_shape_get(bucket) == shape
+        xs, res = ctx.lsq_solve_batch(probs, tol=1e-12)
+    finally:
+        ctx.lsq_batch_shape_set(bucket, -1)
+    assert ctx.lsq_batch_shape_get(bucket) == -1
+    for k, ((A, b, d), x, r) in enumerate(zip(host, xs, res)):
+        x = x.cpu().numpy()
+        bn = np.linalg.norm(b)
+        assert r["status"] == 0 and r["stop"] in (1, 2), (k, r)
+        assert orc.backward_error_kw(A, b, x) <= 1e-10, k
+        ref = orc.solve(A, b, d, probs[k]["zeta"], probs[k]["seed"], 1e-12, orc.default_maxit(A.shape[1], d, 1e-12))
+        assert np.linalg.norm(A @ (x - ref["x"])) <= 1e-10 * bn, k
+        assert abs(r["iters"] - ref["iters"]) <= 2, (k, r["iters"], ref["iters"])
+
+
+def test_batch_shape_set_refuses_bad_shapes(ctx):
+    """A shape too narrow for the bucket's n, an unknown shape or bucket: LSQ_ERR_ARG, nothing changed."""
+    import paper_2506_03070_gb300 as P
+    before = [ctx.lsq_batch_shape_get(k) for k in range(4)]
+    for bucket, shape in ((0, 6), (1, 0), (2, 2), (3, 4), (4, 0), (-1, 0), (0, -2)):
+        with pytest.raises(P.LsqError) as e:
+            ctx.lsq_batch_shape_set(bucket, shape)
+        assert e.value.status == -1
+    assert [ctx.lsq_batch_shape_get(k) for k in range(4)] == before
+    with pytest.raises(P.LsqError):
+        ctx.lsq_batch_shape_get(4)
+
+
 def test_batch_item_errors(ctx):
     import paper_2506_03070_gb300 as P
     A, b = _problem(500, 10, 10.0, 1)

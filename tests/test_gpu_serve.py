@@ -107,6 +107,35 @@ def test_serve_matches_oracle_and_plain_solve(sctx, orc):
         assert abs(info["rnorm"] - np.linalg.norm(r)) <= bound * info["rnorm"]
 
 
+@pytest.mark.parametrize("shapes", [(2, 2, 4, 5), (5, 5, 5, 5)])
+def test_serve_pinned_pass_shapes(sctx, orc, shapes):
+    """Requests with n <= 256 on pinned pass shapes other than the defaults
+    (0, 1, 3, 5; the wider shape of each range, and the widest shape for every
+    range) agree with the oracle; one request spans several blocks."""
+    from paper_2506_03070_gb300 import synth
+    for bucket, shape in enumerate(shapes):
+        sctx.lsq_batch_shape_set(bucket, shape)
+    try:
+        cases = [(5000, 20, 80), (9001, 37, 148), (30001, 100, 400), (7000, 200, 800), (400000, 64, 256)]
+        tickets, host = [], []
+        for k, (m, n, d) in enumerate(cases):
+            p = synth.batched_problem(m, n, 1e5, seed=600 + k, device="cpu")
+            A, b = p["A"].numpy(), p["b"].numpy()
+            host.append((A, b, d))
+            tickets.append(sctx.lsq_submit(torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda(), d, seed=20 + k))
+        res = [sctx.lsq_wait(t) for t in tickets]
+    finally:
+        for bucket in range(4):
+            sctx.lsq_batch_shape_set(bucket, -1)
+    assert max(r[2]["group_blocks"] for r in res) > 1
+    for k, ((A, b, d), (st, x, info)) in enumerate(zip(host, res)):
+        assert st == 0, (k, st)
+        x = x.cpu().numpy()
+        ref = orc.solve(A, b, d, 8, 20 + k, 1e-12, orc.default_maxit(A.shape[1], d, 1e-12))
+        assert abs(info["iters"] - ref["iters"]) <= 2, (k, info["iters"], ref["iters"])
+        assert np.linalg.norm(A @ (x - ref["x"])) <= 1e-10 * np.linalg.norm(b), k
+
+
 def test_serve_host_problems(sctx, orc):
     from paper_2506_03070_gb300 import synth
     p = synth.batched_problem(20000, 80, 1e6, seed=5, device="cpu")
