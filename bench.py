@@ -577,16 +577,25 @@ def _mem_available_bytes():
     return 0
 
 
+def sketch_slabs(d, ncol):
+    """Launches of the FP64 sketch: one per column slab of at most 48e6 bytes
+    of Y (a multiple of 32 columns), as the library splits it."""
+    w = max(32, int(48e6 / (d * 8.0)) // 32 * 32)
+    return 1 if w >= ncol else -(-ncol // w)
+
+
 def launches_per_solve(n, d, prec, blocked):
-    """Kernels of this library one lsq_solve launches: sketch (the mixed form
-    adds the pair-to-FP64 pass), column-major copy, QR (unblocked: 1 kernel;
-    blocked, per 64-column panel of the n columns: the panel kernel, four
-    slicing kernels, three tensor-core GEMMs and T -- the b column always
-    leaves a trailing update), R extraction, inverse, transpose, x0, and the
-    LSQR kernel (with the accuracy pass).  Checked against the ncu launch list
-    of the default bench line (295 per plain solve at 5e6 x 2000)."""
+    """Kernels of this library one lsq_solve launches: sketch (FP64: one per
+    column slab; the mixed form: the chunk-sum kernel and the pair-to-FP64
+    pass), column-major copy, QR (unblocked: 1 kernel; blocked, per 64-column
+    panel of the n columns: the panel kernel, four slicing kernels, three
+    tensor-core GEMMs and T -- the b column always leaves a trailing update),
+    R extraction, inverse, transpose, x0, and the LSQR kernel (with the
+    accuracy pass).  Checked against the ncu launch list of the default bench
+    line (297 per plain solve, 296 per mixed one at 5e6 x 2000)."""
     qr = 9 * ((n + 63) // 64) if blocked else 1
-    return 1 + (1 if prec == 1 else 0) + 1 + qr + 4 + 1
+    sketch = 2 if prec == 1 else sketch_slabs(d, n + 1)
+    return sketch + 1 + qr + 4 + 1
 
 
 def run_headline(args):

@@ -100,6 +100,27 @@ def test_sketch_apply_mixed_variants(ctx, orc, m, n, d, zeta, has_b):
     assert np.linalg.norm(Y - Yo) <= (1 + np.sqrt(m * zeta / d)) * u32 * np.linalg.norm(Yo)
 
 
+def test_sketch_apply_column_slabs(ctx, orc):
+    """A sketch larger than one L2-sized column slab (6400 x 1001: 51 MB in
+    FP64, 77 MB of pairs and chunk sums) is built slab by slab in both forms:
+    every column, b's included, against the oracle's sketch."""
+    m, n, d = 4000, 1000, 6400
+    rng = np.random.default_rng(77)
+    A = rng.standard_normal((m, n))
+    b = rng.standard_normal(m)
+    Ad, bd = _dev(A), _dev(b)
+    Yo = orc.sketch_apply(A, b, d, 8, 23)
+    Y64 = ctx.lsq_sketch(Ad, bd, d, 8, 23, prec=0).cpu().numpy()
+    k = m * 8 / d
+    assert np.max(np.abs(Y64 - Yo)) <= 64 * 2.2e-16 * k / np.sqrt(8) * 4
+    Y32 = ctx.lsq_sketch(Ad, bd, d, 8, 23, prec=1).cpu().numpy().astype(np.float64)
+    u32 = 2.0 ** -24
+    assert np.linalg.norm(Y32 - Yo) <= (1 + np.sqrt(k)) * u32 * np.linalg.norm(Yo)
+    # per column: no slab left out or added twice
+    col = np.linalg.norm(Y32 - Yo, axis=0) / np.linalg.norm(Yo, axis=0)
+    assert col.max() <= 8 * u32, col.max()
+
+
 def test_sketch_apply_mixed_blocked_large(ctx, orc):
     """~5000 terms per entry (m zeta / d at 2.5e6 rows, d = 4000): one FP32
     sum over all of them would be off by ~0.3 sqrt(5000) u32 = 1.3e-6
