@@ -566,11 +566,11 @@ lsq_status lsq_sketch(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64
     // pairs in workspace), rounded once into the FP32 output
     const int64_t ncol = n + (b ? 1 : 0), ldc = (ncol + 3) / 4 * 4;
     const size_t y64 = align_up((size_t)d * ncol * sizeof(double));
-    if ((s = ensure_ws(ctx, y64 + align_up((size_t)d * ldc * sizeof(float)))) != LSQ_OK) return s;
+    if ((s = ensure_ws(ctx, y64 + align_up(2 * (size_t)d * ldc * sizeof(float)))) != LSQ_OK) return s;
     float2* Yp = reinterpret_cast<float2*>(ctx->ws);
     float* Yc = reinterpret_cast<float*>(static_cast<char*>(ctx->ws) + y64);
     CK(cudaMemsetAsync(Yp, 0, (size_t)d * ncol * sizeof(float2), st));
-    CK(cudaMemsetAsync(Yc, 0, (size_t)d * ldc * sizeof(float), st));
+    CK(cudaMemsetAsync(Yc, 0, 2 * (size_t)d * ldc * sizeof(float), st));
     CK(sketch_apply_fold(A, m, n, lda, b, d, zeta, seed, Yc, ldc, Yp, ncol, ctx->d_status, ctx->d_max_rounds,
                          nullptr, nullptr, ctx->d_bar, ctx->sms, st));
     CK(round_to_float(Yp, ncol, static_cast<float*>(Y), ldy, d, ncol, ctx->sms, st));
@@ -809,7 +809,7 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
       *xd = x;
     }
     *Y = cv.take<char>((size_t)d * ldy * yes);
-    Yc = mixed ? cv.take<float>((size_t)d * ldc) : nullptr;
+    Yc = mixed ? cv.take<float>(2 * (size_t)d * ldc) : nullptr;
     pb->W = cv.take<double>((size_t)ncol * d);
     pb->rdiag = cv.take<double>(npad);
     pb->blk = cv.take<char>(precond_blocked_bytes(d, n));
@@ -883,7 +883,7 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
   } else {
     // blocked FP32 accumulation: chunk sums in Yc, folded into float pairs in
     // Y's memory, then turned into the FP64 sketch in place
-    CK(cudaMemsetAsync(Yc, 0, (size_t)d * ldc * sizeof(float), st));
+    CK(cudaMemsetAsync(Yc, 0, 2 * (size_t)d * ldc * sizeof(float), st));
     CK(sketch_apply_fold(A, m, n, lda_dev, b, d, o->zeta, o->seed, Yc, ldc, (float2*)Y, ldy, ctx->d_status,
                          ctx->d_max_rounds, ctx->d_range, ctx->d_fro, ctx->d_bar, ctx->sms, st));
     CK(pairs_to_double((float2*)Y, d * ldy, ctx->sms, st));

@@ -26,8 +26,8 @@ cudaError_t round_to_float(const float2* Y, int64_t ldy, float* out, int64_t ldo
 // In place: each of the count float pairs becomes the double hi + lo.
 cudaError_t pairs_to_double(float2* Y, int64_t count, int sms, cudaStream_t st);
 // The mixed form's sketch with blocked FP32 accumulation: terms are added in
-// FP32 into Yc (d x ldc floats, ldc % 4 == 0, zero on entry and on exit) one
-// chunk of rows at a time, each chunk's sums then added into the float-pair
+// FP32 into Yc (two buffers of d x ldc floats, ldc % 4 == 0, zero on entry and
+// on exit) one chunk of rows at a time, each chunk's sums then added into the float-pair
 // sketch Y (d x ldy pairs, zero on entry; pairs_to_double or round_to_float
 // finish it).  Cooperative launch; bar's counter is reset.
 cudaError_t sketch_apply_fold(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, int64_t d,

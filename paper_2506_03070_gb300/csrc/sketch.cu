@@ -184,7 +184,12 @@ __device__ __forceinline__ float to_float_int(double a) {
 // FP32 (4-wide vector reductions into Yc; lane l owns column groups
 // 4(l + 32t) .. +3, entries past n are b_i (column n) or 0), but only
 // for one chunk of rows at a time; after each chunk the grid meets at a
-// barrier, adds Yc into the running sketch Yp and clears Yc.  A chunk is R rows
+// barrier, adds the chunk's sums into the running sketch Yp and clears them.
+// Yc holds two chunk buffers (chunk k uses buffer k mod 2): a block folds
+// chunk k while the others already reduce chunk k+1 into the other buffer,
+// and the barrier after chunk k+1 (which every block reaches only after its
+// share of chunk k's fold) orders that fold before chunk k+2 reuses the
+// buffer -- one grid barrier per chunk.  A chunk is R rows
 // per warp of the grid, sized so that each entry of Yc receives about
 // kFoldTerms terms (R = kFoldTerms d / (zeta warps), clamped to [1, 32]):
 // FP32 rounding then grows with sqrt(kFoldTerms) instead of sqrt(zeta m / d)
@@ -193,8 +198,9 @@ __device__ __forceinline__ float to_float_int(double a) {
 // FP32 pipe (an FP64 add per entry per chunk would tie up GB300's FP64 pipe);
 // pairs_to_double / round_to_float turn Yp into the sketch.  ||A||_F^2 is
 // summed the same way from the FP32 values of the entries (relative error
-// about 2^-22).  Yc (ldc % 4 == 0, 16-byte aligned) and Yp must be zero on
-// entry; Yc is zero again on exit.  Cooperative launch (grid barriers).
+// about 2^-22).  Yc (2 d x ldc floats, ldc % 4 == 0, 16-byte aligned) and Yp
+// must be zero on entry; Yc is zero again on exit.  Cooperative launch (grid
+// barriers).
 template <int N>
 __global__ void __launch_bounds__(256) k_sketch_fold(const double* __restrict__ A, int64_t m, int n, int64_t lda,
                                                      const double* __restrict__ b, uint64_t d, int zeta,
@@ -213,7 +219,8 @@ __global__ void __launch_bounds__(256) k_sketch_fold(const double* __restrict__ 
   bool bad = false;
   uint32_t ea = 0, eb = 0;
   float fh = 0.f, fl = 0.f;  // sum of A_ij^2 as a float pair
-  for (int64_t c0 = 0; c0 < m; c0 += chunk) {
+  for (int64_t c0 = 0, kc = 0; c0 < m; c0 += chunk, ++kc) {
+    float* yck = Yc + (kc & 1) * (int64_t)d * ldc;  // this chunk's buffer
     const int64_t base = c0 + gw * R;
     const int nrows = (int)max((int64_t)0, min((int64_t)R, m - base));
     if (lane < nrows) {
@@ -252,16 +259,18 @@ __global__ void __launch_bounds__(256) k_sketch_fold(const double* __restrict__ 
         }
         for (int k = 0; k < zeta; ++k) {
           const bool neg = ((sg >> k) & 1ull) == 0ull;
-          red_add_v4(Yc + (int64_t)ci[k] * ldc + 4 * g, flip_sign_f(v[0], neg), flip_sign_f(v[1], neg),
+          red_add_v4(yck + (int64_t)ci[k] * ldc + 4 * g, flip_sign_f(v[0], neg), flip_sign_f(v[1], neg),
                      flip_sign_f(v[2], neg), flip_sign_f(v[3], neg));
         }
       }
     }
     __syncwarp();
-    if (!grid_sync(bar, status, gridDim.x)) break;  // every reduction of the chunk has landed
-    // the chunk's FP32 sums into the running pairs; Yc cleared for the next chunk
+    // every reduction of this chunk has landed, every block's fold of the
+    // previous chunk is done
+    if (!grid_sync(bar, status, gridDim.x)) break;
+    // the chunk's FP32 sums into the running pairs; its buffer cleared for chunk k+2
     for (int64_t r = blockIdx.x; r < (int64_t)d; r += gridDim.x) {
-      float* yc = Yc + r * ldc;
+      float* yc = yck + r * ldc;
       float2* y = Yp + r * ldy;
       for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
         const float2 p = __ldcg(y + c);
@@ -271,7 +280,6 @@ __global__ void __launch_bounds__(256) k_sketch_fold(const double* __restrict__ 
         __stcg(yc + c, 0.f);
       }
     }
-    if (!grid_sync(bar, status, gridDim.x)) break;  // Yc is clear before the next chunk's reductions
   }
   if (bad) atomicOr(status, DS_NONFINITE);
   flush_range(ea, eb, range);
