@@ -437,6 +437,61 @@ __global__ void __launch_bounds__(256) k_slice(const TX* __restrict__ X, int R, 
   }
 }
 
+// The same slices for the plain form (no T) with one block per row: the row's
+// largest magnitude by a block reduction, then its entries sliced by all 256
+// threads (rows of C and U are thousands of entries long; a warp per row left
+// the pass bound by the latency of its ~250 dependent steps).
+template <typename TX>
+__global__ void __launch_bounds__(256) k_slice_rows(const TX* __restrict__ X, int R, int K, int64_t ldx, int S,
+                                                    __nv_bfloat16* __restrict__ out, int Kpad, int* __restrict__ ex,
+                                                    int Rpad) {
+  __shared__ __nv_bfloat16 s_bf[257];  // s_bf[d + 128] = bf16(d), d in [-128, 128]
+  __shared__ double s_red[8];
+  __shared__ int s_e;
+  for (int i = threadIdx.x; i < 257; i += blockDim.x) s_bf[i] = __float2bfloat16_rn((float)(i - 128));
+  __syncthreads();
+  for (int r = blockIdx.x; r < Rpad; r += gridDim.x) {
+    if (r >= R) {  // padding rows of the slice arrays are zero
+      for (int q = 0; q < S; ++q)
+        for (int k = threadIdx.x; k < Kpad; k += blockDim.x) out[((int64_t)q * Rpad + r) * Kpad + k] = s_bf[128];
+      if (threadIdx.x == 0) ex[r] = 0;
+      continue;
+    }
+    const TX* x = X + (int64_t)r * ldx;
+    double mx = 0.0;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) mx = fmax(mx, fabs((double)x[k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, s_red[w]);
+      int e = 0;
+      if (m > 0.0) frexp(m, &e);
+      s_e = e;
+      ex[r] = e;
+    }
+    __syncthreads();
+    const int shift_base = 7 - s_e + 8 * (S - 1);
+    for (int k = threadIdx.x; k < Kpad; k += blockDim.x) {
+      long long F = 0;
+      if (k < K) F = fixed_point((double)x[k], shift_base);
+      for (int q = S - 1; q > 0; --q) {
+        int dg = (int)(F & 0xFF);
+        F >>= 8;  // arithmetic: F = floor(F / 256)
+        if (dg >= 128) {
+          dg -= 256;
+          F += 1;
+        }
+        out[((int64_t)q * Rpad + r) * Kpad + k] = s_bf[dg + 128];
+      }
+      out[(int64_t)r * Kpad + k] = s_bf[(int)F + 128];  // leading digit, |F| <= 128
+    }
+    __syncthreads();  // s_e and s_red are rewritten for the next row
+  }
+}
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point query (the
 // library links no driver library).
 typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -509,6 +564,11 @@ cudaError_t oz_slice(const TX* X, int R, int K, int64_t ldx, const double* T, in
                      int Rpad, int sms, cudaStream_t st) {
   if (R <= 0 || Rpad < R) return R <= 0 ? cudaSuccess : cudaErrorInvalidValue;
   if (T && K > 64) return cudaErrorInvalidValue;  // the U T^T form holds two values per lane
+  if (!T && K > 256) {
+    const int blocks = (int)std::min<int64_t>((int64_t)Rpad, (int64_t)sms * 8);
+    k_slice_rows<TX><<<blocks, 256, 0, st>>>(X, R, K, ldx, S, static_cast<__nv_bfloat16*>(out), Kpad, ex, Rpad);
+    return cudaGetLastError();
+  }
   const int blocks = (int)std::min<int64_t>(((int64_t)Rpad + 7) / 8, (int64_t)sms * 8);
   k_slice<TX><<<blocks, 256, 0, st>>>(X, R, K, ldx, T, S, static_cast<__nv_bfloat16*>(out), Kpad, ex, Rpad);
   return cudaGetLastError();
