@@ -423,7 +423,9 @@ constexpr int kPanelBlocksCap = 320;   // partial-sum slots (the shared-memory k
 // Rows per block of the shared-memory panel kernel.  Measured on the 8000 x 2001
 // sketch (precond phase): 64 rows per block 88.9 ms, 96 rows 78.6 ms, 192 rows
 // 71.4 ms -- more blocks make each grid barrier and the per-column sums over
-// the blocks' partials slower than the smaller per-block share saves.
+// the blocks' partials slower than the smaller per-block share saves; fewer,
+// larger blocks are slower too (later build: 192 rows 63.4 ms, 256 / 320 / 400
+// rows 65.7 / 64.4 / 65.6 ms).
 constexpr int kPanelRowsTarget = 192;
 constexpr int kSlicesMax = 7;  // bf16 slices per row for FP64 data (3 for FP32)
 
