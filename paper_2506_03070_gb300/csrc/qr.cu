@@ -659,25 +659,38 @@ __global__ void k_extract_r(const TW* __restrict__ W, int64_t d, int n, const do
     for (int i = threadIdx.x; i < n; i += blockDim.x) z[i] = (double)W[(int64_t)n * d + i];
 }
 
-// Column c of M = R^{-1} by back substitution, one warp per column, written
-// as row c of Mt (contiguous).  R is row-major n x n.
-__global__ void __launch_bounds__(256) k_tri_inverse(const double* __restrict__ R, int n,
+// Column c of M = R^{-1}, written as row c of Mt (contiguous), by
+// column-oriented back substitution in one block: m_c = 1 / R_cc; then for
+// k = c, c-1, ..., 1 every row i < k takes p_i += R_ik m_k (column k of R,
+// contiguous in Rt = R^T) and the thread that owns row k-1 finishes
+// m_{k-1} = -p_{k-1} / R_{k-1,k-1}, published for the next step through a
+// two-slot shared word (one block barrier per step).  The partial sums p stay
+// in shared memory, so R is read once per column of M and no step waits on a
+// reduction across threads.  Blocks take the longest columns first.
+__global__ void __launch_bounds__(256) k_tri_inverse(const double* __restrict__ Rt, int n,
                                                      double* __restrict__ Mt) {
-  const int lane = threadIdx.x & 31;
-  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (c >= n) return;
+  extern __shared__ double s_p[];  // [n]
+  __shared__ double s_m[2];
+  const int c = n - 1 - (int)blockIdx.x;
   double* mc = Mt + (int64_t)c * n;
-  for (int i = c + 1 + lane; i < n; i += 32) mc[i] = 0.0;
-  if (lane == 0) mc[c] = 1.0 / R[(int64_t)c * n + c];
-  __syncwarp();
-  for (int i = c - 1; i >= 0; --i) {
-    // s = sum_{k=i+1..c} R[i][k] M[k][c]
-    const double* Ri = R + (int64_t)i * n;
-    double s = 0.0;
-    for (int k = i + 1 + lane; k <= c; k += 32) s = fma(Ri[k], mc[k], s);
-    s = warp_allreduce_sum(s);
-    if (lane == 0) mc[i] = -s / Ri[i];
-    __syncwarp();
+  for (int i = threadIdx.x; i < c; i += blockDim.x) s_p[i] = 0.0;
+  for (int i = c + 1 + threadIdx.x; i < n; i += blockDim.x) mc[i] = 0.0;
+  if (threadIdx.x == 0) {
+    const double m = 1.0 / Rt[(int64_t)c * n + c];
+    s_m[c & 1] = m;
+    mc[c] = m;
+  }
+  __syncthreads();
+  for (int k = c; k > 0; --k) {
+    const double mk = s_m[k & 1];
+    const double* col = Rt + (int64_t)k * n;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) s_p[i] = fma(col[i], mk, s_p[i]);
+    if (threadIdx.x == (k - 1) % (int)blockDim.x) {  // owner of row k-1: its update is done
+      const double m = -s_p[k - 1] / Rt[(int64_t)(k - 1) * n + (k - 1)];
+      s_m[(k - 1) & 1] = m;
+      mc[k - 1] = m;
+    }
+    __syncthreads();
   }
 }
 
@@ -757,10 +770,19 @@ cudaError_t precond(const TY* Y, int64_t d, int64_t n64, int64_t ldy, int has_b,
   k_extract_r<TY><<<(unsigned)std::min<int64_t>(((int64_t)n * n + 255) / 256, 1024), 256, 0, st>>>(
       W, d, n, buf.rdiag, Rw, nullptr, 0, buf.status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_tri_inverse<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(Rw, n, buf.Mt);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   {
+    // R^T into M's memory (the inverse reads columns of R), then Mt = rows of
+    // M = columns of R^{-1}, then M = Mt^T over R^T
     dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32)), block(32, 8);
+    k_transpose<<<grid, block, 0, st>>>(Rw, n, M);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t smem = (size_t)n * sizeof(double);
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(k_tri_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+      return e;
+    k_tri_inverse<<<(unsigned)n, 256, smem, st>>>(M, n, buf.Mt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_transpose<<<grid, block, 0, st>>>(buf.Mt, n, M);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

@@ -417,6 +417,39 @@ def test_solve_edge_shapes(ctx, orc):
     assert e.value.status == -1
 
 
+def test_solve_degenerate_inputs(ctx):
+    """Fewer rows than columns: the sketch has rank <= m < n and the rank test
+    refuses it (LSQ_ERR_RANK); no rows at all: the sketch is zero in both forms."""
+    import paper_2506_03070_gb300 as P
+    rng = np.random.default_rng(12)
+    A = rng.standard_normal((10, 20))
+    b = rng.standard_normal(10)
+    with pytest.raises(P.LsqError) as e:
+        ctx.lsq_solve(_dev(A), _dev(b), 64, seed=1)
+    assert e.value.status == -6
+    A0 = torch.zeros((0, 5), dtype=torch.float64, device="cuda")
+    b0 = torch.zeros(0, dtype=torch.float64, device="cuda")
+    for prec in (0, 1):
+        Y = ctx.lsq_sketch(A0, b0, 16, 8, 3, prec=prec)
+        assert Y.shape == (16, 6) and not Y.abs().any().item()
+
+
+def test_solve_largest_n(ctx, orc):
+    """n = 4096, the widest rows built (8 warps per row, 512 columns each; 64
+    panels of the blocked QR): the solution is the least-squares one (LAPACK's
+    pivoted QR on the same A and b) to 1e-10 in the A-norm, KW backward error
+    <= 1e-10."""
+    import scipy.linalg as sl
+    m, n = 12000, 4096
+    A, b, xt = _problem(m, n, 1e6, 4096)
+    x, info = ctx.lsq_solve(_dev(A), _dev(b), 2 * n + 8, seed=3, tol=1e-12)
+    x = x.cpu().numpy()
+    assert info["status"] == 0 and info["stop"] in (1, 2)
+    xs = sl.lstsq(A, b, lapack_driver="gelsy")[0]
+    assert np.linalg.norm(A @ (x - xs)) <= 1e-10 * np.linalg.norm(b)
+    assert orc.backward_error_kw(A, b, x) <= 1e-10
+
+
 def test_solve_tall_matches_oracle(ctx, orc):
     """A taller solve (100000 x 64, d = 256) against the oracle end to end."""
     A, b, xt = _problem(100000, 64, 1e8, 17)
