@@ -590,12 +590,12 @@ def launches_per_solve(n, d, prec, blocked):
     pass), column-major copy, QR (unblocked: 1 kernel; blocked, per 64-column
     panel of the n columns: the panel kernel, four slicing kernels, three
     tensor-core GEMMs and T -- the b column always leaves a trailing update),
-    R extraction, inverse, transpose, x0, and the LSQR kernel (with the
+    R extraction, R^T, inverse, transpose, x0, and the LSQR kernel (with the
     accuracy pass).  Checked against the ncu launch list of the default bench
-    line (297 per plain solve, 296 per mixed one at 5e6 x 2000)."""
+    line (298 per plain solve, 297 per mixed one at 5e6 x 2000)."""
     qr = 9 * ((n + 63) // 64) if blocked else 1
     sketch = 2 if prec == 1 else sketch_slabs(d, n + 1)
-    return sketch + 1 + qr + 4 + 1
+    return sketch + 1 + qr + 5 + 1
 
 
 def run_headline(args):

@@ -395,7 +395,10 @@ __global__ void __launch_bounds__(256) k_panel_smem(TW* __restrict__ W, int64_t 
 
 // T (b x b, column-major, upper) of Q = I - U T U^T from the Gram U^T U and
 // tau (LAPACK larft, forward, columnwise): T[j][j] = tau_j,
-// T[0:j, j] = -tau_j T[0:j, 0:j] (U[:, 0:j]^T u_j).  One block, FP64.
+// T[0:j, j] = -tau_j T[0:j, 0:j] (U[:, 0:j]^T u_j).  One block, FP64: row i of
+// each column's product is split over four consecutive threads (every fourth
+// l from i + q), combined by two shuffles, so its dependent FP64 chain is a
+// quarter as long (b <= 64: 256 threads).
 template <typename TW>
 __global__ void __launch_bounds__(256) k_tform(const double* __restrict__ gram, const TW* __restrict__ tau, int b,
                                                double* __restrict__ T) {
@@ -403,15 +406,17 @@ __global__ void __launch_bounds__(256) k_tform(const double* __restrict__ gram, 
   __shared__ double w[kPanelMax];
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) sT[e] = 0;
   __syncthreads();
+  const int i = threadIdx.x >> 2, q = threadIdx.x & 3;
   for (int j = 0; j < b; ++j) {
     const double tj = (double)tau[j];
     if (threadIdx.x < j) w[threadIdx.x] = gram[threadIdx.x + (int64_t)j * b];
     __syncthreads();
-    if (threadIdx.x < j) {
-      double s = 0;
-      for (int l = threadIdx.x; l < j; ++l) s = fma(sT[threadIdx.x + l * b], w[l], s);
-      sT[threadIdx.x + j * b] = -tj * s;
-    }
+    double s = 0;
+    if (i < j)
+      for (int l = i + q; l < j; l += 4) s = fma(sT[i + l * b], w[l], s);
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    if (i < j && q == 0) sT[i + j * b] = -tj * s;
     if (threadIdx.x == 0) sT[j + j * b] = tj;
     __syncthreads();
   }
