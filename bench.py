@@ -674,6 +674,30 @@ def run_headline(args):
     # accuracy of the mixed solution by the same FP64 pass
     chk_m = ctx.lsq_check(A, b, xm)
 
+    # the plain solve with every LSQR pass on the FP64 pipe (LSQ_FLAG_NATIVE_FP64;
+    # extra key, one warm-up and one timed solve)
+    native = None
+    if not args.no_native:
+        def solve_native():
+            return ctx.lsq_solve(A, b, d, zeta=zeta, seed=C2["sketch_seed"], tol=tol, prec=P.PREC_FP64,
+                                 flags=flags | P.FLAG_NATIVE_FP64, stream=stream)
+        solve_native()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xn, inn = solve_native()
+        e1.record(stream)
+        e1.synchronize()
+        nat_ms = e0.elapsed_time(e1)
+        t_ln = inn["t_lsqr_ms"]
+        native = {"solves_per_s": 1e3 / nat_ms, "ms_per_solve": nat_ms, "steps": 1, "lsqr_iters": inn["iters"],
+                  "phases_ms": {"sketch": inn["t_sketch_ms"], "precond": inn["t_precond_ms"],
+                                "lsqr_and_check": t_ln, "check": inn["t_check_ms"]},
+                  "lsqr_gbs_algorithmic": lsqr_algorithmic_bytes(m, n, inn["iters"]) / (t_ln / 1e3) / 1e9,
+                  "rel_residual_distance_to_plain": float(torch.linalg.vector_norm(A @ (xn - xp))) / bn,
+                  "backward_error_pre": inn["backward_error_pre"], "status": inn["status"],
+                  "dtype": "LSQR passes in native FP64 (FP64 pipe, two FMA per entry); sketch and QR as plain"}
+        del xn
+
     peaks, peak_src = _peaks()
     peak = float(peaks["hbm_gbs"])
     it = statistics.mean(i["iters"] for i in infos)
@@ -733,6 +757,8 @@ def run_headline(args):
                   "dtype": "sketch: terms added in FP32 (chunk sums of ~16 terms per entry, combined in FP64); QR: FP64 (tcgen05 trailing updates, FP32 accumulation); LSQR: df47 + FP64 recurrences"},
         "clocks": clocks,
     }
+    if native is not None:
+        line["native_fp64"] = native
 
     # e2e: host (pinned) A, b through the same C ABI, copies inside the timed region
     e2e = None
@@ -1048,6 +1074,7 @@ def main():
     ap.add_argument("--max-group", type=int, default=0, help="serving: most blocks per request (0: default)")
     ap.add_argument("--batch", type=int, default=4096, help="problems in the batched config")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-native", action="store_true", help="skip the native-FP64 LSQR solve of the headline")
     ap.add_argument("--native", action="store_true", help="LSQR matvecs on the native FP64 pipe")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--m", type=int, default=0, help="custom problem rows (profiling runs)")

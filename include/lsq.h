@@ -60,7 +60,8 @@ typedef int32_t lsq_status;
  * on the FP32/integer pipes (each FP64 entry split exactly into two floats
  * holding its top 47 significant bits, products exact, sums as float pairs:
  * relative matvec error about 1e-14 against 1e-16 in FP64), unless
- * LSQ_FLAG_NATIVE_FP64 asks for the FP64 pipe (n <= 512).  The
+ * LSQ_FLAG_NATIVE_FP64 asks for the FP64 pipe (any n <= 4096; about 2.5x the
+ * time at n = 2000, the pass bound by GB300's FP64 rate).  The
  * pair image is taken of A 2^-s, b 2^-t with exact power-of-two shifts s, t
  * chosen from the largest entries, so any finite FP64 data is in range; only
  * entries below 2^-103 of the largest entry of A (or b) are flushed. */
@@ -239,9 +240,9 @@ lsq_status lsq_set_qr_mode(lsq_ctx* ctx, int32_t mode);
  * App. D.5.1.  A, b, x0, x device.  x receives the final iterate.  Stops when
  * ||(AM)^T r|| <= tol ||AM||_est ||r|| (Paige-Saunders test 2 on the
  * preconditioned problem), ||r|| <= tol ||b||, or at maxit (LSQ_ERR_NOCONV).
- * info may be NULL.  Limits: n <= 4096 (LSQ_ERR_UNSUPPORTED beyond);
- * LSQ_FLAG_NATIVE_FP64 only for n <= 512.  The same limits hold for
- * lsq_solve and lsq_check. */
+ * info may be NULL.  Limits: n <= 4096 (LSQ_ERR_UNSUPPORTED beyond), with
+ * or without LSQ_FLAG_NATIVE_FP64.  The same limits hold for lsq_solve and
+ * lsq_check. */
 lsq_status lsq_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t lda, const double* b,
                     const double* M, const double* x0, double tol, int64_t maxit, int32_t flags, double* x,
                     lsq_info* info, void* stream);

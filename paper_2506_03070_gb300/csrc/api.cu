@@ -626,8 +626,8 @@ lsq_status lsq_lsqr(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t
   if (m < 1 || n < 1 || lda < n) return fail(ctx, LSQ_ERR_ARG, "need m >= 1, n >= 1, lda >= n");
   if (!A || !b || !M || !x0 || !x) return fail(ctx, LSQ_ERR_ARG, "null pointer");
   if (n > kLsqrMaxN) return fail(ctx, LSQ_ERR_UNSUPPORTED, "LSQR kernels built for n <= 4096");
-  if ((flags & LSQ_FLAG_NATIVE_FP64) && !lsqr_native_ok(n))
-    return fail(ctx, LSQ_ERR_UNSUPPORTED, "native FP64 LSQR kernel built for n <= 512");
+  if ((flags & LSQ_FLAG_NATIVE_FP64) && n > kLsqrMaxN)
+    return fail(ctx, LSQ_ERR_UNSUPPORTED, "native FP64 LSQR kernels built for n <= 4096");
   cudaStream_t st = (cudaStream_t)stream;
   const int ni = (int)n, npad = (int)((n + 31) / 32 * 32);
   bool native = (flags & LSQ_FLAG_NATIVE_FP64) || !lsqr_df_ok(A, n, lda);
@@ -677,8 +677,8 @@ lsq_status lsq_hbm(lsq_ctx* ctx, const double* A, int64_t m, int64_t n, int64_t 
   if (!A || !b || !M || !x0 || !x) return fail(ctx, LSQ_ERR_ARG, "null pointer");
   if (!(eta_hat >= 0.0 && eta_hat < 1.0)) return fail(ctx, LSQ_ERR_ARG, "need 0 <= eta_hat < 1");
   if (n > kLsqrMaxN) return fail(ctx, LSQ_ERR_UNSUPPORTED, "LSQR kernels built for n <= 4096");
-  if ((flags & LSQ_FLAG_NATIVE_FP64) && !lsqr_native_ok(n))
-    return fail(ctx, LSQ_ERR_UNSUPPORTED, "native FP64 LSQR kernel built for n <= 512");
+  if ((flags & LSQ_FLAG_NATIVE_FP64) && n > kLsqrMaxN)
+    return fail(ctx, LSQ_ERR_UNSUPPORTED, "native FP64 LSQR kernels built for n <= 4096");
   cudaStream_t st = (cudaStream_t)stream;
   const int ni = (int)n, npad = (int)((n + 31) / 32 * 32);
   bool native = (flags & LSQ_FLAG_NATIVE_FP64) || !lsqr_df_ok(A, n, lda);
@@ -766,8 +766,8 @@ static lsq_status solve_once(lsq_ctx* ctx, const lsq_problem* pr, const lsq_opts
   if (o->prec != LSQ_PREC_FP64 && o->prec != LSQ_PREC_MIXED) return fail(ctx, LSQ_ERR_ARG, "unknown precision");
   if (pr->mem != LSQ_MEM_DEVICE && pr->mem != LSQ_MEM_HOST) return fail(ctx, LSQ_ERR_ARG, "unknown memory kind");
   if (n > kLsqrMaxN) return fail(ctx, LSQ_ERR_UNSUPPORTED, "LSQR kernels built for n <= 4096");
-  if ((o->flags & LSQ_FLAG_NATIVE_FP64) && !lsqr_native_ok(n))
-    return fail(ctx, LSQ_ERR_UNSUPPORTED, "native FP64 LSQR kernel built for n <= 512");
+  if ((o->flags & LSQ_FLAG_NATIVE_FP64) && n > kLsqrMaxN)
+    return fail(ctx, LSQ_ERR_UNSUPPORTED, "native FP64 LSQR kernels built for n <= 4096");
   cudaStream_t st = (cudaStream_t)stream;
   const bool host = pr->mem == LSQ_MEM_HOST;
   // host problems in pinned or registered memory are read in place by the

@@ -179,6 +179,9 @@ cudaError_t lsqr_rows_run(int chunks, const LsqrParams& p, int grid, cudaStream_
 int lsqr_wide_grid(int panels, int n, int sms);
 cudaError_t lsqr_wide_run(int panels, const LsqrParams& p, int grid, cudaStream_t st);
 int lsqr_native_grid(int chunks, bool vec, int sms);
+// Native FP64 kernels for 512 < n <= 4096 (panels = 2, 4 or 8 warps per row).
+int lsqr_native_wide_grid(int panels, int sms);
+cudaError_t lsqr_native_wide_run(int panels, const LsqrParams& p, int grid, cudaStream_t st);
 cudaError_t lsqr_native_run(int chunks, bool vec, const LsqrParams& p, int grid, cudaStream_t st);
 // Self-test of the bounded device waits: kind 0 -- a grid barrier of `blocks`
 // co-resident blocks that expects one block more (it can never fill); kind 1

@@ -83,6 +83,7 @@ bool lsqr_df_ok(const double* A, int64_t n, int64_t lda) {
 bool lsqr_native_ok(int64_t n) { return n >= 1 && n <= 512; }
 
 int lsqr_grid(int n, bool vec, bool native, int sms) {
+  if (native && n > 512) return lsqr_native_wide_grid(panels_for(n), sms);
   if (!native && n > 512) {
     return lsqr_wide_grid(panels_for(n), n, sms);
   }
@@ -93,6 +94,7 @@ int lsqr_grid(int n, bool vec, bool native, int sms) {
 }
 
 cudaError_t lsqr_run(const LsqrParams& p, bool vec, bool native, int grid, cudaStream_t st) {
+  if (native && p.n > 512) return lsqr_native_wide_run(panels_for(p.n), p, grid, st);
   if (!native && p.n > 512) {
     return lsqr_wide_run(panels_for(p.n), p, grid, st);
   }

@@ -268,17 +268,21 @@ __device__ __forceinline__ void row_group_bar(int rg) {
 // layout of the double-float panel pass: the block's warps form kWarps/PW row
 // groups; warp pw of a group owns columns [c0, c0 + pwid), c0 = pw * pwid,
 // pwid = ceil(n/PW) rounded up to 16 (lane l: columns c0 + 2l + 64t, t < 8).
-// Per row: each warp's partial dot of its panel with x, the partials meet in
-// shared memory at the group's named barrier (double-buffered by row
-// parity), every warp sums them in panel order (the same y in all of them),
-// y = b_i - A_i x, and each warp adds y A_ij into its panel's FP64 column sums.
-// FRO adds sum A_ij^2.  Rows are read directly (16-byte loads when A is
+// Per row: each warp's partial dot of its panel with wsign * wvec, the
+// partials meet in shared memory at the group's named barrier
+// (double-buffered by row parity), every warp sums them in panel order (the
+// same y in all of them), y = dot - gamma uin_i (the check: wvec = x,
+// wsign = gamma = -1, uin = b: y = b_i - A_i x), stored to uout when given, and
+// each warp adds y A_ij into its panel's FP64 column sums.  FRO adds sum
+// A_ij^2; UIN2 sums uin_i^2.  Rows are read directly (16-byte loads when A is
 // aligned and lda even); the pass is bound by the FP64 pipe (two FMA per
 // entry).  Outputs as the other passes: gpart row (block, row group), part
-// slots 0 (y^2), 1 (b^2), 2 (A_ij^2).
+// slots 0 (y^2), 1 (uin^2), 2 (A_ij^2).
 // --------------------------------------------------------------------------
-template <int PW, bool FRO>
-__device__ void pass_native_panel(const LsqrParams& p, double* s_scal) {
+template <int PW, bool FRO, bool UIN2>
+__device__ void pass_native_panel(const LsqrParams& p, const double* __restrict__ wvec, double wsign,
+                                  const double* __restrict__ uin, double gamma, double* __restrict__ uout,
+                                  double* s_scal) {
   constexpr int NRG = kWarps / PW, PPL = 8;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int rg = wib / PW, pw = wib % PW;
@@ -291,8 +295,8 @@ __device__ void pass_native_panel(const LsqrParams& p, double* s_scal) {
 #pragma unroll
   for (int t = 0; t < PPL; ++t) {
     const int c = c0 + 2 * lane + 64 * t;
-    xr[2 * t] = c < cend ? p.x[c] : 0.0;
-    xr[2 * t + 1] = c + 1 < cend ? p.x[c + 1] : 0.0;
+    xr[2 * t] = c < cend ? wsign * wvec[c] : 0.0;
+    xr[2 * t + 1] = c + 1 < cend ? wsign * wvec[c + 1] : 0.0;
     g[2 * t] = g[2 * t + 1] = 0.0;
   }
   double ss = 0.0, bb = 0.0, fro = 0.0;
@@ -317,7 +321,7 @@ __device__ void pass_native_panel(const LsqrParams& p, double* s_scal) {
         a[t].x = a[t].y = 0.0;
       }
     }
-    const double bi = p.b[i];
+    const double ui = uin[i];
     double dot = 0.0;
 #pragma unroll
     for (int t = 0; t < PPL; ++t) {
@@ -331,10 +335,11 @@ __device__ void pass_native_panel(const LsqrParams& p, double* s_scal) {
     double ax = slot[0];
 #pragma unroll
     for (int q = 1; q < PW; ++q) ax += slot[q];
-    const double y = bi - ax;
+    const double y = fma(-gamma, ui, ax);
     if (pw == 0) {
+      if (uout && lane == 0) uout[i] = y;
       ss = fma(y, y, ss);
-      bb = fma(bi, bi, bb);
+      if (UIN2) bb = fma(ui, ui, bb);
     }
 #pragma unroll
     for (int t = 0; t < PPL; ++t) {
@@ -367,6 +372,33 @@ __device__ void pass_native_panel(const LsqrParams& p, double* s_scal) {
   }
   __syncthreads();
 }
+
+// The native FP64 passes for wide rows (512 < n <= 4096, LSQ_FLAG_NATIVE_FP64),
+// PW warps per row in column panels: pass_native_panel above.
+template <int PW>
+struct NativePanelPass {
+  double* s_scal;  // kWarps * 6 doubles: per-warp sums, then the row groups' partial dots
+  __device__ void init(LsqrParams& p) {  // y = b - A x0 -> u; sum y^2, sum b^2
+    p.gparts = p.gcount * (kWarps / PW);
+    pass_native_panel<PW, false, true>(p, p.x, -1.0, p.b, -1.0, p.u, s_scal);
+  }
+  __device__ void iter(LsqrParams& p, double gamma) {  // y = A wv - gamma u -> u
+    p.gparts = p.gcount * (kWarps / PW);
+    pass_native_panel<PW, false, false>(p, p.wv, 1.0, p.u, gamma, p.u, s_scal);
+  }
+  __device__ void check(LsqrParams& p) {  // y = b - A x; sum y^2, b^2 (and A_ij^2 unless known)
+    p.gparts = p.gcount * (kWarps / PW);
+    if (p.fro_in)
+      pass_native_panel<PW, false, true>(p, p.x, -1.0, p.b, -1.0, nullptr, s_scal);
+    else
+      pass_native_panel<PW, true, true>(p, p.x, -1.0, p.b, -1.0, nullptr, s_scal);
+  }
+  __device__ void residual(LsqrParams& p, bool) {  // y = b - A x; sum y^2, b^2
+    p.gparts = p.gcount * (kWarps / PW);
+    pass_native_panel<PW, false, true>(p, p.x, -1.0, p.b, -1.0, nullptr, s_scal);
+  }
+};
+
 
 // --------------------------------------------------------------------------
 // The double-float pass (FP32/INT pipes only in the per-entry and per-row
@@ -921,9 +953,9 @@ struct DfPass {
     if (PW > 1) {
       p.gparts = p.gcount * (kWarps / PW);
       if (p.fro_in)
-        pass_native_panel<PW, false>(p, s_scal);
+        pass_native_panel<PW, false, true>(p, p.x, -1.0, p.b, -1.0, nullptr, s_scal);
       else
-        pass_native_panel<PW, true>(p, s_scal);
+        pass_native_panel<PW, true, true>(p, p.x, -1.0, p.b, -1.0, nullptr, s_scal);
       return;
     }
     p.gparts = p.gcount;

@@ -648,11 +648,14 @@ def test_lsqr_wide_rows_match_oracle(ctx, orc, m, n, d, lda_pad):
         assert abs(inf["iters"] - ref["iters"]) <= 2, (inf["iters"], ref["iters"])
         assert np.linalg.norm(A @ (xx - ref["x"])) <= 1e-10 * bn
         assert orc.backward_error_kw(A, b, xx) <= 1e-10
-    # the FP64-pipe kernel is built for n <= 512 only
-    import paper_2506_03070_gb300 as P
-    with pytest.raises(P.LsqError) as e:
-        ctx.lsq_lsqr(Ad, _dev(b), _dev(Mo), _dev(x0), 1e-12, maxit, flags=NATIVE)
-    assert e.value.status == -10
+    # the same rows on the FP64 pipe (LSQ_FLAG_NATIVE_FP64: every pass native,
+    # same panel layout): the oracle's iterates too
+    x_nv, info_nv = ctx.lsq_lsqr(Ad, _dev(b), _dev(Mo), _dev(x0), 1e-12, maxit, flags=NATIVE)
+    assert info_nv["status"] == 0
+    assert abs(info_nv["iters"] - ref["iters"]) <= 2, (info_nv["iters"], ref["iters"])
+    x_nv = x_nv.cpu().numpy()
+    assert np.linalg.norm(A @ (x_nv - ref["x"])) <= 1e-10 * bn
+    assert orc.backward_error_kw(A, b, x_nv) <= 1e-10
 
 
 def test_check_wide_rows_matches_oracle(ctx, orc):
@@ -668,10 +671,12 @@ def test_check_wide_rows_matches_oracle(ctx, orc):
     assert abs(info["anorm_fro"] - parts["fro"]) <= 1e-13 * parts["fro"]
 
 
-def test_solve_wide_rows(ctx, orc):
-    """Whole solve (sketch, QR, inverse, LSQR, check) at n = 1000, d = 4n."""
+@pytest.mark.parametrize("flags", [0, NATIVE])
+def test_solve_wide_rows(ctx, orc, flags):
+    """Whole solve (sketch, QR, inverse, LSQR, check) at n = 1000, d = 4n, with
+    the double-float passes and with native FP64 ones."""
     A, b, xt = _problem(20000, 1000, 1e8, 31)
-    x, info = ctx.lsq_solve(_dev(A), _dev(b), 4000, zeta=8, seed=11, tol=1e-12)
+    x, info = ctx.lsq_solve(_dev(A), _dev(b), 4000, zeta=8, seed=11, tol=1e-12, flags=flags)
     x = x.cpu().numpy()
     assert info["status"] == 0 and info["stop"] in (1, 2)
     assert orc.backward_error_kw(A, b, x) <= 1e-10
