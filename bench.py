@@ -969,7 +969,8 @@ def run_gpu(args, emit=True):
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": _workload(p, args.prec),
-        "roofline": {"bound": "hbm", "kernel": "k_lsqr_native" if args.native else ("k_lsqr_dfp" if n > 512 else "k_lsqr_df"),
+        "roofline": {"bound": "hbm", "kernel": (("k_lsqr_native_wide" if n > 512 else "k_lsqr_native") if args.native
+                                                else ("k_lsqr_dfp" if n > 512 else "k_lsqr_df")),
                      "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None if args.native else (LSQR_DFP_TRAFFIC_RATIO if n > 512 else LSQR_DF_TRAFFIC_RATIO)
