@@ -473,10 +473,13 @@ def test_solve_automatic_embedding_dimension(ctx, orc):
     assert np.linalg.norm(A @ (x.cpu().numpy() - xt)) <= 1e-10 * np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("m,n,d", [(20000, 100, 400), (12000, 600, 2400)])
-def test_hbm_matches_oracle(ctx, orc, m, n, d):
+@pytest.mark.parametrize("m,n,d,flags", [(20000, 100, 400, 0), (12000, 600, 2400, 0), (12000, 600, 2400, 4),
+                                         (8000, 100, 400, 4)])
+def test_hbm_matches_oracle(ctx, orc, m, n, d, flags):
     """Heavy-ball momentum (Algorithm 6): the iterates after k updates follow
-    the oracle's, and the converged solve takes the oracle's iteration count."""
+    the oracle's, and the converged solve takes the oracle's iteration count;
+    flags 4 (LSQ_FLAG_NATIVE_FP64): every pass on the FP64 pipe, one warp per
+    row (n = 100) or column panels (n = 600)."""
     A, b, xt = _problem(m, n, 1e6, m + n + 1)
     Yo = orc.sketch_apply(A, b, d, 8, 3)
     Ro = np.linalg.qr(Yo, mode="r")
@@ -487,11 +490,11 @@ def test_hbm_matches_oracle(ctx, orc, m, n, d):
     bn = np.linalg.norm(b)
     for k in (3, 12):
         ref = orc.hbm(A, b, Mo, x0, a, beta, 1e-30, k)
-        x, info = ctx.lsq_hbm(_dev(A), _dev(b), _dev(Mo), _dev(x0), 1e-30, k, eta)
+        x, info = ctx.lsq_hbm(_dev(A), _dev(b), _dev(Mo), _dev(x0), 1e-30, k, eta, flags=flags)
         assert info["iters"] == k and info["status"] == -7 and info["stop"] == 3
         assert np.linalg.norm(A @ (x.cpu().numpy() - ref["x"])) <= 1e-10 * bn
     ref = orc.hbm(A, b, Mo, x0, a, beta, 1e-12, 500)
-    x, info = ctx.lsq_hbm(_dev(A), _dev(b), _dev(Mo), _dev(x0), 1e-12, 500, eta)
+    x, info = ctx.lsq_hbm(_dev(A), _dev(b), _dev(Mo), _dev(x0), 1e-12, 500, eta, flags=flags)
     assert ref["stop"] in (1, 2) and info["status"] == 0
     assert abs(info["iters"] - ref["iters"]) <= 2, (info["iters"], ref["iters"])
     assert orc.backward_error_kw(A, b, x.cpu().numpy()) <= 1e-10
