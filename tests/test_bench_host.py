@@ -48,3 +48,17 @@ def test_clock_record_without_nvidia_smi_is_none(monkeypatch):
     if c.proc is not None:  # pragma: no cover - nvidia-smi found outside PATH
         pytest.skip("nvidia-smi available")
     assert c.stop() is None and not os.path.exists(c.path)
+
+
+def test_launch_count_follows_the_library_plan():
+    """The claimed launch count per solve: the FP64 sketch's column slabs (at most
+    48e6 bytes of Y, a multiple of 32 columns), the blocked QR's 9 kernels per
+    64-column panel, and the fixed kernels around them -- the counts the ncu launch
+    list of the 5e6 x 2000 bench line showed (298 plain, 297 mixed)."""
+    b = _bench()
+    assert b.sketch_slabs(8000, 2001) == 3   # 736 columns of 64 KB each per slab
+    assert b.sketch_slabs(2000, 501) == 1    # Y of 8 MB: one launch
+    assert b.sketch_slabs(10 ** 6, 33) == 2  # d so large that a slab is the 32-column minimum
+    assert b.launches_per_solve(2000, 8000, 0, True) == 298
+    assert b.launches_per_solve(2000, 8000, 1, True) == 297
+    assert b.launches_per_solve(500, 2000, 0, False) == 9
