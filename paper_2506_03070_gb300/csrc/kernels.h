@@ -164,7 +164,8 @@ enum {
 constexpr int kLsqrMaxN = 4096;
 // True when the double-float LSQR kernel applies (1 <= n <= kLsqrMaxN).
 bool lsqr_df_ok(const double* A, int64_t n, int64_t lda);
-// True when the native-FP64 LSQR kernel (one warp per row) applies: n <= 512.
+// True when the one-warp-per-row native-FP64 LSQR kernel applies: n <= 512
+// (LSQ_FLAG_NATIVE_FP64 runs the column-panel native kernel beyond that).
 bool lsqr_native_ok(int64_t n);
 // Rows of gpart the LSQR kernel needs for a grid (per-warp partials).
 int lsqr_gparts(int grid);

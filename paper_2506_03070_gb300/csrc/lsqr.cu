@@ -17,7 +17,8 @@
 // accuracy check) and the backward-error bounds.
 // The kernels are instantiated in lsqr_rows.cu (double-float, n <= 512),
 // lsqr_wide.cu (double-float, 512 < n <= 4096) and lsqr_native.cu (native
-// FP64, n <= 512); this file dispatches to them and holds the wait self-tests.
+// FP64: one warp per row for n <= 512, column panels up to 4096); this file
+// dispatches to them and holds the wait self-tests.
 #include "lsqr_device.cuh"
 
 namespace lsq {
